@@ -1,0 +1,424 @@
+"""Benchmark: GP operations per second (tree nodes x fitness cases / s) of one
+generation step on a GB300, through libgp's C ABI.
+
+Workload (one step): the resident population of 4000 seeded random trees
+(odd sizes log-uniform on [31, 32767], 48 Sextic fitness cases, 127 seeded
+constants) produces 4000 children by subtree crossover at uniformly chosen
+points (Sec. 3.1), and every child is evaluated (Sec. 2.2) and reduced to its
+mean absolute error (Table gp.details).  `value` = child nodes x 48 / step
+time, inputs resident in HBM; `e2e` repeats the step from pinned host buffers
+through the public API, copies included.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1902_09215_gb300 import synth  # noqa: E402
+
+N_TREES = 4000
+SEED_POP, SEED_XO, CONST_SEED = 3, 11, 2
+WORKLOAD = ("4000 seeded random prefix trees, odd sizes log-uniform 31..32767 nodes, "
+            "48 Sextic cases, 127 constants; step = 4000 subtree crossovers + fitness "
+            "evaluation of the 4000 children")
+METRIC = "GPops/s (tree nodes x fitness cases per second), generation step"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_workload(rank: int):
+    x, y, c = synth.problem(const_seed=CONST_SEED)
+    nodes, offs = synth.population_loguniform(seed=SEED_POP + 1000 * rank, count=N_TREES)
+    sizes = np.diff(offs.astype(np.int64))
+    ops = synth.crossover_points(SEED_XO + 1000 * rank, sizes, N_TREES)
+    return x, y, c, nodes, offs, ops
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("gp_eval.cu", "gp_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1902_09215_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the evaluator from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "eval_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1902_09215_gb300 import gp
+    gp.lib()
+
+    x, y, c, nodes, offs, ops = make_workload(rank)
+    stream = torch.cuda.Stream(dev)
+    prob = gp.Problem(x, y, c)
+    xo = gp.make_xo(*ops)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    with torch.cuda.stream(stream):
+        parents = gp.gp_create_population(prob, nodes, offs, stream)
+
+    def step():
+        kids = gp.gp_crossover(parents, xo, stream)
+        gp.gp_evaluate(kids, stream)
+        return kids
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also sizes the child population)
+    kids = None
+    for _ in range(args.warmup):
+        kids = step()
+        gp.gp_fitness(kids)
+    child_nodes = int(gp.gp_population_get_info(kids).total_nodes)
+    stats = gp.gp_eval_stats_get(kids)
+    del kids
+
+    # ---- timed: K steps, L2 flushed before each, device time per step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    keep = []
+    barrier()
+    launches0 = gp.gp_kernel_launch_count()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[k][0].record(stream)
+                keep.append(step())
+                ev[k][1].record(stream)
+            if len(keep) > 4:
+                keep.pop(0)
+        barrier()
+        wall = time.perf_counter() - t0
+    launches = gp.gp_kernel_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    keep.clear()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = child_nodes * prob.n_cases * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # ---- evaluation alone and crossover alone (device time), same flushing
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+            out.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in out]
+
+    kids = step()
+    gp.gp_fitness(kids)
+    eval_ms = timed(lambda: gp.gp_evaluate(kids, stream), max(10, args.steps // 4))
+    xo_ms = timed(lambda: gp.gp_crossover(parents, xo, stream), max(10, args.steps // 4))
+    child_bytes = child_nodes
+
+    # ---- roofline of the dominant kernel: CUDA events around each launch
+    gp.gp_profile_read(reset=True)
+    gp.gp_profile_enable(True)
+    for _ in range(max(10, args.steps // 4)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            k2 = step()
+    torch.cuda.synchronize()
+    gp.gp_profile_enable(False)
+    prof = gp.gp_profile_read(reset=True)
+    del k2
+    ev0 = prof["eval"]
+    eval_launch_ms = ev0["ms"] / max(ev0["launches"], 1)
+    # algorithmic work of one evaluation: (n-1)/2 binary FP32 operations per
+    # tree per case; the level-0 launch does all but the deferred spine ops
+    n_bin_ops = (child_nodes - N_TREES) // 2 * prob.n_cases
+    peaks, peak_src = measured_peaks()
+    clocks = clk.summary()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12           # FP32 lanes x clock, Tops/s
+    achieved = n_bin_ops / (eval_launch_ms / 1e3) / 1e12
+    traffic = recorded_traffic()
+
+    # ---- end to end through the public API from pinned host memory
+    pin_nodes = torch.from_numpy(nodes).pin_memory()
+    pin_offs = torch.from_numpy(offs.astype(np.uint64).view(np.int64)).pin_memory()
+    nodes_h = pin_nodes.numpy()
+    offs_h = pin_offs.numpy().view(np.uint64)
+    e2e_steps = max(5, args.steps // 10)
+    barrier()
+    te = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        p2 = gp.gp_create_population(prob, nodes_h, offs_h, stream)
+        k3 = gp.gp_crossover(p2, xo, stream)
+        gp.gp_evaluate(k3, stream)
+        fit, _, _ = gp.gp_fitness(k3)
+        te.append(time.perf_counter() - a)
+        del p2, k3
+    e2e_s = float(np.median(te))
+    e2e_value = child_nodes * prob.n_cases * world / e2e_s
+    h2d = int(nodes.nbytes + offs.nbytes + 4 * (x.size + y.size + c.size) + 24 * N_TREES)
+    d2h = int(4 * N_TREES)
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = cpu_baseline(nodes, offs, ops, x, y, c, child_nodes) if world == 1 and not args.no_cpu else None
+    step_sorted = sorted(step_ms)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "GPops/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "trees": N_TREES, "child_nodes_per_step": child_nodes, "cases": int(prob.n_cases),
+            "seeds": {"population": SEED_POP, "crossover": SEED_XO, "constants": CONST_SEED},
+            "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write, outside the events)",
+            "parallelism": f"replicas x{world} (independent populations)",
+            "eval_levels": stats["levels"], "eval_items": stats["items"],
+        },
+        "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
+                       "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
+        "eval_only": {"value": child_nodes * prob.n_cases / (statistics.median(eval_ms) / 1e3),
+                      "unit": "GPops/s", "ms_p50": statistics.median(eval_ms)},
+        "crossover": {"ms_p50": statistics.median(xo_ms),
+                      "GB_per_s": 2 * child_bytes / (statistics.median(xo_ms) / 1e3) / 1e9},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "GPops/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "wall_s_p50": e2e_s},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": "eval_kernel (level 0)",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "peak_note": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_src} max clock); "
+                                  "achieved = (n-1)/2 binary ops x 48 cases per tree / mean launch time",
+                     "launch_ms": eval_launch_ms, "launches_profiled": ev0["launches"],
+                     "kernel_share": {k: v["ms"] for k, v in prof.items() if v["launches"]}},
+        "wall_s": wall,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(nodes, offs, ops, x, y, c, child_nodes):
+    """The oracle as it stands, on this host's cores: children of a bounded
+    sample of the crossover records, evaluated by the oracle's dynamic
+    work queue over all cores, repeated for about 10 s."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    sample = 1000
+    mum, dad, mp, dp = (a[:sample] for a in ops)
+    t0 = time.perf_counter()
+    done_nodes, reps = 0, 0
+    while True:
+        rn, ro = oracle.crossover_population(nodes, offs, mum, dad, mp, dp)
+        oracle.eval_population(rn, ro, x, y, c, n_threads=cores)
+        done_nodes += int(ro[-1])
+        reps += 1
+        if time.perf_counter() - t0 > 10.0:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done_nodes * len(x) / el, "unit": "GPops/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x (crossover of the first {sample} of the 4000 records + oracle "
+                      f"evaluation of those children on {cores} threads), {el:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle, timed as it stands on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle
+    oracle.build()
+    x, y, c, nodes, offs, ops = make_workload(0)
+    cores = os.cpu_count() or 1
+    sample = 200
+    mum, dad, mp, dp = (a[:sample] for a in ops)
+
+    def step():
+        rn, ro = oracle.crossover_population(nodes, offs, mum, dad, mp, dp)
+        oracle.eval_population(rn, ro, x, y, c, n_threads=cores)
+        return int(ro[-1])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    n = 0
+    times = []
+    for _ in range(args.steps):
+        a = time.perf_counter()
+        n += step()
+        times.append(time.perf_counter() - a)
+    el = time.perf_counter() - t0
+    value = n * len(x) / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GPops/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "trees": N_TREES,
+                   "sample": f"each step: first {sample} of the 4000 crossover records"},
+        "cpu_baseline": {"value": value, "unit": "GPops/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} of 4000 crossover records per step, oracle on {cores} threads"},
+        "e2e": {"value": value, "unit": "GPops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

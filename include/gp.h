@@ -1,0 +1,185 @@
+/*
+ * libgp: GB300 (sm_103a) fitness evaluation and subtree crossover of linear
+ * prefix GP trees, after Langdon & Banzhaf, "Faster Genetic Programming
+ * GPquick via multicore and Advanced Vector Extensions" (2019).
+ *
+ * Conventions for every call:
+ *   - Plain C ABI: no exceptions cross it; every call returns gp_status and
+ *     leaves its out-parameters untouched unless it returns GP_OK.
+ *   - Host pointers are owned by the caller and only read (or written, for
+ *     outputs) during the call; libgp copies what it keeps.
+ *   - libgp owns all device memory of a population.  Device buffers are
+ *     allocated with the stream-ordered allocator on the call's stream.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Work is enqueued on it asynchronously unless the call
+ *     says it synchronises.  Calls that touch the same population must be
+ *     ordered by the caller (e.g. all on one stream).
+ *   - Tree encoding (Sec. 2.1-2.2: one byte per node, root first, prefix
+ *     order): 0 '+', 1 '-', 2 '*', 3 protected '/', 4 'x',
+ *     5..5+n_consts-1 constant table entry (code - 5).  Codes 0..3 have two
+ *     arguments, the first argument immediately follows the operator.
+ *   - Not thread-safe per population; distinct populations may be used from
+ *     distinct host threads.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gp_status {
+    GP_OK = 0,
+    GP_EINVAL = 1,      /* bad argument (null pointer, index or size out of range) */
+    GP_ENOMEM = 2,      /* device or host allocation failed, or HBM budget exceeded */
+    GP_EMALFORMED = 3,  /* a tree is not one valid prefix tree over the code table */
+    GP_ECUDA = 4,       /* a CUDA runtime call or kernel failed */
+    GP_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
+    GP_ELIMIT = 6       /* a tree would exceed the problem's node limit */
+} gp_status;
+
+/* Problem definition (Table gp.details): fitness cases, constants, protected
+ * division value and limits.  Copied by gp_create_population. */
+typedef struct gp_problem {
+    uint32_t n_cases;            /* 1..64 fitness cases (the paper uses 48)            */
+    const float *x;              /* host [n_cases] inputs                              */
+    const float *y;              /* host [n_cases] targets                             */
+    uint32_t n_consts;           /* 0..127 constants, codes 5..5+n_consts-1            */
+    const float *consts;         /* host [n_consts]                                    */
+    float protected_div_value;   /* result of a/b when b == 0 (the paper: 1.0f)       */
+    uint64_t max_tree_nodes;     /* node limit for crossover children, 0 = none        */
+    uint64_t hbm_budget_bytes;   /* device bytes a population may hold, 0 = no limit   */
+} gp_problem;
+
+/* One subtree crossover (Sec. 3.1): the child is tree `mum` with the subtree
+ * rooted at node `mum_point` replaced by the subtree of tree `dad` rooted at
+ * node `dad_point`.  Points are node indices in prefix order. */
+typedef struct gp_xo {
+    uint32_t mum, dad;
+    uint64_t mum_point, dad_point;
+} gp_xo;
+
+/* Optional evaluation tuning.  Zero fields mean "choose automatically". */
+typedef struct gp_eval_options {
+    uint32_t chunk_nodes;     /* nodes per independent evaluation chunk (multiple of 16) */
+    uint32_t warps_per_cta;   /* warps of the persistent evaluator per SM (1..32)        */
+    uint32_t window_entries;  /* shared-memory stack entries per warp (even, >= 16)      */
+} gp_eval_options;
+
+/* Device-side view of a population, for zero-copy use by the caller. */
+typedef struct gp_population_info {
+    uint32_t n_trees;
+    uint32_t n_cases;
+    uint64_t total_nodes;
+    const uint8_t *d_nodes;      /* device arena; tree t starts at d_tree_start[t]    */
+    const uint64_t *d_tree_start;
+    const uint64_t *d_tree_size;
+    const float *d_fitness;      /* [n_trees], valid after gp_evaluate                 */
+    const float *d_case_values;  /* [n_trees * n_cases] per-case outputs               */
+    const uint32_t *d_hits;      /* [n_trees] cases with |error| < 0.01                */
+} gp_population_info;
+
+typedef struct gp_population gp_population;
+
+/* Upload `n_trees` trees (packed: tree t is nodes[offsets[t] .. offsets[t+1]),
+ * offsets has n_trees+1 entries, offsets[0] = 0) and validate them on the
+ * device (Sec. 2.1 encoding: every tree is exactly one prefix tree and uses
+ * only codes < 5 + n_consts).  Synchronises with `cuda_stream` once to read
+ * the validation result.  n_trees may be 0.
+ * Errors: GP_EINVAL (null/inconsistent arguments), GP_EMALFORMED (a tree
+ * fails validation), GP_ENOMEM (allocation or budget), GP_ECUDA. */
+gp_status gp_create_population(const gp_problem *problem, uint32_t n_trees,
+                               const uint8_t *nodes, const uint64_t *offsets,
+                               void *cuda_stream, gp_population **out);
+
+/* Create one child per record (Sec. 3.1; the choice of points is the
+ * caller's, made sequentially as in Sec. 2.3, and the copies run on the
+ * device).  Children form a new population with the parents' problem; its
+ * fitness is not evaluated.  Synchronises once to size the children.
+ * Errors: GP_EINVAL (index or point out of range), GP_ELIMIT (a child exceeds
+ * problem->max_tree_nodes), GP_ENOMEM, GP_ECUDA. */
+gp_status gp_crossover(const gp_population *parents, const gp_xo *ops, uint32_t n_ops,
+                       void *cuda_stream, gp_population **children_out);
+
+/* Evaluate every tree on every fitness case (Sec. 2.2 single-pass
+ * evaluation, Table gp.details protected division) and reduce each tree to
+ * its mean absolute error with a sequential fold in case order (Sec. 2.2,
+ * Sec. 3.2) and its hit count.  Asynchronous on `cuda_stream` except for a
+ * short synchronisation when a tree is split into chunks and its upper tree
+ * must be sized.  Results are read with gp_fitness.
+ * Errors: GP_EINVAL, GP_ENOMEM, GP_ECUDA. */
+gp_status gp_evaluate(gp_population *pop, void *cuda_stream);
+gp_status gp_evaluate_ex(gp_population *pop, const gp_eval_options *opt, void *cuda_stream);
+
+/* Wait for the last gp_evaluate of `pop` and copy results to the host.
+ * fitness: [n_trees] MAE (required); case_values: [n_trees * n_cases] per-case
+ * outputs or NULL; hits: [n_trees] or NULL.
+ * Errors: GP_EINVAL (not evaluated yet), GP_EMALFORMED / GP_ECUDA (a device
+ * error recorded during evaluation). */
+gp_status gp_fitness(const gp_population *pop, float *fitness, float *case_values,
+                     uint32_t *hits);
+
+/* Node count of tree `tree`.  Errors: GP_EINVAL. */
+gp_status gp_tree_size(const gp_population *pop, uint32_t tree, uint64_t *n);
+
+/* Copy tree `tree`'s bytes to host `dst` (cap >= its size).  Synchronous.
+ * Errors: GP_EINVAL (cap too small / bad index), GP_ECUDA. */
+gp_status gp_tree_read(const gp_population *pop, uint32_t tree, uint8_t *dst, uint64_t cap);
+
+/* Device pointers and sizes of a population (valid until it is destroyed). */
+gp_status gp_population_get_info(const gp_population *pop, gp_population_info *info);
+
+/* Free a population's device memory (stream-ordered on the stream it was
+ * last used with).  NULL is ignored. */
+void gp_destroy_population(gp_population *pop);
+
+/* Static, human-readable name of a status. */
+const char *gp_status_string(gp_status st);
+
+/* ---- Introspection and measurement (not part of the paper's method). ---- */
+
+/* Shape of the last gp_evaluate of a population: evaluation levels (1 when
+ * no tree was split into chunks), work items over all levels, upper-tree
+ * codes and value-buffer entries created by chunked trees. */
+typedef struct gp_eval_stats {
+    uint32_t levels;
+    uint32_t pad;
+    uint64_t items;
+    uint64_t upper_codes;
+    uint64_t value_entries;
+} gp_eval_stats;
+gp_status gp_eval_stats_get(const gp_population *pop, gp_eval_stats *out);
+
+/* Number of CUDA kernels libgp has launched in this process (all devices). */
+uint64_t gp_kernel_launch_count(void);
+
+/* Kernel kinds for gp_profile_read. */
+enum {
+    GP_KERNEL_EVAL = 0,        /* level-0 evaluator over tree bytes           */
+    GP_KERNEL_EVAL_UPPER = 1,  /* evaluator over upper-tree codes             */
+    GP_KERNEL_PLAN = 2,        /* chunk planning                              */
+    GP_KERNEL_SCAN = 3,        /* plan prefix scan                            */
+    GP_KERNEL_VALIDATE = 4,    /* upload validation                           */
+    GP_KERNEL_EXTENT = 5,      /* crossover subtree extents                   */
+    GP_KERNEL_COPY = 6,        /* crossover / upload segment copy             */
+    GP_KERNEL_KINDS = 8
+};
+typedef struct gp_kernel_profile {
+    uint64_t launches[GP_KERNEL_KINDS];
+    double total_ms[GP_KERNEL_KINDS];
+} gp_kernel_profile;
+
+/* When enabled, every kernel launch is bracketed by CUDA events recorded on
+ * the stream it is launched on.  gp_profile_read waits for the recorded
+ * events, accumulates their elapsed times per kind and returns the running
+ * totals (reset != 0 clears them afterwards). */
+gp_status gp_profile_enable(int on);
+gp_status gp_profile_read(gp_kernel_profile *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H */

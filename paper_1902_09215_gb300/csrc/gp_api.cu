@@ -1,0 +1,827 @@
+// libgp host side: the C ABI of include/gp.h, population memory, the chunk /
+// upper-tree level planner and kernel launches.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "gp.h"
+#include "gp_internal.cuh"
+
+using namespace gpk;
+
+namespace {
+
+// ---------------------------------------------------------------- profiling
+
+std::atomic<uint64_t> g_launches{0};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+double g_prof_ms[GP_KERNEL_KINDS] = {};
+uint64_t g_prof_n[GP_KERNEL_KINDS] = {};
+
+struct ProfScope {
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(int k, cudaStream_t st) : kind(k), s(st) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (g_prof_on && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, s);
+        else
+            a = b = nullptr;
+    }
+    ~ProfScope() {
+        if (a) {
+            cudaEventRecord(b, s);
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            g_prof_pending.push_back({kind, a, b});
+        }
+    }
+};
+
+// ---------------------------------------------------------------- helpers
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return fail_cuda(e_); \
+    } while (0)
+
+gp_status fail_cuda(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return GP_ENOMEM;
+    }
+    return GP_ECUDA;
+}
+
+std::once_flag g_pool_once[64];
+
+void configure_pool(int dev)
+{
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(g_pool_once[dev], [dev]() {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+inline uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+int lanes_for(uint32_t n_cases)
+{
+    if (n_cases <= 16) return 8;
+    if (n_cases <= 32) return 16;
+    if (n_cases <= 48) return 24;
+    return 32;
+}
+
+// Device allocations freed together (stream-ordered).
+struct DevBufs {
+    std::vector<void *> ptrs;
+    cudaError_t alloc(void **p, size_t bytes, cudaStream_t s) {
+        *p = nullptr;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(p, bytes, s);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    void release(cudaStream_t s) {
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+        ptrs.clear();
+    }
+};
+
+int sm_count(int dev)
+{
+    static std::mutex mu;
+    static int cache[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64) cache[dev] = v;
+    return v;
+}
+
+cudaError_t prepare_eval_once(int lanes, bool wide, size_t smem)
+{
+    static std::mutex mu;
+    static size_t done[2][33] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[wide][lanes] >= smem) return cudaSuccess;
+    cudaError_t e = eval_prepare(lanes, wide, smem);
+    if (e == cudaSuccess) done[wide][lanes] = smem;
+    return e;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- population
+
+struct gp_population {
+    int device = 0;
+    cudaStream_t stream = nullptr;          // stream of the last call
+    // problem
+    uint32_t n_cases = 0, lanes = 0, n_consts = 0;
+    float div0 = 1.0f;
+    uint64_t max_tree_nodes = 0, hbm_budget = 0;
+    std::vector<float> hx, hy, hc;          // x, y padded to 2*lanes; constants
+    // trees
+    uint32_t n_trees = 0;
+    uint64_t total_nodes = 0, arena_bytes = 0;
+    std::vector<uint64_t> h_start, h_size;
+    // device
+    DevBufs mem;
+    uint8_t *d_arena = nullptr;
+    uint64_t *d_start = nullptr, *d_size = nullptr;
+    float *d_x = nullptr, *d_y = nullptr, *d_c = nullptr;
+    float *d_fitness = nullptr, *d_values = nullptr;
+    uint32_t *d_hits = nullptr, *d_err = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool evaluated = false;
+    gp_eval_stats stats{};
+};
+
+namespace {
+
+uint64_t population_bytes(uint64_t arena, uint32_t n_trees, uint32_t n_cases)
+{
+    return arena + (uint64_t)n_trees * (16 + 8 + 4ull * n_cases) + 4096;
+}
+
+// Allocate a population's device memory for the given layout (trees not
+// copied yet) and upload the problem tables.
+gp_status alloc_population(gp_population *P, cudaStream_t s)
+{
+    P->stream = s;
+    CK(P->mem.alloc((void **)&P->d_arena, P->arena_bytes, s));
+    CK(P->mem.alloc((void **)&P->d_start, sizeof(uint64_t) * (P->n_trees + 1), s));
+    CK(P->mem.alloc((void **)&P->d_size, sizeof(uint64_t) * (P->n_trees + 1), s));
+    CK(P->mem.alloc((void **)&P->d_fitness, sizeof(float) * (P->n_trees + 1), s));
+    CK(P->mem.alloc((void **)&P->d_values, sizeof(float) * ((uint64_t)P->n_trees * P->n_cases + 1), s));
+    CK(P->mem.alloc((void **)&P->d_hits, sizeof(uint32_t) * (P->n_trees + 1), s));
+    CK(P->mem.alloc((void **)&P->d_err, sizeof(uint32_t) * 4, s));
+    CK(P->mem.alloc((void **)&P->d_x, sizeof(float) * 2 * P->lanes, s));
+    CK(P->mem.alloc((void **)&P->d_y, sizeof(float) * 2 * P->lanes, s));
+    CK(P->mem.alloc((void **)&P->d_c, sizeof(float) * (P->n_consts + 1), s));
+    CK(cudaMemcpyAsync(P->d_x, P->hx.data(), sizeof(float) * 2 * P->lanes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P->d_y, P->hy.data(), sizeof(float) * 2 * P->lanes, cudaMemcpyHostToDevice, s));
+    if (P->n_consts)
+        CK(cudaMemcpyAsync(P->d_c, P->hc.data(), sizeof(float) * P->n_consts, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
+    if (P->n_trees) {
+        CK(cudaMemcpyAsync(P->d_start, P->h_start.data(), sizeof(uint64_t) * P->n_trees,
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(P->d_size, P->h_size.data(), sizeof(uint64_t) * P->n_trees,
+                           cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
+    return GP_OK;
+}
+
+// 16-byte aligned starts for the given sizes.
+void layout_trees(gp_population *P)
+{
+    uint64_t pos = 0;
+    P->h_start.resize(P->n_trees);
+    P->total_nodes = 0;
+    for (uint32_t t = 0; t < P->n_trees; ++t) {
+        P->h_start[t] = pos;
+        pos = round_up(pos + P->h_size[t], 16);
+        P->total_nodes += P->h_size[t];
+    }
+    P->arena_bytes = pos + 64;                // padding for 16-code groups and word loads
+}
+
+void destroy(gp_population *P)
+{
+    if (!P) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(P->device);
+    P->mem.release(P->stream);
+    if (P->ev) cudaEventDestroy(P->ev);
+    cudaSetDevice(cur);
+    delete P;
+}
+
+struct Stream {
+    cudaStream_t s;
+    explicit Stream(void *p) : s(static_cast<cudaStream_t>(p)) {}
+};
+
+// Copy contiguous source ranges to aligned destinations with the segment
+// copy kernel (used for upload re-layout and crossover children).
+gp_status run_copy(const uint8_t *src, uint8_t *dst, const std::vector<XoChild> &kids,
+                   cudaStream_t s, DevBufs &tmp)
+{
+    const uint32_t tile = 16384;
+    std::vector<XoTile> tiles;
+    for (uint32_t c = 0; c < kids.size(); ++c)
+        for (uint64_t b = 0; b < kids[c].n; b += tile) tiles.push_back(XoTile{c, 0, b});
+    if (tiles.empty()) return GP_OK;
+    if (tiles.size() > 0x7fffffffu) return GP_EINVAL;
+    XoChild *d_kids;
+    XoTile *d_tiles;
+    CK(tmp.alloc((void **)&d_kids, sizeof(XoChild) * kids.size(), s));
+    CK(tmp.alloc((void **)&d_tiles, sizeof(XoTile) * tiles.size(), s));
+    CK(cudaMemcpyAsync(d_kids, kids.data(), sizeof(XoChild) * kids.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(XoTile) * tiles.size(), cudaMemcpyHostToDevice, s));
+    ProfScope ps(GP_KERNEL_COPY, s);
+    CK(launch_xo_copy(src, dst, d_kids, d_tiles, (uint32_t)tiles.size(), tile, s));
+    return GP_OK;
+}
+
+// Device validation of every tree (see gp_create_population).
+gp_status validate_population(gp_population *P, cudaStream_t s, DevBufs &tmp, bool *ok)
+{
+    const uint64_t VC = 1 << 16;
+    std::vector<EvalItem> chunks;
+    std::vector<uint32_t> first(P->n_trees + 1);
+    for (uint32_t t = 0; t < P->n_trees; ++t) {
+        first[t] = (uint32_t)chunks.size();
+        for (uint64_t b = 0; b < P->h_size[t]; b += VC) {
+            EvalItem it{};
+            it.begin = P->h_start[t] + b;
+            it.end = P->h_start[t] + std::min(P->h_size[t], b + VC);
+            it.tree = t;
+            chunks.push_back(it);
+        }
+    }
+    first[P->n_trees] = (uint32_t)chunks.size();
+    EvalItem *d_chunks;
+    ValOut *d_out;
+    uint32_t *d_first, *d_bad;
+    CK(tmp.alloc((void **)&d_chunks, sizeof(EvalItem) * chunks.size(), s));
+    CK(tmp.alloc((void **)&d_out, sizeof(ValOut) * chunks.size(), s));
+    CK(tmp.alloc((void **)&d_first, sizeof(uint32_t) * first.size(), s));
+    CK(tmp.alloc((void **)&d_bad, sizeof(uint32_t), s));
+    CK(cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(EvalItem) * chunks.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_first, first.data(), sizeof(uint32_t) * first.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(uint32_t), s));
+    {
+        ProfScope ps(GP_KERNEL_VALIDATE, s);
+        CK(launch_validate(P->d_arena, d_chunks, (uint32_t)chunks.size(), P->n_consts, d_out, s));
+    }
+    {
+        ProfScope ps(GP_KERNEL_VALIDATE, s);
+        CK(launch_validate_trees(d_out, d_first, P->n_trees, d_bad, s));
+    }
+    uint32_t bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *ok = (bad == 0);
+    return GP_OK;
+}
+
+gp_status copy_problem(gp_population *P, const gp_problem *pr)
+{
+    if (!pr || pr->n_cases == 0 || pr->n_cases > kMaxCases || !pr->x || !pr->y) return GP_EINVAL;
+    if (pr->n_consts > 127 || (pr->n_consts && !pr->consts)) return GP_EINVAL;
+    P->n_cases = pr->n_cases;
+    P->lanes = lanes_for(pr->n_cases);
+    P->n_consts = pr->n_consts;
+    P->div0 = pr->protected_div_value;
+    P->max_tree_nodes = pr->max_tree_nodes;
+    P->hbm_budget = pr->hbm_budget_bytes;
+    P->hx.assign(2 * P->lanes, 0.0f);
+    P->hy.assign(2 * P->lanes, 0.0f);
+    std::memcpy(P->hx.data(), pr->x, sizeof(float) * pr->n_cases);
+    std::memcpy(P->hy.data(), pr->y, sizeof(float) * pr->n_cases);
+    P->hc.assign(pr->consts ? pr->consts : nullptr, pr->consts ? pr->consts + pr->n_consts : nullptr);
+    return GP_OK;
+}
+
+void copy_problem_from(gp_population *dst, const gp_population *src)
+{
+    dst->n_cases = src->n_cases;
+    dst->lanes = src->lanes;
+    dst->n_consts = src->n_consts;
+    dst->div0 = src->div0;
+    dst->max_tree_nodes = src->max_tree_nodes;
+    dst->hbm_budget = src->hbm_budget;
+    dst->hx = src->hx;
+    dst->hy = src->hy;
+    dst->hc = src->hc;
+}
+
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// ================================================================= ABI
+
+extern "C" {
+
+const char *gp_status_string(gp_status st)
+{
+    switch (st) {
+    case GP_OK: return "GP_OK";
+    case GP_EINVAL: return "GP_EINVAL: invalid argument";
+    case GP_ENOMEM: return "GP_ENOMEM: out of memory or over the HBM budget";
+    case GP_EMALFORMED: return "GP_EMALFORMED: malformed tree";
+    case GP_ECUDA: return "GP_ECUDA: CUDA error";
+    case GP_ETIMEOUT: return "GP_ETIMEOUT: device wait timed out";
+    case GP_ELIMIT: return "GP_ELIMIT: tree exceeds the node limit";
+    }
+    return "unknown gp_status";
+}
+
+gp_status gp_create_population(const gp_problem *problem, uint32_t n_trees, const uint8_t *nodes,
+                               const uint64_t *offsets, void *cuda_stream, gp_population **out)
+{
+    if (!out || !problem) return GP_EINVAL;
+    if (n_trees > 0 && (!nodes || !offsets)) return GP_EINVAL;
+    if (n_trees > 0 && offsets[0] != 0) return GP_EINVAL;
+    for (uint32_t t = 0; t < n_trees; ++t)
+        if (offsets[t + 1] <= offsets[t]) return GP_EINVAL;
+    cudaStream_t s = Stream(cuda_stream).s;
+    gp_population *P = new (std::nothrow) gp_population();
+    if (!P) return GP_ENOMEM;
+    gp_status st = copy_problem(P, problem);
+    if (st) { delete P; return st; }
+    cudaGetDevice(&P->device);
+    configure_pool(P->device);
+    P->n_trees = n_trees;
+    P->h_size.resize(n_trees);
+    for (uint32_t t = 0; t < n_trees; ++t) P->h_size[t] = offsets[t + 1] - offsets[t];
+    layout_trees(P);
+    if (P->hbm_budget && population_bytes(P->arena_bytes, n_trees, P->n_cases) > P->hbm_budget) {
+        delete P;
+        return GP_ENOMEM;
+    }
+    st = alloc_population(P, s);
+    if (st) { destroy(P); return st; }
+    if (n_trees > 0) {
+        DevBufs tmp;
+        uint8_t *d_stage = nullptr;
+        const uint64_t packed = offsets[n_trees];
+        std::vector<XoChild> kids(n_trees);
+        auto run = [&]() -> gp_status {
+            CK(tmp.alloc((void **)&d_stage, packed + 64, s));
+            CK(cudaMemcpyAsync(d_stage, nodes, packed, cudaMemcpyHostToDevice, s));
+            for (uint32_t t = 0; t < n_trees; ++t) {
+                XoChild &k = kids[t];
+                k = XoChild{};
+                k.dst = P->h_start[t];
+                k.n = P->h_size[t];
+                k.head_src = offsets[t];
+                k.i = k.n;
+            }
+            gp_status r = run_copy(d_stage, P->d_arena, kids, s, tmp);
+            if (r) return r;
+            bool ok = false;
+            r = validate_population(P, s, tmp, &ok);
+            if (r) return r;
+            return ok ? GP_OK : GP_EMALFORMED;
+        };
+        st = run();
+        tmp.release(s);
+        if (st) { destroy(P); return st; }
+    }
+    *out = P;
+    return GP_OK;
+}
+
+gp_status gp_tree_size(const gp_population *P, uint32_t tree, uint64_t *n)
+{
+    if (!P || !n || tree >= P->n_trees) return GP_EINVAL;
+    *n = P->h_size[tree];
+    return GP_OK;
+}
+
+gp_status gp_tree_read(const gp_population *P, uint32_t tree, uint8_t *dst, uint64_t cap)
+{
+    if (!P || !dst || tree >= P->n_trees || cap < P->h_size[tree]) return GP_EINVAL;
+    DeviceGuard dg(P->device);
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaMemcpy(dst, P->d_arena + P->h_start[tree], P->h_size[tree], cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+gp_status gp_population_get_info(const gp_population *P, gp_population_info *info)
+{
+    if (!P || !info) return GP_EINVAL;
+    info->n_trees = P->n_trees;
+    info->n_cases = P->n_cases;
+    info->total_nodes = P->total_nodes;
+    info->d_nodes = P->d_arena;
+    info->d_tree_start = P->d_start;
+    info->d_tree_size = P->d_size;
+    info->d_fitness = P->d_fitness;
+    info->d_case_values = P->d_values;
+    info->d_hits = P->d_hits;
+    return GP_OK;
+}
+
+void gp_destroy_population(gp_population *P) { destroy(P); }
+
+// ---------------------------------------------------------------- evaluate
+
+gp_status gp_evaluate(gp_population *P, void *cuda_stream) { return gp_evaluate_ex(P, nullptr, cuda_stream); }
+
+gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cuda_stream)
+{
+    if (!P) return GP_EINVAL;
+    DeviceGuard dg(P->device);
+    cudaStream_t s = Stream(cuda_stream).s;
+    P->stream = s;
+    P->stats = gp_eval_stats{};
+    if (P->n_trees == 0) {
+        CK(cudaEventRecord(P->ev, s));
+        P->evaluated = true;
+        return GP_OK;
+    }
+    uint32_t C = opt && opt->chunk_nodes ? opt->chunk_nodes : 4096;
+    uint32_t W = opt && opt->warps_per_cta ? opt->warps_per_cta : 32;
+    uint32_t K = opt && opt->window_entries ? opt->window_entries : 32;
+    if (C % 16 || C < 64 || C > (1u << 24) || W < 1 || W > 32 || K < 16 || K % 2 || K > 1024)
+        return GP_EINVAL;
+    const int lanes = (int)P->lanes;
+    const int sms = sm_count(P->device);
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+    if (!(opt && opt->warps_per_cta))        // as many warps as shared memory holds
+        while (W > 1 && eval_smem_bytes(lanes, (int)W, (int)K) > (size_t)maxsm) --W;
+    // Upper levels (32-bit codes) run at most 16 warps per SM.
+    const uint32_t Wu = std::min<uint32_t>(W, 16);
+    const size_t smem = eval_smem_bytes(lanes, (int)W, (int)K);
+    const size_t smem_u = eval_smem_bytes(lanes, (int)Wu, (int)K);
+    if (smem > (size_t)maxsm) return GP_EINVAL;
+    CK(prepare_eval_once(lanes, false, smem));
+    CK(prepare_eval_once(lanes, true, smem_u));
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
+
+    DevBufs ws;
+    auto body = [&]() -> gp_status {
+        // ---- level 0 items: whole small trees, chunks of large trees
+        std::vector<EvalItem> items;
+        std::vector<uint32_t> big;                  // trees cut into chunks
+        std::vector<uint32_t> first_chunk;          // per big tree: first fragment item
+        for (uint32_t t = 0; t < P->n_trees; ++t) {
+            if (P->h_size[t] <= C) continue;
+            big.push_back(t);
+            first_chunk.push_back((uint32_t)items.size());
+            for (uint64_t b = 0; b < P->h_size[t]; b += C) {
+                EvalItem it{};
+                it.begin = P->h_start[t] + b;
+                it.end = P->h_start[t] + std::min<uint64_t>(P->h_size[t], b + C);
+                it.tree = t;
+                it.spill_off = kNoSpill;
+                items.push_back(it);
+            }
+        }
+        first_chunk.push_back((uint32_t)items.size());
+        const uint32_t n_frag0 = (uint32_t)items.size();
+        {
+            std::vector<uint32_t> small;
+            for (uint32_t t = 0; t < P->n_trees; ++t)
+                if (P->h_size[t] <= C) small.push_back(t);
+            std::stable_sort(small.begin(), small.end(),
+                             [&](uint32_t a, uint32_t b) { return P->h_size[a] > P->h_size[b]; });
+            for (uint32_t t : small) {
+                EvalItem it{};
+                it.begin = P->h_start[t];
+                it.end = P->h_start[t] + P->h_size[t];
+                it.tree = t;
+                it.flags = kItemFinal;
+                it.spill_off = kNoSpill;
+                items.push_back(it);
+            }
+        }
+
+        const uint64_t warps_total = (uint64_t)sms * W;   // >= warps of any level
+        const uint64_t spill_per_warp = C;               // an item of <= C codes never holds more
+        uint32_t *d_counter;
+        CK(ws.alloc((void **)&d_counter, sizeof(uint32_t) * 64, s));
+        CK(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t) * 64, s));
+
+        // level state
+        const void *codes = P->d_arena;
+        bool wide = false;
+        const float2 *pt_in = nullptr;
+        std::vector<uint64_t> prev_len(big.size());
+        for (size_t k = 0; k < big.size(); ++k) prev_len[k] = P->h_size[big[k]];
+        std::vector<EvalItem> cur_items = std::move(items);
+        uint32_t n_frag = n_frag0;
+        std::vector<uint32_t> cur_big = big;
+        std::vector<uint32_t> cur_first = first_chunk;
+        uint32_t level = 0;
+
+        for (;;) {
+            if (level >= 63) return GP_EINVAL;
+            EvalItem *d_items;
+            CK(ws.alloc((void **)&d_items, sizeof(EvalItem) * cur_items.size(), s));
+            CK(cudaMemcpyAsync(d_items, cur_items.data(), sizeof(EvalItem) * cur_items.size(),
+                               cudaMemcpyHostToDevice, s));
+            uint32_t *u_next = nullptr;
+            float2 *pt_next = nullptr;
+            std::vector<uint64_t> frag_off;
+            if (n_frag) {
+                PlanOut *d_plan;
+                uint64_t *d_fo, *d_tot;
+                CK(ws.alloc((void **)&d_plan, sizeof(PlanOut) * n_frag, s));
+                CK(ws.alloc((void **)&d_fo, sizeof(uint64_t) * (n_frag + 1), s));
+                CK(ws.alloc((void **)&d_tot, sizeof(uint64_t) * 4, s));
+                {
+                    ProfScope ps(GP_KERNEL_PLAN, s);
+                    CK(launch_plan(wide, codes, d_items, n_frag, d_plan, s));
+                }
+                {
+                    ProfScope ps(GP_KERNEL_SCAN, s);
+                    CK(launch_plan_scan(d_items, d_plan, n_frag, d_fo, d_tot, s));
+                }
+                frag_off.resize(n_frag + 1);
+                uint64_t tot[4] = {};
+                CK(cudaMemcpyAsync(frag_off.data(), d_fo, sizeof(uint64_t) * (n_frag + 1),
+                                   cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(tot, d_tot, sizeof(uint64_t) * 3, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (tot[1] + kPtCode0 >= 0xffffffffull) return GP_ENOMEM;
+                if (tot[2] > spill_per_warp) return GP_EINVAL;   // cannot happen: chunks <= C
+                CK(ws.alloc((void **)&u_next, sizeof(uint32_t) * (round_up(tot[0], 16) + 32), s));
+                CK(ws.alloc((void **)&pt_next, sizeof(float2) * (tot[1] * lanes + 1), s));
+                P->stats.upper_codes += tot[0];
+                P->stats.value_entries += tot[1];
+            }
+            // dedicated spill areas for oversized final items
+            uint64_t dedicated = 0;
+            for (auto &it : cur_items) {
+                if ((it.flags & kItemFinal) && it.end - it.begin > spill_per_warp) {
+                    it.spill_off = warps_total * spill_per_warp + dedicated;
+                    it.spill_cap = it.end - it.begin;
+                    dedicated += it.spill_cap;
+                }
+            }
+            if (dedicated) {
+                // re-upload the items with their spill areas (fragment fields
+                // written by the scan are kept: only finals changed)
+                for (uint32_t i = n_frag; i < cur_items.size(); ++i)
+                    CK(cudaMemcpyAsync(d_items + i, &cur_items[i], sizeof(EvalItem),
+                                       cudaMemcpyHostToDevice, s));
+            }
+            float2 *d_spill;
+            CK(ws.alloc((void **)&d_spill,
+                        sizeof(float2) * lanes * (warps_total * spill_per_warp + dedicated), s));
+
+            EvalParams p{};
+            p.codes = codes;
+            p.items = d_items;
+            p.n_items = (uint32_t)cur_items.size();
+            p.counter = d_counter + level;
+            p.x = P->d_x;
+            p.y = P->d_y;
+            p.consts = P->d_c;
+            p.n_cases = P->n_cases;
+            p.n_consts = P->n_consts;
+            p.div0 = P->div0;
+            p.window = K;
+            p.pt_in = pt_in;
+            p.pt_out = pt_next;
+            p.u_out = u_next;
+            p.values = P->d_values;
+            p.fitness = P->d_fitness;
+            p.hits = P->d_hits;
+            p.spill = d_spill;
+            p.spill_per_warp = spill_per_warp;
+            p.err = P->d_err;
+            {
+                ProfScope ps(wide ? GP_KERNEL_EVAL_UPPER : GP_KERNEL_EVAL, s);
+                CK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s));
+            }
+            P->stats.levels = level + 1;
+            P->stats.items += cur_items.size();
+            if (!n_frag) break;
+
+            // ---- next level: one upper tree per big tree
+            std::vector<EvalItem> next;
+            std::vector<uint32_t> nb, nf;
+            std::vector<uint64_t> nprev;
+            std::vector<EvalItem> finals;
+            for (size_t k = 0; k < cur_big.size(); ++k) {
+                const uint32_t t = cur_big[k];
+                const uint64_t ub = frag_off[cur_first[k]], ue = frag_off[cur_first[k + 1]];
+                const uint64_t len = ue - ub;
+                if (len <= C || len * 2 > prev_len[k]) {
+                    EvalItem it{};
+                    it.begin = ub;
+                    it.end = ue;
+                    it.tree = t;
+                    it.flags = kItemFinal;
+                    it.spill_off = kNoSpill;
+                    finals.push_back(it);
+                } else {
+                    nb.push_back(t);
+                    nf.push_back((uint32_t)next.size());
+                    nprev.push_back(len);
+                    for (uint64_t b = ub; b < ue; b += C) {
+                        EvalItem it{};
+                        it.begin = b;
+                        it.end = std::min<uint64_t>(ue, b + C);
+                        it.tree = t;
+                        it.spill_off = kNoSpill;
+                        next.push_back(it);
+                    }
+                }
+            }
+            nf.push_back((uint32_t)next.size());
+            n_frag = (uint32_t)next.size();
+            std::stable_sort(finals.begin(), finals.end(), [](const EvalItem &a, const EvalItem &b) {
+                return a.end - a.begin > b.end - b.begin;
+            });
+            next.insert(next.end(), finals.begin(), finals.end());
+            cur_items = std::move(next);
+            cur_big = std::move(nb);
+            cur_first = std::move(nf);
+            prev_len = std::move(nprev);
+            codes = u_next;
+            wide = true;
+            pt_in = pt_next;
+            ++level;
+        }
+        return GP_OK;
+    };
+    gp_status st = body();
+    ws.release(s);
+    if (st) return st;
+    CK(cudaEventRecord(P->ev, s));
+    P->evaluated = true;
+    return GP_OK;
+}
+
+gp_status gp_fitness(const gp_population *P, float *fitness, float *case_values, uint32_t *hits)
+{
+    if (!P || (!fitness && P->n_trees)) return GP_EINVAL;
+    if (!P->evaluated) return GP_EINVAL;
+    DeviceGuard dg(P->device);
+    CK(cudaEventSynchronize(P->ev));
+    uint32_t err = 0;
+    CK(cudaMemcpy(&err, P->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (err & kErrMalformed) return GP_EMALFORMED;
+    if (err) return GP_ECUDA;
+    if (P->n_trees == 0) return GP_OK;
+    CK(cudaMemcpy(fitness, P->d_fitness, sizeof(float) * P->n_trees, cudaMemcpyDeviceToHost));
+    if (case_values)
+        CK(cudaMemcpy(case_values, P->d_values, sizeof(float) * (uint64_t)P->n_trees * P->n_cases,
+                      cudaMemcpyDeviceToHost));
+    if (hits) CK(cudaMemcpy(hits, P->d_hits, sizeof(uint32_t) * P->n_trees, cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+gp_status gp_eval_stats_get(const gp_population *P, gp_eval_stats *out)
+{
+    if (!P || !out) return GP_EINVAL;
+    *out = P->stats;
+    return GP_OK;
+}
+
+// ---------------------------------------------------------------- crossover
+
+gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops, void *cuda_stream,
+                       gp_population **children_out)
+{
+    if (!M || !children_out || (n_ops && !ops)) return GP_EINVAL;
+    for (uint32_t k = 0; k < n_ops; ++k) {
+        const gp_xo &o = ops[k];
+        if (o.mum >= M->n_trees || o.dad >= M->n_trees) return GP_EINVAL;
+        if (o.mum_point >= M->h_size[o.mum] || o.dad_point >= M->h_size[o.dad]) return GP_EINVAL;
+    }
+    DeviceGuard dg(M->device);
+    cudaStream_t s = Stream(cuda_stream).s;
+    gp_population *C = new (std::nothrow) gp_population();
+    if (!C) return GP_ENOMEM;
+    copy_problem_from(C, M);
+    C->device = M->device;
+    C->n_trees = n_ops;
+    C->h_size.resize(n_ops);
+    DevBufs tmp;
+    std::vector<uint64_t> ends(2 * (size_t)n_ops);
+    auto run = [&]() -> gp_status {
+        if (n_ops) {
+            std::vector<ExtentQuery> q(2 * (size_t)n_ops);
+            for (uint32_t k = 0; k < n_ops; ++k) {
+                q[2 * k] = ExtentQuery{M->h_start[ops[k].mum], M->h_size[ops[k].mum], ops[k].mum_point};
+                q[2 * k + 1] = ExtentQuery{M->h_start[ops[k].dad], M->h_size[ops[k].dad], ops[k].dad_point};
+            }
+            ExtentQuery *d_q;
+            uint64_t *d_end;
+            uint32_t *d_err;
+            CK(tmp.alloc((void **)&d_q, sizeof(ExtentQuery) * q.size(), s));
+            CK(tmp.alloc((void **)&d_end, sizeof(uint64_t) * q.size(), s));
+            CK(tmp.alloc((void **)&d_err, sizeof(uint32_t), s));
+            CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
+            CK(cudaMemcpyAsync(d_q, q.data(), sizeof(ExtentQuery) * q.size(), cudaMemcpyHostToDevice, s));
+            {
+                ProfScope ps(GP_KERNEL_EXTENT, s);
+                CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_err, s));
+            }
+            uint32_t err = 0;
+            CK(cudaMemcpyAsync(ends.data(), d_end, sizeof(uint64_t) * q.size(), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (err) return GP_EMALFORMED;
+        }
+        for (uint32_t k = 0; k < n_ops; ++k) {
+            const uint64_t i = ops[k].mum_point, j = ops[k].dad_point;
+            const uint64_t em = ends[2 * k], ed = ends[2 * k + 1];
+            C->h_size[k] = i + (ed - j) + (M->h_size[ops[k].mum] - em);
+            if (C->max_tree_nodes && C->h_size[k] > C->max_tree_nodes) return GP_ELIMIT;
+        }
+        layout_trees(C);
+        if (C->hbm_budget && population_bytes(C->arena_bytes, n_ops, C->n_cases) > C->hbm_budget)
+            return GP_ENOMEM;
+        gp_status r = alloc_population(C, s);
+        if (r) return r;
+        std::vector<XoChild> kids(n_ops);
+        for (uint32_t k = 0; k < n_ops; ++k) {
+            const uint64_t i = ops[k].mum_point, j = ops[k].dad_point;
+            const uint64_t em = ends[2 * k], ed = ends[2 * k + 1];
+            const uint64_t ms = M->h_start[ops[k].mum], ds = M->h_start[ops[k].dad];
+            XoChild &c = kids[k];
+            c = XoChild{};
+            c.dst = C->h_start[k];
+            c.n = C->h_size[k];
+            c.head_src = ms;
+            c.i = i;
+            c.mid_src = ds + j;
+            c.ld = ed - j;
+            c.tail_src = ms + em;                // tail byte p comes from mum[em + p - i - ld]
+        }
+        return run_copy(M->d_arena, C->d_arena, kids, s, tmp);
+    };
+    gp_status st = run();
+    tmp.release(s);
+    if (st) { destroy(C); return st; }
+    *children_out = C;
+    return GP_OK;
+}
+
+// ---------------------------------------------------------------- profiling ABI
+
+uint64_t gp_kernel_launch_count(void) { return g_launches.load(); }
+
+gp_status gp_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return GP_OK;
+}
+
+gp_status gp_profile_read(gp_kernel_profile *out, int reset)
+{
+    if (!out) return GP_EINVAL;
+    std::vector<ProfRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        recs.swap(g_prof_pending);
+    }
+    for (auto &r : recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(g_prof_mu);
+            g_prof_ms[r.kind] += ms;
+            g_prof_n[r.kind] += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int k = 0; k < GP_KERNEL_KINDS; ++k) {
+        out->launches[k] = g_prof_n[k];
+        out->total_ms[k] = g_prof_ms[k];
+        if (reset) { g_prof_n[k] = 0; g_prof_ms[k] = 0.0; }
+    }
+    return GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,720 @@
+// Fitness evaluation kernels for linear prefix GP trees (sm_103a).
+//
+// The paper (Sec. 2.2) evaluates a tree in a single pass over its prefix
+// byte buffer, every opcode acting on all 48 fitness cases at once through
+// an external stack of 48-float frames; the reduction to fitness is a plain
+// loop in case order.  Here:
+//   - one warp interprets one item; lane l holds fitness cases 2l and 2l+1 as
+//     a float2, so each '+', '-', '*' is one packed f32x2 instruction for
+//     all cases, and every opcode decision is warp-uniform;
+//   - the tree is read right to left (reversed prefix order is a postfix
+//     program): a leaf pushes, an operator pops its second argument and
+//     combines it with the top of stack, which holds its first argument.
+//     Every node is still one IEEE operation on its children's values, so
+//     the per-case results are bit-identical to the recursive EVAL;
+//   - the top of stack lives in registers, the next entries in a per-warp
+//     shared-memory window, and deeper entries spill to global memory;
+//   - a tree longer than one chunk is cut into chunks evaluated
+//     independently: each chunk evaluates its complete subtrees and emits an
+//     "upper tree" fragment in which those subtrees are value-buffer leaves
+//     and the operators whose arguments reach past the chunk stay operators.
+//     The upper tree is evaluated by the next launch (recursively if large).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gp_internal.cuh"
+
+namespace gpk {
+
+// ---------------------------------------------------------------- arithmetic
+
+__device__ __forceinline__ unsigned long long f2u(float2 a) {
+    return *reinterpret_cast<unsigned long long *>(&a);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long u) {
+    return *reinterpret_cast<float2 *>(&u);
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(r);
+}
+// Protected division (Table gp.details): a / b, or the problem's value
+// (1.0f in the paper) when b == 0.  IEEE round-to-nearest division.
+__device__ __forceinline__ float pdiv(float a, float b, float d0) {
+    return (b != 0.0f) ? __fdiv_rn(a, b) : d0;
+}
+__device__ __forceinline__ float2 apply_op(uint32_t c, float2 a, float2 b, float d0) {
+    if (c == 0) return f2_add(a, b);
+    if (c == 1) return f2_sub(a, b);
+    if (c == 2) return f2_mul(a, b);
+    return make_float2(pdiv(a.x, b.x, d0), pdiv(a.y, b.y, d0));
+}
+
+// ---------------------------------------------------------------- code groups
+
+// 16 consecutive codes, 16-code aligned, loaded with 128-bit loads.  Every
+// lane loads the same address, so one request serves the warp.  The group is
+// walked as four sub-words of four codes each (sub(q), code(sub, k)), so the
+// interpreter body is unrolled only four times: the loop stays small enough
+// for the instruction cache despite data-dependent branching.
+template <typename Code> struct Group;
+
+template <> struct Group<uint8_t> {
+    typedef uint32_t Sub;
+    uint4 w;
+    __device__ __forceinline__ void load(const uint8_t *p) {
+        w = __ldg(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ Sub sub(int q) const {
+        return q == 3 ? w.w : q == 2 ? w.z : q == 1 ? w.y : w.x;
+    }
+    __device__ __forceinline__ static uint32_t code(Sub v, int k) { return (v >> (8 * k)) & 0xFFu; }
+    // All lanes hold the same word; an OR-reduction over the warp returns it
+    // as a value the compiler knows to be uniform.
+    __device__ __forceinline__ static Sub uniform(Sub v, uint32_t mask) { return __reduce_or_sync(mask, v); }
+    __device__ __forceinline__ uint32_t first() const { return w.x & 0xFFu; }
+    __device__ __forceinline__ void prefetch_values(const float2 *, int, int) const {}
+};
+
+template <> struct Group<uint32_t> {
+    typedef uint4 Sub;
+    uint4 w[4];
+    __device__ __forceinline__ void load(const uint32_t *p) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+        w[0] = __ldg(q); w[1] = __ldg(q + 1); w[2] = __ldg(q + 2); w[3] = __ldg(q + 3);
+    }
+    __device__ __forceinline__ Sub sub(int q) const {
+        return q == 3 ? w[3] : q == 2 ? w[2] : q == 1 ? w[1] : w[0];
+    }
+    __device__ __forceinline__ static uint32_t code(Sub v, int k) {
+        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+    }
+    __device__ __forceinline__ static Sub uniform(Sub v, uint32_t mask) {
+        return make_uint4(__reduce_or_sync(mask, v.x), __reduce_or_sync(mask, v.y),
+                          __reduce_or_sync(mask, v.z), __reduce_or_sync(mask, v.w));
+    }
+    __device__ __forceinline__ uint32_t first() const { return w[0].x; }
+    // Pull this group's value-buffer leaves into L1 ahead of their use.
+    __device__ __forceinline__ void prefetch_values(const float2 *pt, int lanes, int lane) const {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t c[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c[k] >= kPtCode0)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(pt + (uint64_t)(c[k] - kPtCode0) * lanes + lane));
+        }
+    }
+};
+
+// ---------------------------------------------------------------- one item
+
+// Dynamic shared memory: the leaf table at offset 0, then one stack window
+// per warp, then per-warp scratch for the fitness fold.  Stack and table
+// accesses use 32-bit byte offsets into this array.
+extern __shared__ __align__(16) unsigned char smem[];
+
+__device__ __forceinline__ float2 &sm2(uint32_t off) {
+    return *reinterpret_cast<float2 *>(smem + off);
+}
+
+// Stack entries are handled as packed float2 in a 64-bit register and moved
+// with volatile shared-memory accesses at absolute 32-bit shared addresses,
+// so they stay ordered with respect to the inline-PTX interpreter below.
+__device__ __forceinline__ uint64_t pk(float2 v) { return f2u(v); }
+__device__ __forceinline__ float2 upk(uint64_t v) { return u2f(v); }
+__device__ __forceinline__ void sts64(uint32_t a, uint64_t v) {
+    asm volatile("st.shared.b64 [%0], %1;" ::"r"(a), "l"(v));
+}
+__device__ __forceinline__ uint64_t lds64(uint32_t a) {
+    uint64_t v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+    return v;
+}
+
+// Four one-byte codes of `w`, read from the high byte down (right to left in
+// the tree), on a stack whose top value is `tos` and whose next free window
+// entry is at shared address `t` (entries S bytes apart, this lane's column).
+// The caller guarantees at least four entries below `t` and room for four
+// more.  Codes are warp-uniform, so every branch is marked .uni.
+//   leaf c >= 4 : push tos; tos = table[c] (shared address tb + c*S)
+//   op   c < 4  : tos = tos (op) pop   -- tos holds the operator's first
+//                 argument, the popped entry its second
+//   '/' is protected: a zero divisor gives d0.
+#define GP_NODE_PTX(BIT)                                                        \
+    "{\n\t.reg .pred pl, p;\n\t.reg .b32 c, a;\n\t.reg .b64 v;\n\t"            \
+    ".reg .f32 tx, ty, bx, by, qx, qy;\n\t"                                    \
+    "bfe.u32 c, %2, " #BIT ", 8;\n\t"                                         \
+    "setp.gt.u32 pl, c, 3;\n\t"                                               \
+    "@pl bra.uni LEAF;\n\t"                                                   \
+    "sub.u32 %1, %1, %5;\n\t"                                                 \
+    "ld.shared.b64 v, [%1];\n\t"                                              \
+    "setp.eq.u32 p, c, 2;\n\t@p bra.uni MUL;\n\t"                             \
+    "setp.eq.u32 p, c, 0;\n\t@p bra.uni ADD;\n\t"                             \
+    "setp.eq.u32 p, c, 1;\n\t@p bra.uni SUB;\n\t"                             \
+    "mov.b64 {tx, ty}, %0;\n\tmov.b64 {bx, by}, v;\n\t"                       \
+    "div.rn.f32 qx, tx, bx;\n\tsetp.neu.f32 p, bx, 0f00000000;\n\t"           \
+    "selp.f32 tx, qx, %4, p;\n\t"                                             \
+    "div.rn.f32 qy, ty, by;\n\tsetp.neu.f32 p, by, 0f00000000;\n\t"           \
+    "selp.f32 ty, qy, %4, p;\n\t"                                             \
+    "mov.b64 %0, {tx, ty};\n\tbra.uni END;\n"                                  \
+    "ADD:\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni END;\n"                        \
+    "SUB:\n\tsub.rn.f32x2 %0, %0, v;\n\tbra.uni END;\n"                        \
+    "MUL:\n\tmul.rn.f32x2 %0, %0, v;\n\tbra.uni END;\n"                        \
+    "LEAF:\n\tst.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %5;\n\t"              \
+    "mad.lo.u32 a, c, %5, %3;\n\tld.shared.b64 %0, [a];\n"                     \
+    "END:\n\t}\n\t"
+
+template <uint32_t S>
+__device__ __forceinline__ void fast4_u8(uint64_t &tos, uint32_t &t, uint32_t w, uint32_t tb, float d0) {
+    asm volatile(GP_NODE_PTX(24) GP_NODE_PTX(16) GP_NODE_PTX(8) GP_NODE_PTX(0)
+                 : "+l"(tos), "+r"(t)
+                 : "r"(w), "r"(tb), "f"(d0), "n"(S));
+}
+
+template <int LANES, typename Code, bool WIDE>
+__device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &it, uint32_t win_sa,
+                                          uint32_t tbl_sa, float *errs, float2 *__restrict__ spill,
+                                          uint64_t spill_cap, int lane, uint32_t mask, float y0, float y1)
+{
+    constexpr uint32_t S = LANES * sizeof(float2);          // bytes per stack entry / table row
+    const Code *codes = static_cast<const Code *>(P.codes);
+    const int K = (int)P.window;
+    const float d0 = P.div0;
+    const bool is_final = (it.flags & kItemFinal) != 0;
+    const uint32_t tb = tbl_sa + lane * 8u - 4u * S;        // + code * S = leaf table row
+    const uint32_t wb = win_sa + lane * 8u;                 // this lane's column of the window
+
+    uint64_t tos = 0;                     // top of stack (first argument of the next operator)
+    bool have = false;                    // tos holds a value of this item
+    uint32_t t = wb;                      // next free window entry (shared address)
+    uint64_t g = 0;                       // entries spilled below the window
+    uint64_t ecur = it.frag_off + it.frag_len;   // fragment codes are written backwards
+    uint64_t ptn = it.pt_base;
+    uint32_t prev = 0xFFFFFFFFu;          // code at the position right of the current one
+    uint32_t fault = 0;                   // kErr* bits; any fault ends the item
+    const uint32_t dmax = (uint32_t)(K - 4) * S;   // room for four pushes below this
+
+    auto leafval = [&](uint32_t c) -> uint64_t {
+        if (WIDE && c >= kPtCode0)
+            return pk(P.pt_in[(uint64_t)(c - kPtCode0) * LANES + lane]);
+        return lds64(tb + c * S);
+    };
+    // Fragment output stays inside the slot the plan reserved for it.
+    auto emit = [&](uint32_t code) {
+        if (ecur == it.frag_off) { fault |= kErrPlan; return; }
+        --ecur;
+        if (lane == 0) P.u_out[ecur] = code;
+    };
+    auto new_pt = [&](uint64_t v) -> uint32_t {
+        if (ptn >= it.pt_base + it.pt_cnt) { fault |= kErrPlan; return kPtCode0; }
+        P.pt_out[ptn * LANES + lane] = upk(v);
+        return (uint32_t)(kPtCode0 + ptn++);
+    };
+    // Keep room for four pushes in the window, and four pops whenever
+    // entries are spilled; the window is refilled / spilled half-way.
+    auto rebalance = [&]() {
+        const uint32_t d = t - wb;
+        if (d > dmax) {
+            const int sp = (int)(d / S);
+            const int h = sp - K / 2;
+            if (g + (uint64_t)h > spill_cap) {
+                fault |= kErrSpill;
+                return;
+            }
+            for (int i = 0; i < h; ++i) spill[(g + i) * LANES + lane] = upk(lds64(wb + i * S));
+            for (int i = h; i < sp; ++i) sts64(wb + (i - h) * S, lds64(wb + i * S));
+            g += h;
+            t -= h * S;
+        } else if (d < 4 * S && g > 0) {
+            const int sp = (int)(d / S);
+            const int h = (int)umin64(g, (uint64_t)(K / 2 - sp));
+            for (int i = sp - 1; i >= 0; --i) sts64(wb + (i + h) * S, lds64(wb + i * S));
+            for (int i = 0; i < h; ++i) sts64(wb + i * S, pk(spill[(g - h + i) * LANES + lane]));
+            g -= h;
+            t += h * S;
+        }
+    };
+    // Unchecked step for upper-tree codes (the byte-code path uses fast4_u8).
+    auto step_fast = [&](uint32_t c) {
+        switch (c) {
+        case 0: t -= S; tos = pk(f2_add(upk(tos), upk(lds64(t)))); break;
+        case 1: t -= S; tos = pk(f2_sub(upk(tos), upk(lds64(t)))); break;
+        case 2: t -= S; tos = pk(f2_mul(upk(tos), upk(lds64(t)))); break;
+        case 3: {
+            t -= S;
+            const float2 a = upk(tos), b = upk(lds64(t));
+            tos = pk(make_float2(pdiv(a.x, b.x, d0), pdiv(a.y, b.y, d0)));
+            break;
+        }
+        default:
+            sts64(t, tos);
+            t += S;
+            tos = leafval(c);
+            break;
+        }
+    };
+    // Checked step (nothing spilled, fewer than five values known): detects
+    // operators whose arguments lie beyond the item.
+    auto step_checked = [&](uint32_t c) {
+        if (c >= 4) {
+            const uint64_t v = leafval(c);
+            if (have) {
+                sts64(t, tos);
+                t += S;
+            }
+            tos = v;
+            have = true;
+        } else if (t != wb) {             // a window entry implies have
+            t -= S;
+            tos = pk(apply_op(c, upk(tos), upk(lds64(t)), d0));
+        } else if (is_final) {
+            fault |= kErrMalformed;       // stack underflow: not a valid tree
+        } else {
+            // Spine operator: its second argument (and maybe its first) lies
+            // to the right of this chunk.  Emit it into the upper tree; a
+            // first argument that is an x/constant leaf passes through, any
+            // other first argument becomes an entry of this level's value
+            // buffer (entries of the previous level's buffer are not visible
+            // to the next level, so they are copied too).
+            if (have) emit((prev >= 4 && prev < kPtCode0) ? prev : new_pt(tos));
+            emit(c);
+            have = false;
+        }
+        prev = c;
+    };
+
+    const uint64_t b = it.begin, e = it.end;
+    const uint32_t fast_span = (uint32_t)(K - 8) * S;   // fast iff 4S <= depth <= (K-4)S
+    if (e > b) {
+        int64_t gs = (int64_t)((e - 1) & ~15ull);
+        const int64_t glo = (int64_t)(b & ~15ull);
+        Group<Code> cur;
+        cur.load(codes + gs);
+        for (; gs >= glo; gs -= 16) {
+            Group<Code> nxt;
+            if (gs - 16 >= glo) nxt.load(codes + gs - 16);
+            const bool full = (uint64_t)gs >= b && (uint64_t)gs + 16 <= e;
+#pragma unroll 1
+            for (int q = 3; q >= 0; --q) {
+                typename Group<Code>::Sub v = cur.sub(q);
+                if (WIDE) v = Group<Code>::uniform(v, mask);
+                bool fast = full && (t - wb - 4 * S) <= fast_span;
+                if (!fast) {
+                    rebalance();
+                    if (fault) break;
+                    fast = full && (t - wb - 4 * S) <= fast_span;
+                }
+                if (fast) {
+                    if constexpr (WIDE) {
+#pragma unroll
+                        for (int k = 3; k >= 0; --k) step_fast(Group<Code>::code(v, k));
+                    } else {
+                        fast4_u8<S>(tos, t, v, tb, d0);
+                    }
+                    prev = Group<Code>::code(v, 0);
+                } else if (full) {
+#pragma unroll
+                    for (int k = 3; k >= 0; --k) step_checked(Group<Code>::code(v, k));
+                } else {
+#pragma unroll
+                    for (int k = 3; k >= 0; --k) {
+                        const uint64_t pos = (uint64_t)gs + 4 * q + k;
+                        if (pos >= b && pos < e) step_checked(Group<Code>::code(v, k));
+                    }
+                }
+                if (fault) break;
+            }
+            if (fault) break;
+            if (gs - 16 >= glo) nxt.prefetch_values(P.pt_in, LANES, lane);
+            cur = nxt;
+        }
+    } else if (is_final) {
+        fault |= kErrMalformed;
+    }
+    const int sp = (int)((t - wb) / S);
+
+    if (is_final) {
+        const uint32_t tr = it.tree;
+        const uint32_t nc = P.n_cases;
+        const bool ok = !fault && have && sp == 0 && g == 0;
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(P.err, fault ? fault : kErrMalformed);
+                P.fitness[tr] = __int_as_float(0x7fffffff);
+                P.hits[tr] = 0;
+            }
+            return;
+        }
+        const float2 o = upk(tos);
+        const uint32_t i0 = 2 * lane, i1 = i0 + 1;
+        if (i0 < nc) P.values[(uint64_t)tr * nc + i0] = o.x;
+        if (i1 < nc) P.values[(uint64_t)tr * nc + i1] = o.y;
+        const float e0 = fabsf(o.x - y0), e1 = fabsf(o.y - y1);
+        errs[i0] = e0;
+        errs[i1] = e1;
+        const unsigned h0 = __ballot_sync(mask, i0 < nc && e0 < 0.01f);
+        const unsigned h1 = __ballot_sync(mask, i1 < nc && e1 < 0.01f);
+        __syncwarp(mask);
+        if (lane == 0) {
+            // Sec. 2.2 / 3.2: fixed-order reduction, a plain loop over cases.
+            float acc = 0.0f;
+            for (uint32_t i = 0; i < nc; ++i) acc = acc + errs[i];
+            P.fitness[tr] = __fdiv_rn(acc, (float)nc);
+            P.hits[tr] = __popc(h0) + __popc(h1);
+        }
+        __syncwarp(mask);
+        return;
+    }
+
+    if (fault) {
+        if (lane == 0) atomicOr(P.err, fault);
+        return;
+    }
+    // Values left on the stack are the complete subtrees at the chunk's left
+    // end; the bottom one is the rightmost, so it is emitted first.
+    for (uint64_t i = 0; i < g; ++i) emit(new_pt(pk(spill[i * LANES + lane])));
+    for (int i = 0; i < sp; ++i) emit(new_pt(lds64(wb + i * S)));
+    if (have) emit(new_pt(tos));
+    if (fault || ecur != it.frag_off || ptn != it.pt_base + it.pt_cnt) {
+        if (lane == 0) atomicOr(P.err, kErrPlan);
+    }
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int LANES, typename Code, bool WIDE>
+__global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P)
+{
+    const int nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr uint32_t S = LANES * sizeof(float2);
+    const uint32_t win0 = kLeafRows * S;                    // first window (bytes)
+
+    // Leaf table: row 0 is x (per lane, two cases), row r >= 1 constant r-1.
+    for (int i = threadIdx.x; i < (int)(kLeafRows * LANES); i += blockDim.x) {
+        const int row = i / LANES, l = i - row * LANES;
+        float2 v;
+        if (row == 0) v = make_float2(P.x[2 * l], P.x[2 * l + 1]);
+        else if ((uint32_t)(row - 1) < P.n_consts) v = make_float2(P.consts[row - 1], P.consts[row - 1]);
+        else v = make_float2(0.f, 0.f);
+        sm2(row * S + l * 8) = v;
+    }
+    __syncthreads();
+    if (lane >= LANES) return;
+
+    const uint32_t mask = (LANES == 32) ? 0xffffffffu : ((1u << LANES) - 1u);
+    const uint32_t win_off = win0 + (uint32_t)warp * P.window * S;
+    // The fitness fold's scratch reuses the window, which is empty by then.
+    float *errs = reinterpret_cast<float *>(smem + win_off);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const float y0 = P.y[2 * lane], y1 = P.y[2 * lane + 1];
+    const uint64_t gw = (uint64_t)blockIdx.x * nwarps + warp;
+    float2 *myspill = P.spill + gw * P.spill_per_warp * LANES;
+
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(P.counter, 1u);
+        idx = __shfl_sync(mask, idx, 0);
+        if (idx >= P.n_items) break;
+        const EvalItem it = P.items[idx];
+        float2 *area = myspill;
+        uint64_t cap = P.spill_per_warp;
+        if (it.spill_off != kNoSpill) {
+            area = P.spill + it.spill_off * LANES;
+            cap = it.spill_cap;
+        }
+        eval_item<LANES, Code, WIDE>(P, it, sbase + win_off, sbase, errs, area, cap, lane, mask, y0, y1);
+    }
+}
+
+size_t eval_smem_bytes(int lanes, int warps, int window)
+{
+    return (size_t)kLeafRows * lanes * sizeof(float2) + (size_t)warps * window * lanes * sizeof(float2);
+}
+
+template <int LANES>
+static void *eval_fn(bool wide)
+{
+    return wide ? (void *)eval_kernel<LANES, uint32_t, true>
+                : (void *)eval_kernel<LANES, uint8_t, false>;
+}
+
+static void *eval_fn_for(int lanes, bool wide)
+{
+    switch (lanes) {
+    case 8: return eval_fn<8>(wide);
+    case 16: return eval_fn<16>(wide);
+    case 24: return eval_fn<24>(wide);
+    case 32: return eval_fn<32>(wide);
+    default: return nullptr;
+    }
+}
+
+cudaError_t eval_prepare(int lanes, bool wide, size_t smem)
+{
+    void *fn = eval_fn_for(lanes, wide);
+    if (!fn) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
+                        size_t smem, cudaStream_t s)
+{
+    void *fn = eval_fn_for(lanes, wide);
+    if (!fn) return cudaErrorInvalidValue;
+    EvalParams pp = p;
+    void *args[] = {&pp};
+    return cudaLaunchKernel(fn, dim3(ctas), dim3(warps * 32), args, smem, s);
+}
+
+// ---------------------------------------------------------------- planning
+
+// Stack-size transfer function of a run of codes read right to left:
+// k -> max(k + d, c).  A leaf maps k -> k+1; an operator maps k -> k-1 when
+// both arguments are on the stack and otherwise (a spine operator) leaves no
+// known value, k -> max(k-1, 0).  The family is closed under composition.
+struct Xfer {
+    int64_t d, c;
+};
+__device__ __forceinline__ Xfer xfer_after(Xfer first, Xfer then) {
+    return Xfer{first.d + then.d, max(first.c + then.d, then.c)};
+}
+constexpr int64_t kNegInf = -(int64_t(1) << 60);
+
+// One warp per fragment item: counts the codes and value-buffer entries the
+// chunk will emit, replaying exactly the evaluator's spine rule.
+template <typename Code>
+__global__ void plan_kernel(const Code *__restrict__ codes, const EvalItem *__restrict__ items,
+                            uint32_t n, PlanOut *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    const EvalItem it = items[w];
+    const uint64_t len = it.end - it.begin;
+    const uint64_t seg = (len + 31) / 32;
+    const uint64_t lo = umin64(it.begin + lane * seg, it.end);
+    const uint64_t hi = umin64(lo + seg, it.end);
+
+    Xfer f{0, kNegInf};
+    for (uint64_t p = hi; p > lo; --p) {
+        const uint32_t c = codes[p - 1];
+        if (c >= 4) f = Xfer{f.d + 1, f.c + 1};
+        else f = Xfer{f.d - 1, max(f.c - 1, (int64_t)0)};
+    }
+    // suffix composition: G_lane = F_lane after F_{lane+1} after ... F_31
+    Xfer G = f;
+    for (int off = 1; off < 32; off <<= 1) {
+        Xfer o;
+        o.d = __shfl_down_sync(0xffffffffu, G.d, off);
+        o.c = __shfl_down_sync(0xffffffffu, G.c, off);
+        if (lane + off < 32) G = xfer_after(o, G);
+    }
+    Xfer R;
+    R.d = __shfl_down_sync(0xffffffffu, G.d, 1);
+    R.c = __shfl_down_sync(0xffffffffu, G.c, 1);
+    int64_t kn = (lane == 31) ? 0 : max(R.d, R.c);
+
+    uint32_t spine = 0, spine1 = 0, spine1_pt = 0;
+    int64_t mx = kn;
+    uint32_t prev = (hi < it.end) ? (uint32_t)codes[hi] : 0xFFFFFFFFu;
+    for (uint64_t p = hi; p > lo; --p) {
+        const uint32_t c = codes[p - 1];
+        if (c >= 4) {
+            ++kn;
+            mx = max(mx, kn);
+        } else if (kn >= 2) {
+            --kn;
+        } else {
+            ++spine;
+            if (kn == 1) {
+                ++spine1;
+                if (prev < 4 || prev >= kPtCode0) ++spine1_pt;
+            }
+            kn = 0;
+        }
+        prev = c;
+    }
+    const int64_t kn_final = __shfl_sync(0xffffffffu, kn, 0);
+    uint32_t a = spine + spine1, bcount = spine1_pt;
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        bcount += __shfl_down_sync(0xffffffffu, bcount, off);
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    }
+    if (lane == 0) {
+        PlanOut o;
+        o.frag_len = a + (uint32_t)kn_final;
+        o.pt_cnt = bcount + (uint32_t)kn_final;
+        o.max_kn = (uint32_t)mx;
+        o.pad = 0;
+        out[w] = o;
+    }
+}
+
+cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uint32_t n,
+                        PlanOut *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int threads = 256;
+    const uint32_t blocks = (uint32_t)(((uint64_t)n * 32 + threads - 1) / threads);
+    if (wide) plan_kernel<uint32_t><<<blocks, threads, 0, s>>>((const uint32_t *)codes, items, n, out);
+    else plan_kernel<uint8_t><<<blocks, threads, 0, s>>>((const uint8_t *)codes, items, n, out);
+    return cudaGetLastError();
+}
+
+// Single-CTA exclusive scan of the plan: fragment offsets and value-buffer
+// bases, written into the items; totals = {codes, entries, max stack}.
+__global__ void plan_scan_kernel(EvalItem *items, const PlanOut *plan, uint32_t n,
+                                 uint64_t *frag_off, uint64_t *totals)
+{
+    __shared__ uint64_t sa[1024], sb[1024];
+    __shared__ uint32_t smx[1024];
+    const uint32_t t = threadIdx.x, T = blockDim.x;
+    const uint32_t per = (n + T - 1) / T;
+    const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
+    uint64_t a = 0, b = 0;
+    uint32_t mx = 0;
+    for (uint32_t i = lo; i < hi; ++i) {
+        a += plan[i].frag_len;
+        b += plan[i].pt_cnt;
+        mx = max(mx, plan[i].max_kn);
+    }
+    sa[t] = a; sb[t] = b; smx[t] = mx;
+    __syncthreads();
+    for (uint32_t off = 1; off < T; off <<= 1) {
+        uint64_t va = 0, vb = 0;
+        uint32_t vm = 0;
+        if (t >= off) { va = sa[t - off]; vb = sb[t - off]; vm = smx[t - off]; }
+        __syncthreads();
+        if (t >= off) { sa[t] += va; sb[t] += vb; smx[t] = max(smx[t], vm); }
+        __syncthreads();
+    }
+    uint64_t ra = sa[t] - a, rb = sb[t] - b;   // exclusive
+    for (uint32_t i = lo; i < hi; ++i) {
+        const PlanOut p = plan[i];
+        items[i].frag_off = ra;
+        items[i].frag_len = p.frag_len;
+        items[i].pt_base = rb;
+        items[i].pt_cnt = p.pt_cnt;
+        frag_off[i] = ra;
+        ra += p.frag_len;
+        rb += p.pt_cnt;
+    }
+    if (t == T - 1) {
+        frag_off[n] = sa[t];
+        totals[0] = sa[t];
+        totals[1] = sb[t];
+        totals[2] = smx[t];
+    }
+}
+
+cudaError_t launch_plan_scan(EvalItem *items, const PlanOut *plan, uint32_t n,
+                             uint64_t *frag_off, uint64_t *totals, cudaStream_t s)
+{
+    plan_scan_kernel<<<1, 1024, 0, s>>>(items, plan, n, frag_off, totals);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- validation
+
+// Upload check (Sec. 2.1 encoding): read right to left, every operator needs
+// two values on the stack and exactly one value remains.  Per chunk: the
+// smallest incoming stack that avoids underflow and the net change; chunks
+// compose as  need = max(need_R, need_L - delta_R), delta = delta_R + delta_L.
+struct Need {
+    int64_t need, delta;
+};
+__device__ __forceinline__ Need need_after(Need first, Need then) {
+    return Need{max(first.need, then.need - first.delta), first.delta + then.delta};
+}
+
+__global__ void validate_kernel(const uint8_t *__restrict__ codes, const EvalItem *__restrict__ chunks,
+                                uint32_t n, uint32_t n_consts, ValOut *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    const EvalItem it = chunks[w];
+    const uint64_t len = it.end - it.begin;
+    const uint64_t seg = (len + 31) / 32;
+    const uint64_t lo = umin64(it.begin + lane * seg, it.end);
+    const uint64_t hi = umin64(lo + seg, it.end);
+    Need f{kNegInf, 0};
+    uint32_t bad = 0;
+    for (uint64_t p = hi; p > lo; --p) {
+        const uint32_t c = codes[p - 1];
+        if (c >= 5 + n_consts) bad = 1;
+        if (c >= 4) {
+            f.delta += 1;
+        } else {
+            f.need = max(f.need, 2 - f.delta);
+            f.delta -= 1;
+        }
+    }
+    Need G = f;
+    for (int off = 1; off < 32; off <<= 1) {
+        Need o;
+        o.need = __shfl_down_sync(0xffffffffu, G.need, off);
+        o.delta = __shfl_down_sync(0xffffffffu, G.delta, off);
+        if (lane + off < 32) G = need_after(o, G);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        ValOut v;
+        v.need = G.need;
+        v.delta = G.delta;
+        v.bad_code = bad;
+        v.pad = 0;
+        out[w] = v;
+    }
+}
+
+cudaError_t launch_validate(const uint8_t *codes, const EvalItem *chunks, uint32_t n_chunks,
+                            uint32_t n_consts, ValOut *out, cudaStream_t s)
+{
+    if (n_chunks == 0) return cudaSuccess;
+    const int threads = 256;
+    const uint32_t blocks = (uint32_t)(((uint64_t)n_chunks * 32 + threads - 1) / threads);
+    validate_kernel<<<blocks, threads, 0, s>>>(codes, chunks, n_chunks, n_consts, out);
+    return cudaGetLastError();
+}
+
+__global__ void validate_trees_kernel(const ValOut *__restrict__ v, const uint32_t *__restrict__ first,
+                                      uint32_t n_trees, uint32_t *bad_count)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_trees) return;
+    const uint32_t a = first[t], b = first[t + 1];
+    Need acc{kNegInf, 0};
+    bool bad = (a == b);
+    for (uint32_t k = b; k > a; --k) {
+        const ValOut c = v[k - 1];
+        bad |= c.bad_code != 0;
+        acc = need_after(acc, Need{c.need, c.delta});
+    }
+    if (bad || acc.need > 0 || acc.delta != 1) atomicAdd(bad_count, 1u);
+}
+
+cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,
+                                  uint32_t n_trees, uint32_t *bad_count, cudaStream_t s)
+{
+    if (n_trees == 0) return cudaSuccess;
+    validate_trees_kernel<<<(n_trees + 255) / 256, 256, 0, s>>>(chunk_out, tree_first_chunk,
+                                                               n_trees, bad_count);
+    return cudaGetLastError();
+}
+
+}  // namespace gpk

@@ -1,0 +1,117 @@
+// Internal types shared by libgp's host code and its CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gpk {
+
+constexpr uint32_t kMaxCases = 64;
+constexpr uint32_t kLeafRows = 128;     // codes 4 ('x') .. 131 (constant 126)
+constexpr uint32_t kPtCode0 = 132;      // upper-tree code >= 132: value-buffer entry code-132
+constexpr uint32_t kItemFinal = 1u;     // item covers a whole (upper) tree: produce fitness
+constexpr uint64_t kNoSpill = ~0ull;
+
+// Device error word bits.
+constexpr uint32_t kErrMalformed = 1u;  // final item ended with != 1 value or underflowed
+constexpr uint32_t kErrSpill = 2u;      // operand stack outgrew its spill area
+constexpr uint32_t kErrPlan = 4u;       // fragment emitted a different shape than planned
+constexpr uint32_t kErrExtent = 8u;     // subtree extent walked off the end of a tree
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// One unit of evaluator work: a contiguous range of a level's code array.
+// A final item covers a whole tree (level 0) or a whole upper tree and
+// yields the tree's outputs; a fragment item covers one chunk of a larger
+// tree and writes that chunk's part of the next level's upper tree.
+struct alignas(16) EvalItem {
+    uint64_t begin, end;     // code positions [begin, end)
+    uint64_t frag_off;       // fragment: upper-tree position of its first code
+    uint64_t pt_base;        // fragment: first value-buffer entry it writes
+    uint64_t spill_off;      // dedicated spill area (in stack entries) or kNoSpill
+    uint64_t spill_cap;      // capacity of the dedicated spill area (entries)
+    uint32_t frag_len;       // fragment: number of upper-tree codes it writes
+    uint32_t pt_cnt;         // fragment: number of value-buffer entries it writes
+    uint32_t tree;
+    uint32_t flags;
+};
+static_assert(sizeof(EvalItem) == 64, "EvalItem layout");
+
+struct PlanOut {
+    uint32_t frag_len;       // codes the chunk contributes to the upper tree
+    uint32_t pt_cnt;         // value-buffer entries it creates
+    uint32_t max_kn;         // deepest operand stack while evaluating it
+    uint32_t pad;
+};
+
+struct ValOut {              // validation summary of one chunk (right-to-left)
+    int64_t need;            // minimum incoming stack size with no underflow
+    int64_t delta;           // net change of the stack size
+    uint32_t bad_code;
+    uint32_t pad;
+};
+
+struct EvalParams {
+    const void *codes;             // uint8_t (level 0) or uint32_t (upper levels)
+    const EvalItem *items;
+    uint32_t n_items;
+    uint32_t *counter;             // work counter, zero at launch
+    const float *x;                // [2*lanes], padded with zeros
+    const float *y;                // [2*lanes], padded with zeros
+    const float *consts;           // [n_consts]
+    uint32_t n_cases;
+    uint32_t n_consts;
+    float div0;
+    uint32_t window;               // shared-memory stack entries per warp
+    const float2 *pt_in;           // value buffer read by upper-tree codes >= 132
+    float2 *pt_out;                // value buffer written by fragments
+    uint32_t *u_out;               // next level's upper-tree codes
+    float *values;                 // [n_trees * n_cases]
+    float *fitness;                // [n_trees]
+    uint32_t *hits;                // [n_trees]
+    float2 *spill;                 // spill memory, [entries][lanes] float2
+    uint64_t spill_per_warp;       // entries per resident warp
+    uint32_t *err;
+};
+
+struct XoChild {                   // child = M[0,i) ++ D[j,e_d) ++ M[e_m,n_m)
+    uint64_t dst;                  // destination start (16-byte aligned)
+    uint64_t n;                    // child size
+    uint64_t head_src;             // source of bytes [0, i)
+    uint64_t i;
+    uint64_t mid_src;              // source of bytes [i, i+ld)
+    uint64_t ld;
+    uint64_t tail_src;             // source of bytes [i+ld, n)
+    uint64_t pad;
+};
+
+struct XoTile {
+    uint32_t child;
+    uint32_t pad;
+    uint64_t begin;                // child byte offset of the tile
+};
+
+struct ExtentQuery {
+    uint64_t tree_start, tree_size, point;
+};
+
+// Launchers (defined in the .cu files; return the launch's error).
+size_t eval_smem_bytes(int lanes, int warps, int window);
+cudaError_t eval_prepare(int lanes, bool wide, size_t smem);
+cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
+                        size_t smem, cudaStream_t s);
+cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uint32_t n,
+                        PlanOut *out, cudaStream_t s);
+cudaError_t launch_plan_scan(EvalItem *items, const PlanOut *plan, uint32_t n,
+                             uint64_t *frag_off /*[n+1]*/, uint64_t *totals /*[3]*/,
+                             cudaStream_t s);
+cudaError_t launch_validate(const uint8_t *codes, const EvalItem *chunks, uint32_t n_chunks,
+                            uint32_t n_consts, ValOut *out, cudaStream_t s);
+cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,
+                                  uint32_t n_trees, uint32_t *bad_count, cudaStream_t s);
+cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n,
+                          uint64_t *end, uint32_t *err, cudaStream_t s);
+cudaError_t launch_xo_copy(const uint8_t *src, uint8_t *dst, const XoChild *children,
+                           const XoTile *tiles, uint32_t n_tiles, uint32_t tile_bytes,
+                           cudaStream_t s);
+
+}  // namespace gpk

@@ -1,0 +1,130 @@
+// Subtree crossover on the device (Sec. 3.1, Sec. 2.3): the host chooses the
+// points sequentially; the device finds the two subtree extents and copies
+// child = mum[0,i) ++ dad[j,e_d) ++ mum[e_m,n_m).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gp_internal.cuh"
+
+namespace gpk {
+
+// One warp per query: the end (exclusive) of the subtree rooted at `point`.
+// Reading left to right, `need` counts subtrees still to be read: an
+// operator adds one, a leaf removes one; the subtree ends where it reaches
+// zero.  Each step covers 32 lanes x 16 bytes.
+__global__ void extent_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
+                              uint32_t n, uint64_t *__restrict__ end_out, uint32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    const ExtentQuery Q = q[w];
+    const uint64_t tend = Q.tree_start + Q.tree_size;
+    uint64_t pos = Q.tree_start + Q.point;
+    int64_t need = 1;
+    for (;;) {
+        if (pos >= tend) {
+            if (lane == 0) {
+                atomicOr(err, kErrExtent);
+                end_out[w] = Q.tree_size;
+            }
+            return;
+        }
+        const uint64_t lo = pos + 16ull * lane;
+        int s = 0, mn = 1 << 30;
+        for (int k = 0; k < 16; ++k) {
+            if (lo + k < tend) {
+                s += (arena[lo + k] < 4) ? 1 : -1;
+                mn = min(mn, s);
+            }
+        }
+        // exclusive prefix of s over lanes
+        int incl = s;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        const int excl = incl - s;
+        const bool closes = (lo < tend) && (need + excl + mn <= 0);
+        const unsigned ball = __ballot_sync(0xffffffffu, closes);
+        if (ball) {
+            const int f = __ffs(ball) - 1;
+            if (lane == f) {
+                int64_t r = need + excl;
+                uint64_t k = 0;
+                for (; k < 16; ++k) {
+                    r += (arena[lo + k] < 4) ? 1 : -1;
+                    if (r == 0) break;
+                }
+                end_out[w] = lo + k + 1 - Q.tree_start;
+            }
+            return;
+        }
+        need += __shfl_sync(0xffffffffu, incl, 31);
+        pos += 512;
+    }
+}
+
+cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n,
+                          uint64_t *end, uint32_t *err, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int threads = 256;
+    const uint32_t blocks = (uint32_t)(((uint64_t)n * 32 + threads - 1) / threads);
+    extent_kernel<<<blocks, threads, 0, s>>>(arena, q, n, end, err);
+    return cudaGetLastError();
+}
+
+// Source byte of child byte p.
+__device__ __forceinline__ uint64_t xo_src(const XoChild &c, uint64_t p) {
+    if (p < c.i) return c.head_src + p;
+    if (p < c.i + c.ld) return c.mid_src + (p - c.i);
+    return c.tail_src + (p - c.i - c.ld);
+}
+
+// Four source bytes starting at byte address a (any alignment), from two
+// aligned words.  Sources are padded by at least 8 bytes on both ends.
+__device__ __forceinline__ uint32_t load4_unaligned(const uint8_t *src, uint64_t a) {
+    const uint64_t al = a & ~3ull;
+    const uint32_t w0 = __ldg(reinterpret_cast<const uint32_t *>(src + al));
+    const uint32_t w1 = __ldg(reinterpret_cast<const uint32_t *>(src + al + 4));
+    const uint32_t sh = (uint32_t)(a & 3);
+    return __byte_perm(w0, w1, 0x3210u + 0x1111u * sh);
+}
+
+// One CTA per tile of one child; every thread writes aligned 32-bit words.
+__global__ void xo_copy_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                               const XoChild *__restrict__ children, const XoTile *__restrict__ tiles,
+                               uint32_t tile_bytes)
+{
+    const XoTile T = tiles[blockIdx.x];
+    const XoChild c = children[T.child];
+    const uint64_t tend = umin64(T.begin + tile_bytes, (c.n + 3) & ~3ull);
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + c.dst);
+    const uint64_t b1 = c.i, b2 = c.i + c.ld;
+    for (uint64_t p = T.begin + 4ull * threadIdx.x; p < tend; p += 4ull * blockDim.x) {
+        uint32_t word;
+        const uint64_t q = p + 3;
+        const bool one_seg = (q < c.n) && ((q < b1) || (p >= b1 && q < b2) || (p >= b2));
+        if (one_seg) {
+            word = load4_unaligned(src, xo_src(c, p));
+        } else {
+            word = 0;
+            for (int k = 0; k < 4; ++k) {
+                if (p + k < c.n) word |= (uint32_t)src[xo_src(c, p + k)] << (8 * k);
+            }
+        }
+        d32[p >> 2] = word;
+    }
+}
+
+cudaError_t launch_xo_copy(const uint8_t *src, uint8_t *dst, const XoChild *children,
+                           const XoTile *tiles, uint32_t n_tiles, uint32_t tile_bytes,
+                           cudaStream_t s)
+{
+    if (n_tiles == 0) return cudaSuccess;
+    xo_copy_kernel<<<n_tiles, 256, 0, s>>>(src, dst, children, tiles, tile_bytes);
+    return cudaGetLastError();
+}
+
+}  // namespace gpk

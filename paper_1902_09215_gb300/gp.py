@@ -1,0 +1,270 @@
+"""Python binding of libgp (include/gp.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  All evaluation
+and crossover work runs in libgp's CUDA kernels; if libgp.so is missing or
+fails to load, every call raises.  Streams may be given as None (legacy
+default stream), a raw cudaStream_t integer, or any object with a
+`cuda_stream` attribute (e.g. torch.cuda.Stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_EMALFORMED, GP_ECUDA, GP_ETIMEOUT, GP_ELIMIT = range(7)
+KERNEL_KINDS = ["eval", "eval_upper", "plan", "scan", "validate", "extent", "copy", "unused"]
+
+EXPORTED = [
+    "gp_create_population", "gp_crossover", "gp_evaluate", "gp_evaluate_ex", "gp_fitness",
+    "gp_tree_size", "gp_tree_read", "gp_population_get_info", "gp_destroy_population",
+    "gp_status_string", "gp_eval_stats_get", "gp_kernel_launch_count", "gp_profile_enable",
+    "gp_profile_read",
+]
+
+
+class gp_problem(C.Structure):
+    _fields_ = [("n_cases", C.c_uint32), ("x", C.POINTER(C.c_float)), ("y", C.POINTER(C.c_float)),
+                ("n_consts", C.c_uint32), ("consts", C.POINTER(C.c_float)),
+                ("protected_div_value", C.c_float), ("max_tree_nodes", C.c_uint64),
+                ("hbm_budget_bytes", C.c_uint64)]
+
+
+class gp_xo(C.Structure):
+    _fields_ = [("mum", C.c_uint32), ("dad", C.c_uint32), ("mum_point", C.c_uint64),
+                ("dad_point", C.c_uint64)]
+
+
+class gp_eval_options(C.Structure):
+    _fields_ = [("chunk_nodes", C.c_uint32), ("warps_per_cta", C.c_uint32),
+                ("window_entries", C.c_uint32)]
+
+
+class gp_population_info(C.Structure):
+    _fields_ = [("n_trees", C.c_uint32), ("n_cases", C.c_uint32), ("total_nodes", C.c_uint64),
+                ("d_nodes", C.c_void_p), ("d_tree_start", C.c_void_p), ("d_tree_size", C.c_void_p),
+                ("d_fitness", C.c_void_p), ("d_case_values", C.c_void_p), ("d_hits", C.c_void_p)]
+
+
+class gp_eval_stats(C.Structure):
+    _fields_ = [("levels", C.c_uint32), ("pad", C.c_uint32), ("items", C.c_uint64),
+                ("upper_codes", C.c_uint64), ("value_entries", C.c_uint64)]
+
+
+class gp_kernel_profile(C.Structure):
+    _fields_ = [("launches", C.c_uint64 * 8), ("total_ms", C.c_double * 8)]
+
+
+class GpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {gp_status_string(status)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libgp.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libgp.so not found at {path}: run __graft_entry__.build()")
+            L = C.CDLL(path)
+            P, vp = C.POINTER, C.c_void_p
+            L.gp_create_population.argtypes = [P(gp_problem), C.c_uint32, P(C.c_uint8), P(C.c_uint64), vp, P(vp)]
+            L.gp_crossover.argtypes = [vp, P(gp_xo), C.c_uint32, vp, P(vp)]
+            L.gp_evaluate.argtypes = [vp, vp]
+            L.gp_evaluate_ex.argtypes = [vp, P(gp_eval_options), vp]
+            L.gp_fitness.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_uint32)]
+            L.gp_tree_size.argtypes = [vp, C.c_uint32, P(C.c_uint64)]
+            L.gp_tree_read.argtypes = [vp, C.c_uint32, P(C.c_uint8), C.c_uint64]
+            L.gp_population_get_info.argtypes = [vp, P(gp_population_info)]
+            L.gp_destroy_population.argtypes = [vp]
+            L.gp_destroy_population.restype = None
+            L.gp_status_string.argtypes = [C.c_int]
+            L.gp_status_string.restype = C.c_char_p
+            L.gp_eval_stats_get.argtypes = [vp, P(gp_eval_stats)]
+            L.gp_kernel_launch_count.argtypes = []
+            L.gp_kernel_launch_count.restype = C.c_uint64
+            L.gp_profile_enable.argtypes = [C.c_int]
+            L.gp_profile_read.argtypes = [P(gp_kernel_profile), C.c_int]
+            _lib = L
+    return _lib
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return C.c_void_p(s)
+    return C.c_void_p(int(s.cuda_stream))
+
+
+def _check(st, where):
+    if st != GP_OK:
+        raise GpError(st, where)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def gp_status_string(st: int) -> str:
+    return lib().gp_status_string(int(st)).decode()
+
+
+class Problem:
+    """Fitness cases, constants and limits (kept alive while in use)."""
+
+    def __init__(self, x, y, consts, protected_div_value=1.0, max_tree_nodes=0, hbm_budget_bytes=0):
+        self.x = np.ascontiguousarray(x, dtype=np.float32)
+        self.y = np.ascontiguousarray(y, dtype=np.float32)
+        self.consts = np.ascontiguousarray(consts, dtype=np.float32)
+        if self.x.shape != self.y.shape:
+            raise ValueError("x and y must have the same length")
+        c = self.consts if self.consts.size else np.zeros(1, np.float32)
+        self._c = c
+        self.struct = gp_problem(self.x.shape[0], _ptr(self.x, C.c_float), _ptr(self.y, C.c_float),
+                                 self.consts.shape[0], _ptr(c, C.c_float), float(protected_div_value),
+                                 int(max_tree_nodes), int(hbm_budget_bytes))
+
+    @property
+    def n_cases(self):
+        return self.x.shape[0]
+
+
+class Population:
+    """Owns one gp_population handle."""
+
+    def __init__(self, handle, n_trees, n_cases):
+        self.handle = handle
+        self.n_trees = n_trees
+        self.n_cases = n_cases
+
+    def __del__(self):
+        try:
+            gp_destroy_population(self)
+        except Exception:
+            pass
+
+    @property
+    def _h(self):
+        if self.handle is None:
+            raise RuntimeError("population destroyed")
+        return self.handle
+
+
+def gp_create_population(problem: Problem, nodes, offsets, stream=None) -> Population:
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = offsets.shape[0] - 1
+    if n < 0:
+        raise ValueError("offsets needs n_trees + 1 entries")
+    nb = nodes if nodes.size else np.zeros(1, np.uint8)
+    out = C.c_void_p()
+    st = lib().gp_create_population(C.byref(problem.struct), n, _ptr(nb, C.c_uint8),
+                                    _ptr(offsets, C.c_uint64), _stream(stream), C.byref(out))
+    _check(st, "gp_create_population")
+    return Population(out, n, problem.n_cases)
+
+
+def make_xo(mum, dad, mum_point, dad_point):
+    ops = (gp_xo * len(mum))()
+    for k, (a, b, i, j) in enumerate(zip(mum, dad, mum_point, dad_point)):
+        ops[k] = gp_xo(int(a), int(b), int(i), int(j))
+    return ops
+
+
+def gp_crossover(parents: Population, ops, stream=None) -> Population:
+    """ops: a ctypes array of gp_xo, or a tuple (mum, dad, mum_point, dad_point)."""
+    if isinstance(ops, tuple):
+        ops = make_xo(*ops)
+    out = C.c_void_p()
+    st = lib().gp_crossover(parents._h, ops, len(ops), _stream(stream), C.byref(out))
+    _check(st, "gp_crossover")
+    return Population(out, len(ops), parents.n_cases)
+
+
+def gp_evaluate(pop: Population, stream=None, chunk_nodes=0, warps_per_cta=0, window_entries=0):
+    if chunk_nodes or warps_per_cta or window_entries:
+        o = gp_eval_options(int(chunk_nodes), int(warps_per_cta), int(window_entries))
+        st = lib().gp_evaluate_ex(pop._h, C.byref(o), _stream(stream))
+    else:
+        st = lib().gp_evaluate(pop._h, _stream(stream))
+    _check(st, "gp_evaluate")
+
+
+def gp_fitness(pop: Population, case_values=False, hits=False):
+    fit = np.empty(max(pop.n_trees, 1), np.float32)
+    vals = np.empty((max(pop.n_trees, 1), pop.n_cases), np.float32) if case_values else None
+    h = np.empty(max(pop.n_trees, 1), np.uint32) if hits else None
+    st = lib().gp_fitness(pop._h, _ptr(fit, C.c_float),
+                          _ptr(vals, C.c_float) if vals is not None else None,
+                          _ptr(h, C.c_uint32) if h is not None else None)
+    _check(st, "gp_fitness")
+    n = pop.n_trees
+    return fit[:n], (vals[:n] if vals is not None else None), (h[:n] if h is not None else None)
+
+
+def gp_tree_size(pop: Population, tree: int) -> int:
+    n = C.c_uint64()
+    _check(lib().gp_tree_size(pop._h, int(tree), C.byref(n)), "gp_tree_size")
+    return int(n.value)
+
+
+def gp_tree_read(pop: Population, tree: int) -> np.ndarray:
+    n = gp_tree_size(pop, tree)
+    buf = np.empty(max(n, 1), np.uint8)
+    _check(lib().gp_tree_read(pop._h, int(tree), _ptr(buf, C.c_uint8), n), "gp_tree_read")
+    return buf[:n]
+
+
+def gp_population_get_info(pop: Population) -> gp_population_info:
+    info = gp_population_info()
+    _check(lib().gp_population_get_info(pop._h, C.byref(info)), "gp_population_get_info")
+    return info
+
+
+def gp_destroy_population(pop: Population):
+    if pop.handle is not None:
+        lib().gp_destroy_population(pop.handle)
+        pop.handle = None
+
+
+def gp_eval_stats_get(pop: Population) -> dict:
+    s = gp_eval_stats()
+    _check(lib().gp_eval_stats_get(pop._h, C.byref(s)), "gp_eval_stats_get")
+    return {"levels": s.levels, "items": s.items, "upper_codes": s.upper_codes,
+            "value_entries": s.value_entries}
+
+
+def gp_kernel_launch_count() -> int:
+    return int(lib().gp_kernel_launch_count())
+
+
+def gp_profile_enable(on: bool):
+    _check(lib().gp_profile_enable(1 if on else 0), "gp_profile_enable")
+
+
+def gp_profile_read(reset: bool = False) -> dict:
+    p = gp_kernel_profile()
+    _check(lib().gp_profile_read(C.byref(p), 1 if reset else 0), "gp_profile_read")
+    return {k: {"launches": int(p.launches[i]), "ms": float(p.total_ms[i])}
+            for i, k in enumerate(KERNEL_KINDS) if k != "unused"}
+
+
+def read_all_trees(pop: Population):
+    """(nodes, offsets) of every tree, packed."""
+    trees = [gp_tree_read(pop, t) for t in range(pop.n_trees)]
+    sizes = np.array([t.shape[0] for t in trees], dtype=np.uint64)
+    offs = np.zeros(len(trees) + 1, np.uint64)
+    np.cumsum(sizes, out=offs[1:])
+    return (np.concatenate(trees) if trees else np.zeros(0, np.uint8)), offs

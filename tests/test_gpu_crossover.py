@@ -1,0 +1,82 @@
+"""GPU parity for subtree crossover (Sec. 3.1): children byte-identical to
+the oracle's three-segment copy."""
+import numpy as np
+import pytest
+
+from paper_1902_09215_gb300 import synth
+from tests.gpu_util import gpu, same_f32  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def make_pop(gp, nodes, offs, **kw):
+    x, y, c = synth.problem()
+    return gp.gp_create_population(gp.Problem(x, y, c, **kw), nodes, offs)
+
+
+def test_crossover_population_4000(gpu, oracle):
+    nodes, offs = synth.population_loguniform(seed=3)
+    pop = make_pop(gpu, nodes, offs)
+    sizes = np.diff(offs.astype(np.int64))
+    ops = synth.crossover_points(11, sizes, 4000)
+    kids = gpu.gp_crossover(pop, ops)
+    kn, ko = gpu.read_all_trees(kids)
+    rn, ro = oracle.crossover_population(nodes, offs, *ops)
+    assert np.array_equal(ko, ro)
+    assert np.array_equal(kn, rn)
+
+
+def test_crossover_edge_points(gpu, oracle):
+    rng = np.random.default_rng(3)
+    trees = [synth.random_tree(rng, n) for n in (1, 3, 31, 1001, 20001)]
+    nodes, offs = synth.pack(trees)
+    pop = make_pop(gpu, nodes, offs)
+    sizes = np.diff(offs.astype(np.int64))
+    recs = []
+    for a in range(len(trees)):
+        for b in range(len(trees)):
+            for i in {0, int(sizes[a]) - 1, int(sizes[a]) // 2}:
+                for j in {0, int(sizes[b]) - 1, int(sizes[b]) // 3}:
+                    recs.append((a, b, i, j))
+    ops = tuple(np.array(v) for v in zip(*recs))
+    kids = gpu.gp_crossover(pop, ops)
+    kn, ko = gpu.read_all_trees(kids)
+    rn, ro = oracle.crossover_population(nodes, offs, *ops)
+    assert np.array_equal(kn, rn) and np.array_equal(ko, ro)
+
+
+def test_children_evaluate_like_oracle(gpu, oracle):
+    x, y, c = synth.problem()
+    nodes, offs = synth.population_loguniform(seed=8, count=600, hi=20001)
+    pop = make_pop(gpu, nodes, offs)
+    ops = synth.crossover_points(2, np.diff(offs.astype(np.int64)), 600)
+    kids = gpu.gp_crossover(pop, ops)
+    gpu.gp_evaluate(kids)
+    fit, vals, hits = gpu.gp_fitness(kids, case_values=True, hits=True)
+    rn, ro = oracle.crossover_population(nodes, offs, *ops)
+    ref = oracle.eval_population(rn, ro, x, y, c, n_threads=8)
+    assert same_f32(vals, ref["out"]) and same_f32(fit, ref["fitness"])
+    assert np.array_equal(hits, ref["hits"])
+
+
+def test_node_limit(gpu):
+    rng = np.random.default_rng(4)
+    nodes, offs = synth.pack([synth.random_tree(rng, 101), synth.random_tree(rng, 101)])
+    pop = make_pop(gpu, nodes, offs, max_tree_nodes=150)
+    # replacing a leaf of tree 0 by the whole of tree 1 gives 201 nodes
+    leaf = int(np.nonzero(nodes[:101] >= 4)[0][0])
+    with pytest.raises(gpu.GpError) as e:
+        gpu.gp_crossover(pop, (np.array([0]), np.array([1]), np.array([leaf]), np.array([0])))
+    assert e.value.status == gpu.GP_ELIMIT
+    ok = gpu.gp_crossover(pop, (np.array([0]), np.array([1]), np.array([0]), np.array([0])))
+    assert gpu.gp_tree_size(ok, 0) == 101
+
+
+def test_bad_points_rejected(gpu):
+    nodes, offs = synth.population_small()
+    pop = make_pop(gpu, nodes, offs)
+    with pytest.raises(gpu.GpError) as e:
+        gpu.gp_crossover(pop, (np.array([0]), np.array([1]), np.array([10 ** 6]), np.array([0])))
+    assert e.value.status == gpu.GP_EINVAL
+    with pytest.raises(gpu.GpError):
+        gpu.gp_crossover(pop, (np.array([0]), np.array([999]), np.array([0]), np.array([0])))
