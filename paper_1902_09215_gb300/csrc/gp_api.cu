@@ -472,12 +472,13 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     if (!(opt && opt->warps_per_cta))        // as many warps as shared memory holds
-        while (W > 1 && eval_smem_bytes(lanes, (int)W, (int)K) > (size_t)maxsm) --W;
-    // Upper levels (32-bit codes) run at most 16 warps per SM.
-    const uint32_t Wu = std::min<uint32_t>(W, 16);
-    const size_t smem = eval_smem_bytes(lanes, (int)W, (int)K);
-    const size_t smem_u = eval_smem_bytes(lanes, (int)Wu, (int)K);
-    if (smem > (size_t)maxsm) return GP_EINVAL;
+        while (W > 1 && eval_smem_bytes(lanes, (int)W, (int)K, false) > (size_t)maxsm) --W;
+    // Upper levels (32-bit codes) run at most 16 warps per SM, with staging.
+    uint32_t Wu = std::min<uint32_t>(W, 16);
+    while (Wu > 1 && eval_smem_bytes(lanes, (int)Wu, (int)K, true) > (size_t)maxsm) --Wu;
+    const size_t smem = eval_smem_bytes(lanes, (int)W, (int)K, false);
+    const size_t smem_u = eval_smem_bytes(lanes, (int)Wu, (int)K, true);
+    if (smem > (size_t)maxsm || smem_u > (size_t)maxsm) return GP_EINVAL;
     CK(prepare_eval_once(lanes, false, smem));
     CK(prepare_eval_once(lanes, true, smem_u));
     CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
@@ -570,6 +571,7 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
                 if (tot[1] + kPtCode0 >= 0xffffffffull) return GP_ENOMEM;
                 if (tot[2] > spill_per_warp) return GP_EINVAL;   // cannot happen: chunks <= C
                 CK(ws.alloc((void **)&u_next, sizeof(uint32_t) * (round_up(tot[0], 16) + 32), s));
+                CK(cudaMemsetAsync(u_next + tot[0], 0, sizeof(uint32_t) * (round_up(tot[0], 16) + 32 - tot[0]), s));
                 CK(ws.alloc((void **)&pt_next, sizeof(float2) * (tot[1] * lanes + 1), s));
                 P->stats.upper_codes += tot[0];
                 P->stats.value_entries += tot[1];

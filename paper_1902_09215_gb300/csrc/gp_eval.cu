@@ -84,7 +84,6 @@ template <> struct Group<uint8_t> {
     // as a value the compiler knows to be uniform.
     __device__ __forceinline__ static Sub uniform(Sub v, uint32_t mask) { return __reduce_or_sync(mask, v); }
     __device__ __forceinline__ uint32_t first() const { return w.x & 0xFFu; }
-    __device__ __forceinline__ void prefetch_values(const float2 *, int, int) const {}
 };
 
 template <> struct Group<uint32_t> {
@@ -105,17 +104,6 @@ template <> struct Group<uint32_t> {
                           __reduce_or_sync(mask, v.z), __reduce_or_sync(mask, v.w));
     }
     __device__ __forceinline__ uint32_t first() const { return w[0].x; }
-    // Pull this group's value-buffer leaves into L1 ahead of their use.
-    __device__ __forceinline__ void prefetch_values(const float2 *pt, int lanes, int lane) const {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t c[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (c[k] >= kPtCode0)
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(pt + (uint64_t)(c[k] - kPtCode0) * lanes + lane));
-        }
-    }
 };
 
 // ---------------------------------------------------------------- one item
@@ -143,50 +131,94 @@ __device__ __forceinline__ uint64_t lds64(uint32_t a) {
     return v;
 }
 
-// Four one-byte codes of `w`, read from the high byte down (right to left in
-// the tree), on a stack whose top value is `tos` and whose next free window
-// entry is at shared address `t` (entries S bytes apart, this lane's column).
-// The caller guarantees at least four entries below `t` and room for four
-// more.  Codes are warp-uniform, so every branch is marked .uni.
+// Asynchronous 8-byte global -> shared copies (value-buffer staging).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
+
+// The group interpreter below keeps the top of stack `tos` in a register and
+// the rest of the operand stack in this lane's column of the shared window;
+// `t` is the shared address of the next free entry (entries S bytes apart).
 //   leaf c >= 4 : push tos; tos = table[c] (shared address tb + c*S)
-//   op   c < 4  : tos = tos (op) pop   -- tos holds the operator's first
+//   op   c < 4  : tos = tos (op) pop -- tos holds the operator's first
 //                 argument, the popped entry its second
 //   '/' is protected: a zero divisor gives d0.
-#define GP_NODE_PTX(BIT)                                                        \
-    "{\n\t.reg .pred pl, p;\n\t.reg .b32 c, a;\n\t.reg .b64 v;\n\t"            \
-    ".reg .f32 tx, ty, bx, by, qx, qy;\n\t"                                    \
-    "bfe.u32 c, %2, " #BIT ", 8;\n\t"                                         \
-    "setp.gt.u32 pl, c, 3;\n\t"                                               \
-    "@pl bra.uni LEAF;\n\t"                                                   \
-    "sub.u32 %1, %1, %5;\n\t"                                                 \
-    "ld.shared.b64 v, [%1];\n\t"                                              \
-    "setp.eq.u32 p, c, 2;\n\t@p bra.uni MUL;\n\t"                             \
-    "setp.eq.u32 p, c, 0;\n\t@p bra.uni ADD;\n\t"                             \
-    "setp.eq.u32 p, c, 1;\n\t@p bra.uni SUB;\n\t"                             \
-    "mov.b64 {tx, ty}, %0;\n\tmov.b64 {bx, by}, v;\n\t"                       \
-    "div.rn.f32 qx, tx, bx;\n\tsetp.neu.f32 p, bx, 0f00000000;\n\t"           \
-    "selp.f32 tx, qx, %4, p;\n\t"                                             \
-    "div.rn.f32 qy, ty, by;\n\tsetp.neu.f32 p, by, 0f00000000;\n\t"           \
-    "selp.f32 ty, qy, %4, p;\n\t"                                             \
-    "mov.b64 %0, {tx, ty};\n\tbra.uni END;\n"                                  \
-    "ADD:\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni END;\n"                        \
-    "SUB:\n\tsub.rn.f32x2 %0, %0, v;\n\tbra.uni END;\n"                        \
-    "MUL:\n\tmul.rn.f32x2 %0, %0, v;\n\tbra.uni END;\n"                        \
-    "LEAF:\n\tst.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %5;\n\t"              \
-    "mad.lo.u32 a, c, %5, %3;\n\tld.shared.b64 %0, [a];\n"                     \
-    "END:\n\t}\n\t"
+// One node of the group interpreter below (code = byte BIT of register w,
+// node index IDX for unique labels).  Operands: %0 tos, %1 t, %7 tb, %11 S.
+//   leaf  : push tos; tos = table[c]
+//   op    : v = pop; tos = tos (op) v; '/' jumps to the shared DIV routine
+#define GP_GNODE(BIT, IDX)                                                       \
+    "bfe.u32 c, w, " #BIT ", 8;\n\t"                                           \
+    "setp.gt.u32 pl, c, 3;\n\t"                                                \
+    "@pl bra.uni LF" #IDX ";\n\t"                                              \
+    "sub.u32 %1, %1, %11;\n\t"                                                 \
+    "ld.shared.b64 v, [%1];\n\t"                                               \
+    "setp.lt.u32 p, c, 2;\n\t"                                                 \
+    "@p bra.uni LO" #IDX ";\n\t"                                               \
+    "setp.eq.u32 p, c, 2;\n\t"                                                 \
+    "@p bra.uni MU" #IDX ";\n\t"                                               \
+    "mov.u32 ret, " #IDX ";\n\t"                                               \
+    "bra.uni DIVR;\n"                                                          \
+    "MU" #IDX ":\n\tmul.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
+    "LO" #IDX ":\n\tsetp.eq.u32 p, c, 0;\n\t@p bra.uni AD" #IDX ";\n\t"          \
+    "sub.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"                          \
+    "AD" #IDX ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
+    "LF" #IDX ":\n\tst.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %11;\n\t"          \
+    "mad.lo.u32 a, c, %11, %7;\n\tld.shared.b64 %0, [a];\n"                      \
+    "E" #IDX ":\n\t"
 
+// Word entry: leave with %2 = Q unless the window holds >= 4 entries and has
+// room for 4 more (t - lo <= span), then interpret its four codes.
+#define GP_GWORD(Q, REG, I0, I1, I2, I3)                                         \
+    "W" #Q ":\n\tsub.u32 dd, %1, %9;\n\tsetp.gt.u32 p, dd, %10;\n\t"               \
+    "@p bra.uni X" #Q ";\n\tmov.b32 w, " REG ";\n\t"                              \
+    GP_GNODE(24, I0) GP_GNODE(16, I1) GP_GNODE(8, I2) GP_GNODE(0, I3)
+
+// Interprets the codes of one 16-code group (words w3..w0, each read from
+// its high byte down, i.e. right to left in the tree) starting at word q,
+// for as long as each next word can run without checks.  Returns the index
+// of the first word it did not interpret, or -1.  Codes are warp-uniform,
+// so every branch is marked .uni; protected division (a zero divisor gives
+// d0) is one shared routine reached with a return index.
 template <uint32_t S>
-__device__ __forceinline__ void fast4_u8(uint64_t &tos, uint32_t &t, uint32_t w, uint32_t tb, float d0) {
-    asm volatile(GP_NODE_PTX(24) GP_NODE_PTX(16) GP_NODE_PTX(8) GP_NODE_PTX(0)
-                 : "+l"(tos), "+r"(t)
-                 : "r"(w), "r"(tb), "f"(d0), "n"(S));
+__device__ __forceinline__ int group_u8(uint64_t &tos, uint32_t &t, int q, uint4 w4, uint32_t tb,
+                                        float d0, uint32_t lo, uint32_t span)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, pl;\n\t.reg .b32 c, a, w, ret, dd;\n\t.reg .b64 v;\n\t"
+        ".reg .f32 tx, ty, bx, by, qx, qy;\n\t"
+        "ENT: .branchtargets W0, W1, W2, W3;\n\t"
+        "brx.idx.uni %2, ENT;\n"
+        GP_GWORD(3, "%6", 0, 1, 2, 3)
+        GP_GWORD(2, "%5", 4, 5, 6, 7)
+        GP_GWORD(1, "%4", 8, 9, 10, 11)
+        GP_GWORD(0, "%3", 12, 13, 14, 15)
+        "mov.s32 %2, -1;\n\tbra.uni DONE;\n"
+        "X3:\n\tmov.s32 %2, 3;\n\tbra.uni DONE;\n"
+        "X2:\n\tmov.s32 %2, 2;\n\tbra.uni DONE;\n"
+        "X1:\n\tmov.s32 %2, 1;\n\tbra.uni DONE;\n"
+        "X0:\n\tmov.s32 %2, 0;\n\tbra.uni DONE;\n"
+        "DIVR:\n\tmov.b64 {tx, ty}, %0;\n\tmov.b64 {bx, by}, v;\n\t"
+        "div.rn.f32 qx, tx, bx;\n\tsetp.neu.f32 p, bx, 0f00000000;\n\tselp.f32 tx, qx, %8, p;\n\t"
+        "div.rn.f32 qy, ty, by;\n\tsetp.neu.f32 p, by, 0f00000000;\n\tselp.f32 ty, qy, %8, p;\n\t"
+        "mov.b64 %0, {tx, ty};\n\t"
+        "RET: .branchtargets E0, E1, E2, E3, E4, E5, E6, E7, E8, E9, E10, E11, E12, E13, E14, E15;\n\t"
+        "brx.idx.uni ret, RET;\n"
+        "DONE:\n\t}"
+        : "+l"(tos), "+r"(t), "+r"(q)
+        : "r"(w4.x), "r"(w4.y), "r"(w4.z), "r"(w4.w), "r"(tb), "f"(d0), "r"(lo), "r"(span), "n"(S));
+    return q;
 }
+
 
 template <int LANES, typename Code, bool WIDE>
 __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &it, uint32_t win_sa,
-                                          uint32_t tbl_sa, float *errs, float2 *__restrict__ spill,
-                                          uint64_t spill_cap, int lane, uint32_t mask, float y0, float y1)
+                                          uint32_t tbl_sa, uint32_t stage_sa, float *errs,
+                                          float2 *__restrict__ spill, uint64_t spill_cap, int lane,
+                                          uint32_t mask, float y0, float y1)
 {
     constexpr uint32_t S = LANES * sizeof(float2);          // bytes per stack entry / table row
     const Code *codes = static_cast<const Code *>(P.codes);
@@ -206,10 +238,26 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
     uint32_t fault = 0;                   // kErr* bits; any fault ends the item
     const uint32_t dmax = (uint32_t)(K - 4) * S;   // room for four pushes below this
 
+    // Upper trees: value-buffer leaves of the current group were copied to
+    // staging buffer `buf`, slot = position in the group (jcur).
+    uint32_t buf = 0, jcur = 0;
     auto leafval = [&](uint32_t c) -> uint64_t {
-        if (WIDE && c >= kPtCode0)
-            return pk(P.pt_in[(uint64_t)(c - kPtCode0) * LANES + lane]);
+        if (WIDE && c >= kPtCode0) return lds64(stage_sa + (buf * 16 + jcur) * S);
         return lds64(tb + c * S);
+    };
+    auto stage = [&](const Group<Code> &grp, int64_t gbase, uint32_t into) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const typename Group<Code>::Sub v = grp.sub(q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t c = Group<Code>::code(v, k);
+                const uint64_t pos = (uint64_t)gbase + 4 * q + k;
+                if (pos >= it.begin && pos < it.end && c >= kPtCode0)
+                    cp_async8(stage_sa + (into * 16 + 4 * q + k) * S,
+                              P.pt_in + (uint64_t)(c - kPtCode0) * LANES + lane);
+            }
+        }
     };
     // Fragment output stays inside the slot the plan reserved for it.
     auto emit = [&](uint32_t code) {
@@ -246,7 +294,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
             t += h * S;
         }
     };
-    // Unchecked step for upper-tree codes (the byte-code path uses fast4_u8).
+    // Unchecked step for upper-tree codes (the byte-code path uses group_u8).
     auto step_fast = [&](uint32_t c) {
         switch (c) {
         case 0: t -= S; tos = pk(f2_add(upk(tos), upk(lds64(t)))); break;
@@ -297,49 +345,96 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
 
     const uint64_t b = it.begin, e = it.end;
     const uint32_t fast_span = (uint32_t)(K - 8) * S;   // fast iff 4S <= depth <= (K-4)S
+    const uint32_t fast_lo = wb + 4 * S;
     if (e > b) {
         int64_t gs = (int64_t)((e - 1) & ~15ull);
         const int64_t glo = (int64_t)(b & ~15ull);
-        Group<Code> cur;
+        Group<Code> cur, nxt;
         cur.load(codes + gs);
+        if (WIDE && gs - 16 >= glo) nxt.load(codes + gs - 16);
+        if constexpr (WIDE) {
+            stage(cur, gs, 0);
+            cp_async_commit();
+        }
         for (; gs >= glo; gs -= 16) {
-            Group<Code> nxt;
-            if (gs - 16 >= glo) nxt.load(codes + gs - 16);
+            Group<Code> nxt2;                 // upper trees look two groups ahead
+            if constexpr (WIDE) {
+                if (gs - 32 >= glo) nxt2.load(codes + gs - 32);
+            } else {
+                if (gs - 16 >= glo) nxt2.load(codes + gs - 16);
+            }
+            if constexpr (WIDE) {
+                // Copies for the next group overlap this group's work.
+                if (gs - 16 >= glo) stage(nxt, gs - 16, buf ^ 1);
+                cp_async_commit();
+                cp_async_wait1();
+            }
             const bool full = (uint64_t)gs >= b && (uint64_t)gs + 16 <= e;
+            if constexpr (!WIDE) {
+                if (full) {
+                    int q = 3;
+                    for (;;) {
+                        q = group_u8<S>(tos, t, q, cur.w, tb, d0, fast_lo, fast_span);
+                        if (q < 0) break;
+                        rebalance();
+                        if (fault) break;
+                        if ((t - fast_lo) <= fast_span) continue;     // runnable after all
+                        // Shallow stack (nothing spilled): this word with checks.
+                        if (q < 3) prev = Group<Code>::code(cur.sub(q + 1), 0);
+                        const uint32_t v = cur.sub(q);
+#pragma unroll
+                        for (int k = 3; k >= 0; --k) step_checked(Group<Code>::code(v, k));
+                        if (fault || --q < 0) break;
+                    }
+                    prev = cur.first();
+                    if (fault) break;
+                    cur = nxt2;
+                    continue;
+                }
+            }
 #pragma unroll 1
             for (int q = 3; q >= 0; --q) {
                 typename Group<Code>::Sub v = cur.sub(q);
                 if (WIDE) v = Group<Code>::uniform(v, mask);
-                bool fast = full && (t - wb - 4 * S) <= fast_span;
+                bool fast = full && (t - fast_lo) <= fast_span;
                 if (!fast) {
                     rebalance();
                     if (fault) break;
-                    fast = full && (t - wb - 4 * S) <= fast_span;
+                    fast = full && (t - fast_lo) <= fast_span;
                 }
                 if (fast) {
-                    if constexpr (WIDE) {
 #pragma unroll
-                        for (int k = 3; k >= 0; --k) step_fast(Group<Code>::code(v, k));
-                    } else {
-                        fast4_u8<S>(tos, t, v, tb, d0);
+                    for (int k = 3; k >= 0; --k) {
+                        jcur = 4 * q + k;
+                        step_fast(Group<Code>::code(v, k));
                     }
                     prev = Group<Code>::code(v, 0);
                 } else if (full) {
 #pragma unroll
-                    for (int k = 3; k >= 0; --k) step_checked(Group<Code>::code(v, k));
+                    for (int k = 3; k >= 0; --k) {
+                        jcur = 4 * q + k;
+                        step_checked(Group<Code>::code(v, k));
+                    }
                 } else {
 #pragma unroll
                     for (int k = 3; k >= 0; --k) {
                         const uint64_t pos = (uint64_t)gs + 4 * q + k;
+                        jcur = 4 * q + k;
                         if (pos >= b && pos < e) step_checked(Group<Code>::code(v, k));
                     }
                 }
                 if (fault) break;
             }
             if (fault) break;
-            if (gs - 16 >= glo) nxt.prefetch_values(P.pt_in, LANES, lane);
-            cur = nxt;
+            if constexpr (WIDE) {
+                cur = nxt;
+                nxt = nxt2;
+                buf ^= 1;
+            } else {
+                cur = nxt2;
+            }
         }
+        if constexpr (WIDE) cp_async_wait0();   // staging is idle before the next item
     } else if (is_final) {
         fault |= kErrMalformed;
     }
@@ -401,6 +496,8 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr uint32_t S = LANES * sizeof(float2);
     const uint32_t win0 = kLeafRows * S;                    // first window (bytes)
+    // Upper-tree kernels: two 16-entry staging buffers per warp after the windows.
+    const uint32_t stage0 = win0 + (uint32_t)nwarps * P.window * S;
 
     // Leaf table: row 0 is x (per lane, two cases), row r >= 1 constant r-1.
     for (int i = threadIdx.x; i < (int)(kLeafRows * LANES); i += blockDim.x) {
@@ -435,13 +532,16 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
             area = P.spill + it.spill_off * LANES;
             cap = it.spill_cap;
         }
-        eval_item<LANES, Code, WIDE>(P, it, sbase + win_off, sbase, errs, area, cap, lane, mask, y0, y1);
+        eval_item<LANES, Code, WIDE>(P, it, sbase + win_off, sbase,
+                                     sbase + stage0 + (uint32_t)warp * 32 * S + lane * 8u, errs, area,
+                                     cap, lane, mask, y0, y1);
     }
 }
 
-size_t eval_smem_bytes(int lanes, int warps, int window)
+size_t eval_smem_bytes(int lanes, int warps, int window, bool wide)
 {
-    return (size_t)kLeafRows * lanes * sizeof(float2) + (size_t)warps * window * lanes * sizeof(float2);
+    return (size_t)kLeafRows * lanes * sizeof(float2) +
+           (size_t)warps * (window + (wide ? 32 : 0)) * lanes * sizeof(float2);
 }
 
 template <int LANES>

@@ -95,7 +95,7 @@ struct ExtentQuery {
 };
 
 // Launchers (defined in the .cu files; return the launch's error).
-size_t eval_smem_bytes(int lanes, int warps, int window);
+size_t eval_smem_bytes(int lanes, int warps, int window, bool wide);
 cudaError_t eval_prepare(int lanes, bool wide, size_t smem);
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
                         size_t smem, cudaStream_t s);
