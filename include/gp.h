@@ -115,6 +115,11 @@ gp_status gp_evaluate(gp_population *pop, void *cuda_stream);
 gp_status gp_evaluate_ex(gp_population *pop, const gp_eval_options *opt, void *cuda_stream);
 
 /* Wait for the last gp_evaluate of `pop` and copy results to the host.
+ * gp_evaluate splits medium trees into chunks whose upper-tree fragments
+ * use fixed-size slots; a tree whose fragments did not fit (very wide
+ * shapes) is queued on the device and evaluated again here, through planned
+ * upper-tree levels, before results are copied.  Device-side results
+ * (gp_population_get_info) are complete once gp_fitness has returned.
  * fitness: [n_trees] MAE (required); case_values: [n_trees * n_cases] per-case
  * outputs or NULL; hits: [n_trees] or NULL.
  * Errors: GP_EINVAL (not evaluated yet), GP_EMALFORMED / GP_ECUDA (a device
@@ -143,10 +148,12 @@ const char *gp_status_string(gp_status st);
 
 /* Shape of the last gp_evaluate of a population: evaluation levels (1 when
  * no tree was split into chunks), work items over all levels, upper-tree
- * codes and value-buffer entries created by chunked trees. */
+ * codes and value-buffer entries created by planned levels, and trees that
+ * gp_fitness evaluated again through planned levels because their chunk
+ * fragments did not fit the fixed per-chunk slots. */
 typedef struct gp_eval_stats {
     uint32_t levels;
-    uint32_t pad;
+    uint32_t redone;           /* trees re-evaluated through planned levels */
     uint64_t items;
     uint64_t upper_codes;
     uint64_t value_entries;

@@ -137,6 +137,12 @@ cudaError_t prepare_eval_once(int lanes, bool wide, size_t smem)
 
 // ---------------------------------------------------------------- population
 
+struct EvalCfg {
+    uint32_t C = 0, W = 0, K = 0, Wu = 0;  // chunk, warps (level 0 / upper), window
+    int lanes = 0, sms = 0;
+    size_t smem = 0, smem_u = 0;
+};
+
 struct gp_population {
     int device = 0;
     cudaStream_t stream = nullptr;          // stream of the last call
@@ -156,8 +162,11 @@ struct gp_population {
     float *d_x = nullptr, *d_y = nullptr, *d_c = nullptr;
     float *d_fitness = nullptr, *d_values = nullptr;
     uint32_t *d_hits = nullptr, *d_err = nullptr;
+    uint32_t *d_redo = nullptr;              // [1 + n_trees] trees to evaluate again
     cudaEvent_t ev = nullptr;
     bool evaluated = false;
+    bool redo_pending = false;
+    EvalCfg cfg{};
     gp_eval_stats stats{};
 };
 
@@ -180,6 +189,8 @@ gp_status alloc_population(gp_population *P, cudaStream_t s)
     CK(P->mem.alloc((void **)&P->d_values, sizeof(float) * ((uint64_t)P->n_trees * P->n_cases + 1), s));
     CK(P->mem.alloc((void **)&P->d_hits, sizeof(uint32_t) * (P->n_trees + 1), s));
     CK(P->mem.alloc((void **)&P->d_err, sizeof(uint32_t) * 4, s));
+    CK(P->mem.alloc((void **)&P->d_redo, sizeof(uint32_t) * (P->n_trees + 1), s));
+    CK(cudaMemsetAsync(P->d_redo, 0, sizeof(uint32_t), s));
     CK(P->mem.alloc((void **)&P->d_x, sizeof(float) * 2 * P->lanes, s));
     CK(P->mem.alloc((void **)&P->d_y, sizeof(float) * 2 * P->lanes, s));
     CK(P->mem.alloc((void **)&P->d_c, sizeof(float) * (P->n_consts + 1), s));
@@ -450,48 +461,72 @@ void gp_destroy_population(gp_population *P) { destroy(P); }
 
 gp_status gp_evaluate(gp_population *P, void *cuda_stream) { return gp_evaluate_ex(P, nullptr, cuda_stream); }
 
-gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cuda_stream)
+}  // extern "C"
+
+namespace {
+
+// Medium trees (more than one chunk, at most kFuseMaxChunks) are evaluated
+// without a planning pass: every chunk right-aligns its upper-tree fragment
+// in a slot of C codes and keeps up to kFusePt value entries per slot; one
+// "rope" item per tree then walks the slots in a second launch.
+constexpr uint32_t kFuseMaxChunks = 32;
+
+uint32_t fuse_pt_cap(uint32_t C) { return std::max<uint32_t>(64, C / 16); }
+
+gp_status eval_config(const gp_population *P, const gp_eval_options *opt, EvalCfg *cfg)
 {
-    if (!P) return GP_EINVAL;
-    DeviceGuard dg(P->device);
-    cudaStream_t s = Stream(cuda_stream).s;
-    P->stream = s;
-    P->stats = gp_eval_stats{};
-    if (P->n_trees == 0) {
-        CK(cudaEventRecord(P->ev, s));
-        P->evaluated = true;
-        return GP_OK;
-    }
-    uint32_t C = opt && opt->chunk_nodes ? opt->chunk_nodes : 4096;
-    uint32_t W = opt && opt->warps_per_cta ? opt->warps_per_cta : 32;
-    uint32_t K = opt && opt->window_entries ? opt->window_entries : 32;
-    if (C % 16 || C < 64 || C > (1u << 24) || W < 1 || W > 32 || K < 16 || K % 2 || K > 1024)
+    EvalCfg c{};
+    c.C = opt && opt->chunk_nodes ? opt->chunk_nodes : 4096;
+    c.W = opt && opt->warps_per_cta ? opt->warps_per_cta : 32;
+    c.K = opt && opt->window_entries ? opt->window_entries : 32;
+    if (c.C % 16 || c.C < 64 || c.C > (1u << 24) || c.W < 1 || c.W > 32 || c.K < 16 || c.K % 2 ||
+        c.K > 1024)
         return GP_EINVAL;
-    const int lanes = (int)P->lanes;
-    const int sms = sm_count(P->device);
+    c.lanes = (int)P->lanes;
+    c.sms = sm_count(P->device);
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     if (!(opt && opt->warps_per_cta))        // as many warps as shared memory holds
-        while (W > 1 && eval_smem_bytes(lanes, (int)W, (int)K, false) > (size_t)maxsm) --W;
+        while (c.W > 1 && eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false) > (size_t)maxsm) --c.W;
     // Upper levels (32-bit codes) run at most 16 warps per SM, with staging.
-    uint32_t Wu = std::min<uint32_t>(W, 16);
-    while (Wu > 1 && eval_smem_bytes(lanes, (int)Wu, (int)K, true) > (size_t)maxsm) --Wu;
-    const size_t smem = eval_smem_bytes(lanes, (int)W, (int)K, false);
-    const size_t smem_u = eval_smem_bytes(lanes, (int)Wu, (int)K, true);
-    if (smem > (size_t)maxsm || smem_u > (size_t)maxsm) return GP_EINVAL;
-    CK(prepare_eval_once(lanes, false, smem));
-    CK(prepare_eval_once(lanes, true, smem_u));
-    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
+    c.Wu = std::min<uint32_t>(c.W, 16);
+    while (c.Wu > 1 && eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.K, true) > (size_t)maxsm) --c.Wu;
+    c.smem = eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false);
+    c.smem_u = eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.K, true);
+    if (c.smem > (size_t)maxsm || c.smem_u > (size_t)maxsm) return GP_EINVAL;
+    *cfg = c;
+    return GP_OK;
+}
 
+// Evaluate the given trees (all enqueued on s).  Small trees are one final
+// item; medium trees are fused chunks plus a rope item (when allowed);
+// large trees go through planned upper-tree levels, which synchronise once
+// per level to size the next one.
+gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const EvalCfg &cfg,
+                     bool allow_fused, cudaStream_t s)
+{
+    const uint32_t C = cfg.C, K = cfg.K;
+    const int lanes = cfg.lanes, sms = cfg.sms;
+    CK(prepare_eval_once(lanes, false, cfg.smem));
+    CK(prepare_eval_once(lanes, true, cfg.smem_u));
     DevBufs ws;
     auto body = [&]() -> gp_status {
-        // ---- level 0 items: whole small trees, chunks of large trees
+        std::vector<uint32_t> small, medium, big;
+        for (uint32_t t : trees) {
+            const uint64_t n = P->h_size[t];
+            if (n <= C) small.push_back(t);
+            else if (allow_fused && n <= (uint64_t)kFuseMaxChunks * C) medium.push_back(t);
+            else big.push_back(t);
+        }
+        auto by_size = [&](uint32_t a, uint32_t b) { return P->h_size[a] > P->h_size[b]; };
+        std::stable_sort(small.begin(), small.end(), by_size);
+        std::stable_sort(medium.begin(), medium.end(), by_size);
+
+        // ---- level 0: planned chunks of large trees, fused chunks of medium
+        // trees (largest first), whole small trees (largest first)
         std::vector<EvalItem> items;
-        std::vector<uint32_t> big;                  // trees cut into chunks
-        std::vector<uint32_t> first_chunk;          // per big tree: first fragment item
-        for (uint32_t t = 0; t < P->n_trees; ++t) {
-            if (P->h_size[t] <= C) continue;
-            big.push_back(t);
+        std::vector<uint32_t> first_chunk;          // per large tree: first fragment item
+        for (uint32_t t : big) {
             first_chunk.push_back((uint32_t)items.size());
             for (uint64_t b = 0; b < P->h_size[t]; b += C) {
                 EvalItem it{};
@@ -504,28 +539,58 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
         }
         first_chunk.push_back((uint32_t)items.size());
         const uint32_t n_frag0 = (uint32_t)items.size();
-        {
-            std::vector<uint32_t> small;
-            for (uint32_t t = 0; t < P->n_trees; ++t)
-                if (P->h_size[t] <= C) small.push_back(t);
-            std::stable_sort(small.begin(), small.end(),
-                             [&](uint32_t a, uint32_t b) { return P->h_size[a] > P->h_size[b]; });
-            for (uint32_t t : small) {
+        std::vector<EvalItem> ropes;
+        uint64_t slots = 0;
+        for (uint32_t t : medium) {
+            const uint32_t m = (uint32_t)((P->h_size[t] + C - 1) / C);
+            for (uint32_t j = 0; j < m; ++j) {
                 EvalItem it{};
-                it.begin = P->h_start[t];
-                it.end = P->h_start[t] + P->h_size[t];
+                it.begin = P->h_start[t] + (uint64_t)j * C;
+                it.end = P->h_start[t] + std::min<uint64_t>(P->h_size[t], (uint64_t)(j + 1) * C);
                 it.tree = t;
-                it.flags = kItemFinal;
+                it.flags = kItemFused;
+                it.frag_off = slots + j;
+                it.pt_base = slots;
+                it.frag_len = m;
                 it.spill_off = kNoSpill;
                 items.push_back(it);
             }
+            EvalItem r{};
+            r.tree = t;
+            r.flags = kItemFinal | kItemRope;
+            r.pt_base = slots;
+            r.frag_len = m;
+            r.spill_off = kNoSpill;
+            ropes.push_back(r);
+            slots += m;
+        }
+        for (uint32_t t : small) {
+            EvalItem it{};
+            it.begin = P->h_start[t];
+            it.end = P->h_start[t] + P->h_size[t];
+            it.tree = t;
+            it.flags = kItemFinal;
+            it.spill_off = kNoSpill;
+            items.push_back(it);
         }
 
-        const uint64_t warps_total = (uint64_t)sms * W;   // >= warps of any level
-        const uint64_t spill_per_warp = C;               // an item of <= C codes never holds more
+        const uint64_t warps_total = (uint64_t)sms * cfg.W;   // >= warps of any level
+        const uint64_t spill_per_warp = C;                    // a chunk never holds more
         uint32_t *d_counter;
         CK(ws.alloc((void **)&d_counter, sizeof(uint32_t) * 64, s));
         CK(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t) * 64, s));
+        // fused slots
+        const uint32_t pt_cap = fuse_pt_cap(C);
+        uint32_t *fz_codes = nullptr, *fz_len = nullptr, *fz_over = nullptr;
+        float2 *fz_pt = nullptr;
+        if (slots) {
+            CK(ws.alloc((void **)&fz_codes, sizeof(uint32_t) * (slots * C + 32), s));
+            CK(ws.alloc((void **)&fz_pt, sizeof(float2) * (slots * pt_cap * lanes + 1), s));
+            CK(ws.alloc((void **)&fz_len, sizeof(uint32_t) * slots, s));
+            CK(ws.alloc((void **)&fz_over, sizeof(uint32_t) * P->n_trees, s));
+            CK(cudaMemsetAsync(fz_over, 0, sizeof(uint32_t) * P->n_trees, s));
+            P->redo_pending = true;
+        }
 
         // level state
         const void *codes = P->d_arena;
@@ -541,6 +606,7 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
 
         for (;;) {
             if (level >= 63) return GP_EINVAL;
+            if (cur_items.empty()) break;
             EvalItem *d_items;
             CK(ws.alloc((void **)&d_items, sizeof(EvalItem) * cur_items.size(), s));
             CK(cudaMemcpyAsync(d_items, cur_items.data(), sizeof(EvalItem) * cur_items.size(),
@@ -571,7 +637,8 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
                 if (tot[1] + kPtCode0 >= 0xffffffffull) return GP_ENOMEM;
                 if (tot[2] > spill_per_warp) return GP_EINVAL;   // cannot happen: chunks <= C
                 CK(ws.alloc((void **)&u_next, sizeof(uint32_t) * (round_up(tot[0], 16) + 32), s));
-                CK(cudaMemsetAsync(u_next + tot[0], 0, sizeof(uint32_t) * (round_up(tot[0], 16) + 32 - tot[0]), s));
+                CK(cudaMemsetAsync(u_next + tot[0], 0,
+                                   sizeof(uint32_t) * (round_up(tot[0], 16) + 32 - tot[0]), s));
                 CK(ws.alloc((void **)&pt_next, sizeof(float2) * (tot[1] * lanes + 1), s));
                 P->stats.upper_codes += tot[0];
                 P->stats.value_entries += tot[1];
@@ -579,7 +646,7 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
             // dedicated spill areas for oversized final items
             uint64_t dedicated = 0;
             for (auto &it : cur_items) {
-                if ((it.flags & kItemFinal) && it.end - it.begin > spill_per_warp) {
+                if ((it.flags & kItemFinal) && !(it.flags & kItemRope) && it.end - it.begin > spill_per_warp) {
                     it.spill_off = warps_total * spill_per_warp + dedicated;
                     it.spill_cap = it.end - it.begin;
                     dedicated += it.spill_cap;
@@ -617,42 +684,50 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
             p.spill = d_spill;
             p.spill_per_warp = spill_per_warp;
             p.err = P->d_err;
+            p.fz_codes = fz_codes;
+            p.fz_pt = fz_pt;
+            p.fz_len = fz_len;
+            p.fz_over = fz_over;
+            p.fz_redo = P->d_redo;
+            p.fz_cap_codes = C;
+            p.fz_cap_pt = pt_cap;
             {
                 ProfScope ps(wide ? GP_KERNEL_EVAL_UPPER : GP_KERNEL_EVAL, s);
-                CK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s));
+                CK(launch_eval(lanes, wide, p, sms, (int)(wide ? cfg.Wu : cfg.W), wide ? cfg.smem_u : cfg.smem, s));
             }
             P->stats.levels = level + 1;
             P->stats.items += cur_items.size();
-            if (!n_frag) break;
 
-            // ---- next level: one upper tree per big tree
+            // ---- next level: one upper tree per large tree, plus the ropes
             std::vector<EvalItem> next;
             std::vector<uint32_t> nb, nf;
             std::vector<uint64_t> nprev;
             std::vector<EvalItem> finals;
-            for (size_t k = 0; k < cur_big.size(); ++k) {
-                const uint32_t t = cur_big[k];
-                const uint64_t ub = frag_off[cur_first[k]], ue = frag_off[cur_first[k + 1]];
-                const uint64_t len = ue - ub;
-                if (len <= C || len * 2 > prev_len[k]) {
-                    EvalItem it{};
-                    it.begin = ub;
-                    it.end = ue;
-                    it.tree = t;
-                    it.flags = kItemFinal;
-                    it.spill_off = kNoSpill;
-                    finals.push_back(it);
-                } else {
-                    nb.push_back(t);
-                    nf.push_back((uint32_t)next.size());
-                    nprev.push_back(len);
-                    for (uint64_t b = ub; b < ue; b += C) {
+            if (n_frag) {
+                for (size_t k = 0; k < cur_big.size(); ++k) {
+                    const uint32_t t = cur_big[k];
+                    const uint64_t ub = frag_off[cur_first[k]], ue = frag_off[cur_first[k + 1]];
+                    const uint64_t len = ue - ub;
+                    if (len <= C || len * 2 > prev_len[k]) {
                         EvalItem it{};
-                        it.begin = b;
-                        it.end = std::min<uint64_t>(ue, b + C);
+                        it.begin = ub;
+                        it.end = ue;
                         it.tree = t;
+                        it.flags = kItemFinal;
                         it.spill_off = kNoSpill;
-                        next.push_back(it);
+                        finals.push_back(it);
+                    } else {
+                        nb.push_back(t);
+                        nf.push_back((uint32_t)next.size());
+                        nprev.push_back(len);
+                        for (uint64_t b = ub; b < ue; b += C) {
+                            EvalItem it{};
+                            it.begin = b;
+                            it.end = std::min<uint64_t>(ue, b + C);
+                            it.tree = t;
+                            it.spill_off = kNoSpill;
+                            next.push_back(it);
+                        }
                     }
                 }
             }
@@ -661,6 +736,9 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
             std::stable_sort(finals.begin(), finals.end(), [](const EvalItem &a, const EvalItem &b) {
                 return a.end - a.begin > b.end - b.begin;
             });
+            // ropes join the first upper level, largest trees first
+            next.insert(next.end(), ropes.begin(), ropes.end());
+            ropes.clear();
             next.insert(next.end(), finals.begin(), finals.end());
             cur_items = std::move(next);
             cur_big = std::move(nb);
@@ -675,18 +753,64 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
     };
     gp_status st = body();
     ws.release(s);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cuda_stream)
+{
+    if (!P) return GP_EINVAL;
+    DeviceGuard dg(P->device);
+    cudaStream_t s = Stream(cuda_stream).s;
+    P->stream = s;
+    P->stats = gp_eval_stats{};
+    P->redo_pending = false;
+    if (P->n_trees == 0) {
+        CK(cudaEventRecord(P->ev, s));
+        P->evaluated = true;
+        return GP_OK;
+    }
+    EvalCfg cfg;
+    gp_status st = eval_config(P, opt, &cfg);
+    if (st) return st;
+    P->cfg = cfg;
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
+    CK(cudaMemsetAsync(P->d_redo, 0, sizeof(uint32_t), s));
+    std::vector<uint32_t> all(P->n_trees);
+    for (uint32_t t = 0; t < P->n_trees; ++t) all[t] = t;
+    st = eval_trees(P, all, cfg, true, s);
     if (st) return st;
     CK(cudaEventRecord(P->ev, s));
     P->evaluated = true;
     return GP_OK;
 }
 
-gp_status gp_fitness(const gp_population *P, float *fitness, float *case_values, uint32_t *hits)
+gp_status gp_fitness(const gp_population *Pc, float *fitness, float *case_values, uint32_t *hits)
 {
+    gp_population *P = const_cast<gp_population *>(Pc);
     if (!P || (!fitness && P->n_trees)) return GP_EINVAL;
     if (!P->evaluated) return GP_EINVAL;
     DeviceGuard dg(P->device);
     CK(cudaEventSynchronize(P->ev));
+    if (P->redo_pending) {
+        // Trees whose chunk fragments did not fit their slots are evaluated
+        // again through planned upper-tree levels (rare: very wide shapes).
+        P->redo_pending = false;
+        uint32_t n = 0;
+        CK(cudaMemcpy(&n, P->d_redo, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (n) {
+            std::vector<uint32_t> redo(n);
+            CK(cudaMemcpy(redo.data(), P->d_redo + 1, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+            std::sort(redo.begin(), redo.end());
+            gp_status st = eval_trees(P, redo, P->cfg, false, P->stream);
+            if (st) return st;
+            CK(cudaStreamSynchronize(P->stream));
+            P->stats.redone = n;
+        }
+    }
     uint32_t err = 0;
     CK(cudaMemcpy(&err, P->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (err & kErrMalformed) return GP_EMALFORMED;

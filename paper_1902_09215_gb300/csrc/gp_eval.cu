@@ -221,10 +221,12 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
                                           uint32_t mask, float y0, float y1)
 {
     constexpr uint32_t S = LANES * sizeof(float2);          // bytes per stack entry / table row
-    const Code *codes = static_cast<const Code *>(P.codes);
+    const Code *codes0 = static_cast<const Code *>(P.codes);
     const int K = (int)P.window;
     const float d0 = P.div0;
     const bool is_final = (it.flags & kItemFinal) != 0;
+    const bool fused = (it.flags & kItemFused) != 0;      // chunk of a medium tree
+    const bool rope = WIDE && (it.flags & kItemRope) != 0; // final over a medium tree's slots
     const uint32_t tb = tbl_sa + lane * 8u - 4u * S;        // + code * S = leaf table row
     const uint32_t wb = win_sa + lane * 8u;                 // this lane's column of the window
 
@@ -232,8 +234,15 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
     bool have = false;                    // tos holds a value of this item
     uint32_t t = wb;                      // next free window entry (shared address)
     uint64_t g = 0;                       // entries spilled below the window
-    uint64_t ecur = it.frag_off + it.frag_len;   // fragment codes are written backwards
-    uint64_t ptn = it.pt_base;
+    // Fragment output: planned items write at planned offsets; fused chunks
+    // right-align their codes in their own slot and number their value
+    // entries from the slot's first entry.
+    const uint64_t e_lo = fused ? it.frag_off * P.fz_cap_codes : it.frag_off;
+    uint64_t ecur = fused ? e_lo + P.fz_cap_codes : it.frag_off + it.frag_len;
+    const uint64_t pt_lo = fused ? it.frag_off * P.fz_cap_pt : it.pt_base;
+    const uint64_t pt_hi = fused ? pt_lo + P.fz_cap_pt : it.pt_base + it.pt_cnt;
+    uint64_t ptn = pt_lo;
+    bool pt_full = false;                 // a fused chunk ran out of value slots
     uint32_t prev = 0xFFFFFFFFu;          // code at the position right of the current one
     uint32_t fault = 0;                   // kErr* bits; any fault ends the item
     const uint32_t dmax = (uint32_t)(K - 4) * S;   // room for four pushes below this
@@ -245,6 +254,14 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
         if (WIDE && c >= kPtCode0) return lds64(stage_sa + (buf * 16 + jcur) * S);
         return lds64(tb + c * S);
     };
+    if (rope && P.fz_over[it.tree]) {
+        // A chunk of this tree ran out of value slots: queue the tree for a
+        // re-evaluation through planned upper-tree levels.
+        if (lane == 0) P.fz_redo[1 + atomicAdd(P.fz_redo, 1u)] = it.tree;
+        return;
+    }
+    const float2 *pt_src = P.pt_in;       // value entries read by the current range
+    uint64_t rb = it.begin, re = it.end;  // the current range
     auto stage = [&](const Group<Code> &grp, int64_t gbase, uint32_t into) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -253,22 +270,27 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
             for (int k = 0; k < 4; ++k) {
                 const uint32_t c = Group<Code>::code(v, k);
                 const uint64_t pos = (uint64_t)gbase + 4 * q + k;
-                if (pos >= it.begin && pos < it.end && c >= kPtCode0)
+                if (pos >= rb && pos < re && c >= kPtCode0)
                     cp_async8(stage_sa + (into * 16 + 4 * q + k) * S,
-                              P.pt_in + (uint64_t)(c - kPtCode0) * LANES + lane);
+                              pt_src + (uint64_t)(c - kPtCode0) * LANES + lane);
             }
         }
     };
-    // Fragment output stays inside the slot the plan reserved for it.
+    // Fragment output stays inside the slot reserved for it.
     auto emit = [&](uint32_t code) {
-        if (ecur == it.frag_off) { fault |= kErrPlan; return; }
+        if (ecur == e_lo) { fault |= kErrPlan; return; }
         --ecur;
-        if (lane == 0) P.u_out[ecur] = code;
+        if (lane == 0) (fused ? P.fz_codes : P.u_out)[ecur] = code;
     };
     auto new_pt = [&](uint64_t v) -> uint32_t {
-        if (ptn >= it.pt_base + it.pt_cnt) { fault |= kErrPlan; return kPtCode0; }
-        P.pt_out[ptn * LANES + lane] = upk(v);
-        return (uint32_t)(kPtCode0 + ptn++);
+        if (ptn >= pt_hi) {
+            if (fused) pt_full = true;    // the tree is re-evaluated without chunk slots
+            else fault |= kErrPlan;
+            return kPtCode0;
+        }
+        (fused ? P.fz_pt : P.pt_out)[ptn * LANES + lane] = upk(v);
+        // planned fragments number entries globally, fused chunks per slot
+        return (uint32_t)(kPtCode0 + (fused ? ptn++ - pt_lo : ptn++));
     };
     // Keep room for four pushes in the window, and four pops whenever
     // entries are spilled; the window is refilled / spilled half-way.
@@ -343,9 +365,21 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
         prev = c;
     };
 
-    const uint64_t b = it.begin, e = it.end;
     const uint32_t fast_span = (uint32_t)(K - 8) * S;   // fast iff 4S <= depth <= (K-4)S
     const uint32_t fast_lo = wb + 4 * S;
+    // A rope item walks its tree's chunk fragments from the last to the
+    // first, each right to left, on one continuous stack.
+    const uint32_t nranges = rope ? it.frag_len : 1;
+    for (uint32_t r = 0; r < nranges && !fault; ++r) {
+    const Code *codes = codes0;
+    if (rope) {
+        const uint64_t slot = it.pt_base + (nranges - 1 - r);
+        codes = reinterpret_cast<const Code *>(P.fz_codes + slot * P.fz_cap_codes);
+        re = P.fz_cap_codes;
+        rb = re - P.fz_len[slot];
+        pt_src = P.fz_pt + slot * P.fz_cap_pt * LANES;
+    }
+    const uint64_t b = rb, e = re;
     if (e > b) {
         int64_t gs = (int64_t)((e - 1) & ~15ull);
         const int64_t glo = (int64_t)(b & ~15ull);
@@ -353,6 +387,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
         cur.load(codes + gs);
         if (WIDE && gs - 16 >= glo) nxt.load(codes + gs - 16);
         if constexpr (WIDE) {
+            buf = 0;                          // each range starts its own pipeline
             stage(cur, gs, 0);
             cp_async_commit();
         }
@@ -435,7 +470,9 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
             }
         }
         if constexpr (WIDE) cp_async_wait0();   // staging is idle before the next item
-    } else if (is_final) {
+    }
+    }
+    if (!rope && it.end <= it.begin && is_final) {
         fault |= kErrMalformed;
     }
     const int sp = (int)((t - wb) / S);
@@ -444,6 +481,10 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
         const uint32_t tr = it.tree;
         const uint32_t nc = P.n_cases;
         const bool ok = !fault && have && sp == 0 && g == 0;
+        if (rope && fault) {              // e.g. deeper than the spill area: redo as planned
+            if (lane == 0) P.fz_redo[1 + atomicAdd(P.fz_redo, 1u)] = tr;
+            return;
+        }
         if (!ok) {
             if (lane == 0) {
                 atomicOr(P.err, fault ? fault : kErrMalformed);
@@ -482,6 +523,14 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
     for (uint64_t i = 0; i < g; ++i) emit(new_pt(pk(spill[i * LANES + lane])));
     for (int i = 0; i < sp; ++i) emit(new_pt(lds64(wb + i * S)));
     if (have) emit(new_pt(tos));
+    if (fused) {
+        if (lane == 0) {
+            P.fz_len[it.frag_off] = (uint32_t)(e_lo + P.fz_cap_codes - ecur);
+            if (pt_full) P.fz_over[it.tree] = 1u;
+        }
+        if (fault && lane == 0) atomicOr(P.err, kErrPlan);
+        return;
+    }
     if (fault || ecur != it.frag_off || ptn != it.pt_base + it.pt_cnt) {
         if (lane == 0) atomicOr(P.err, kErrPlan);
     }

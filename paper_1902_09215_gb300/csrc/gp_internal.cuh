@@ -9,6 +9,8 @@ constexpr uint32_t kMaxCases = 64;
 constexpr uint32_t kLeafRows = 128;     // codes 4 ('x') .. 131 (constant 126)
 constexpr uint32_t kPtCode0 = 132;      // upper-tree code >= 132: value-buffer entry code-132
 constexpr uint32_t kItemFinal = 1u;     // item covers a whole (upper) tree: produce fitness
+constexpr uint32_t kItemFused = 2u;     // chunk of a medium tree, finished by its last chunk
+constexpr uint32_t kItemRope = 4u;      // final item over a medium tree's chunk fragments
 constexpr uint64_t kNoSpill = ~0ull;
 
 // Device error word bits.
@@ -23,6 +25,10 @@ __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { re
 // A final item covers a whole tree (level 0) or a whole upper tree and
 // yields the tree's outputs; a fragment item covers one chunk of a larger
 // tree and writes that chunk's part of the next level's upper tree.
+// A fused item is a chunk of a medium tree: it writes its fragment into its
+// own slot (frag_off = slot, pt_base = the tree's first slot, frag_len = the
+// tree's chunk count) and the chunk that completes the tree evaluates the
+// tree's upper tree from all its slots.
 struct alignas(16) EvalItem {
     uint64_t begin, end;     // code positions [begin, end)
     uint64_t frag_off;       // fragment: upper-tree position of its first code
@@ -71,6 +77,15 @@ struct EvalParams {
     float2 *spill;                 // spill memory, [entries][lanes] float2
     uint64_t spill_per_warp;       // entries per resident warp
     uint32_t *err;
+    // medium trees (fused items)
+    uint32_t *fz_codes;            // [slots][fz_cap_codes] fragment codes, right-aligned
+    float2 *fz_pt;                 // [slots][fz_cap_pt][lanes] value entries
+    uint32_t *fz_len;              // [slots] fragment length
+    uint32_t *fz_done;             // [n_trees] finished chunks
+    uint32_t *fz_over;             // [n_trees] a chunk ran out of value slots
+    uint32_t *fz_redo;             // [1 + n_trees]: count, then trees to re-evaluate
+    uint32_t fz_cap_codes;
+    uint32_t fz_cap_pt;
 };
 
 struct XoChild {                   // child = M[0,i) ++ D[j,e_d) ++ M[e_m,n_m)

@@ -51,7 +51,7 @@ class gp_population_info(C.Structure):
 
 
 class gp_eval_stats(C.Structure):
-    _fields_ = [("levels", C.c_uint32), ("pad", C.c_uint32), ("items", C.c_uint64),
+    _fields_ = [("levels", C.c_uint32), ("redone", C.c_uint32), ("items", C.c_uint64),
                 ("upper_codes", C.c_uint64), ("value_entries", C.c_uint64)]
 
 
@@ -242,7 +242,7 @@ def gp_destroy_population(pop: Population):
 def gp_eval_stats_get(pop: Population) -> dict:
     s = gp_eval_stats()
     _check(lib().gp_eval_stats_get(pop._h, C.byref(s)), "gp_eval_stats_get")
-    return {"levels": s.levels, "items": s.items, "upper_codes": s.upper_codes,
+    return {"levels": s.levels, "redone": s.redone, "items": s.items, "upper_codes": s.upper_codes,
             "value_entries": s.value_entries}
 
 
