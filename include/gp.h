@@ -67,6 +67,7 @@ typedef struct gp_eval_options {
     uint32_t chunk_nodes;     /* nodes per independent evaluation chunk (multiple of 16) */
     uint32_t warps_per_cta;   /* warps of the persistent evaluator per SM (1..32)        */
     uint32_t window_entries;  /* shared-memory stack entries per warp (even, >= 16)      */
+    uint32_t upper_window_entries; /* the same for upper-tree levels                    */
 } gp_eval_options;
 
 /* Device-side view of a population, for zero-copy use by the caller. */

@@ -138,7 +138,7 @@ cudaError_t prepare_eval_once(int lanes, bool wide, size_t smem)
 // ---------------------------------------------------------------- population
 
 struct EvalCfg {
-    uint32_t C = 0, W = 0, K = 0, Wu = 0;  // chunk, warps (level 0 / upper), window
+    uint32_t C = 0, W = 0, K = 0, Wu = 0, Ku = 0;  // chunk, warps and windows (level 0 / upper)
     int lanes = 0, sms = 0;
     size_t smem = 0, smem_u = 0;
 };
@@ -479,8 +479,11 @@ gp_status eval_config(const gp_population *P, const gp_eval_options *opt, EvalCf
     c.C = opt && opt->chunk_nodes ? opt->chunk_nodes : 4096;
     c.W = opt && opt->warps_per_cta ? opt->warps_per_cta : 32;
     c.K = opt && opt->window_entries ? opt->window_entries : 32;
+    // Upper trees hold many pending values (the residual subtrees of every
+    // chunk), so their window is deeper.
+    c.Ku = opt && opt->upper_window_entries ? opt->upper_window_entries : std::max<uint32_t>(c.K, 96);
     if (c.C % 16 || c.C < 64 || c.C > (1u << 24) || c.W < 1 || c.W > 32 || c.K < 16 || c.K % 2 ||
-        c.K > 1024)
+        c.K > 1024 || c.Ku < 16 || c.Ku % 2 || c.Ku > 1024)
         return GP_EINVAL;
     c.lanes = (int)P->lanes;
     c.sms = sm_count(P->device);
@@ -490,9 +493,9 @@ gp_status eval_config(const gp_population *P, const gp_eval_options *opt, EvalCf
         while (c.W > 1 && eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false) > (size_t)maxsm) --c.W;
     // Upper levels (32-bit codes) run at most 16 warps per SM, with staging.
     c.Wu = std::min<uint32_t>(c.W, 16);
-    while (c.Wu > 1 && eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.K, true) > (size_t)maxsm) --c.Wu;
+    while (c.Wu > 1 && eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true) > (size_t)maxsm) --c.Wu;
     c.smem = eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false);
-    c.smem_u = eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.K, true);
+    c.smem_u = eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true);
     if (c.smem > (size_t)maxsm || c.smem_u > (size_t)maxsm) return GP_EINVAL;
     *cfg = c;
     return GP_OK;
@@ -505,7 +508,7 @@ gp_status eval_config(const gp_population *P, const gp_eval_options *opt, EvalCf
 gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const EvalCfg &cfg,
                      bool allow_fused, cudaStream_t s)
 {
-    const uint32_t C = cfg.C, K = cfg.K;
+    const uint32_t C = cfg.C;
     const int lanes = cfg.lanes, sms = cfg.sms;
     CK(prepare_eval_once(lanes, false, cfg.smem));
     CK(prepare_eval_once(lanes, true, cfg.smem_u));
@@ -674,7 +677,7 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
             p.n_cases = P->n_cases;
             p.n_consts = P->n_consts;
             p.div0 = P->div0;
-            p.window = K;
+            p.window = wide ? cfg.Ku : cfg.K;
             p.pt_in = pt_in;
             p.pt_out = pt_next;
             p.u_out = u_next;

@@ -106,6 +106,67 @@ template <> struct Group<uint32_t> {
     __device__ __forceinline__ uint32_t first() const { return w[0].x; }
 };
 
+// Upper-tree variant of the group interpreter: one 32-bit code per operand
+// (%3 + position), leaves >= 132 read the staged value entry of their
+// position in the group (%24 + position * S), other leaves the leaf table.
+#define GP_UNODE(CREG, J, IDX)                                                   \
+    "setp.gt.u32 pl, " CREG ", 3;\n\t"                                         \
+    "@pl bra.uni LF" #IDX ";\n\t"                                              \
+    "sub.u32 %1, %1, %23;\n\t"                                                 \
+    "ld.shared.b64 v, [%1];\n\t"                                               \
+    "setp.lt.u32 p, " CREG ", 2;\n\t"                                          \
+    "@p bra.uni LO" #IDX ";\n\t"                                               \
+    "setp.eq.u32 p, " CREG ", 2;\n\t"                                          \
+    "@p bra.uni MU" #IDX ";\n\t"                                               \
+    "mov.u32 ret, " #IDX ";\n\t"                                               \
+    "bra.uni DIVR;\n"                                                          \
+    "MU" #IDX ":\n\tmul.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
+    "LO" #IDX ":\n\tsetp.eq.u32 p, " CREG ", 0;\n\t@p bra.uni AD" #IDX ";\n\t"   \
+    "sub.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"                          \
+    "AD" #IDX ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
+    "LF" #IDX ":\n\tst.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %23;\n\t"          \
+    "setp.lt.u32 p, " CREG ", 132;\n\t@p bra.uni TB" #IDX ";\n\t"              \
+    "ld.shared.b64 %0, [%24+" #J "*%23];\n\tbra.uni E" #IDX ";\n"                \
+    "TB" #IDX ":\n\tmad.lo.u32 a, " CREG ", %23, %19;\n\tld.shared.b64 %0, [a];\n" \
+    "E" #IDX ":\n\t"
+
+#define GP_UWORD(Q, C3, C2, C1, C0, J3, J2, J1, J0, I0, I1, I2, I3)              \
+    "W" #Q ":\n\tsub.u32 dd, %1, %21;\n\tsetp.gt.u32 p, dd, %22;\n\t"               \
+    "@p bra.uni X" #Q ";\n\t"                                                     \
+    GP_UNODE(C3, J3, I0) GP_UNODE(C2, J2, I1) GP_UNODE(C1, J1, I2) GP_UNODE(C0, J0, I3)
+
+template <uint32_t S>
+__device__ __forceinline__ int group_u32(uint64_t &tos, uint32_t &t, int q, const uint4 *w, uint32_t tb,
+                                         float d0, uint32_t lo, uint32_t span, uint32_t stage)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, pl;\n\t.reg .b32 a, ret, dd;\n\t.reg .b64 v;\n\t"
+        ".reg .f32 tx, ty, bx, by, qx, qy;\n\t"
+        "ENT: .branchtargets W0, W1, W2, W3;\n\t"
+        "brx.idx.uni %2, ENT;\n"
+        GP_UWORD(3, "%18", "%17", "%16", "%15", 15, 14, 13, 12, 0, 1, 2, 3)
+        GP_UWORD(2, "%14", "%13", "%12", "%11", 11, 10, 9, 8, 4, 5, 6, 7)
+        GP_UWORD(1, "%10", "%9", "%8", "%7", 7, 6, 5, 4, 8, 9, 10, 11)
+        GP_UWORD(0, "%6", "%5", "%4", "%3", 3, 2, 1, 0, 12, 13, 14, 15)
+        "mov.s32 %2, -1;\n\tbra.uni DONE;\n"
+        "X3:\n\tmov.s32 %2, 3;\n\tbra.uni DONE;\n"
+        "X2:\n\tmov.s32 %2, 2;\n\tbra.uni DONE;\n"
+        "X1:\n\tmov.s32 %2, 1;\n\tbra.uni DONE;\n"
+        "X0:\n\tmov.s32 %2, 0;\n\tbra.uni DONE;\n"
+        "DIVR:\n\tmov.b64 {tx, ty}, %0;\n\tmov.b64 {bx, by}, v;\n\t"
+        "div.rn.f32 qx, tx, bx;\n\tsetp.neu.f32 p, bx, 0f00000000;\n\tselp.f32 tx, qx, %20, p;\n\t"
+        "div.rn.f32 qy, ty, by;\n\tsetp.neu.f32 p, by, 0f00000000;\n\tselp.f32 ty, qy, %20, p;\n\t"
+        "mov.b64 %0, {tx, ty};\n\t"
+        "RET: .branchtargets E0, E1, E2, E3, E4, E5, E6, E7, E8, E9, E10, E11, E12, E13, E14, E15;\n\t"
+        "brx.idx.uni ret, RET;\n"
+        "DONE:\n\t}"
+        : "+l"(tos), "+r"(t), "+r"(q)
+        : "r"(w[0].x), "r"(w[0].y), "r"(w[0].z), "r"(w[0].w), "r"(w[1].x), "r"(w[1].y), "r"(w[1].z),
+          "r"(w[1].w), "r"(w[2].x), "r"(w[2].y), "r"(w[2].z), "r"(w[2].w), "r"(w[3].x), "r"(w[3].y),
+          "r"(w[3].z), "r"(w[3].w), "r"(tb), "f"(d0), "r"(lo), "r"(span), "n"(S), "r"(stage));
+    return q;
+}
+
 // ---------------------------------------------------------------- one item
 
 // Dynamic shared memory: the leaf table at offset 0, then one stack window
@@ -424,6 +485,33 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
                     prev = cur.first();
                     if (fault) break;
                     cur = nxt2;
+                    continue;
+                }
+            }
+            if constexpr (WIDE) {
+                if (full) {
+                    int q = 3;
+                    for (;;) {
+                        q = group_u32<S>(tos, t, q, cur.w, tb, d0, fast_lo, fast_span,
+                                         stage_sa + buf * 16 * S);
+                        if (q < 0) break;
+                        rebalance();
+                        if (fault) break;
+                        if ((t - fast_lo) <= fast_span) continue;     // runnable after all
+                        if (q < 3) prev = Group<Code>::code(cur.sub(q + 1), 0);
+                        const typename Group<Code>::Sub v = cur.sub(q);
+#pragma unroll
+                        for (int k = 3; k >= 0; --k) {
+                            jcur = 4 * q + k;
+                            step_checked(Group<Code>::code(v, k));
+                        }
+                        if (fault || --q < 0) break;
+                    }
+                    prev = cur.first();
+                    if (fault) break;
+                    cur = nxt;
+                    nxt = nxt2;
+                    buf ^= 1;
                     continue;
                 }
             }

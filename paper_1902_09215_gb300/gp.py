@@ -41,7 +41,7 @@ class gp_xo(C.Structure):
 
 class gp_eval_options(C.Structure):
     _fields_ = [("chunk_nodes", C.c_uint32), ("warps_per_cta", C.c_uint32),
-                ("window_entries", C.c_uint32)]
+                ("window_entries", C.c_uint32), ("upper_window_entries", C.c_uint32)]
 
 
 class gp_population_info(C.Structure):
@@ -193,9 +193,11 @@ def gp_crossover(parents: Population, ops, stream=None) -> Population:
     return Population(out, len(ops), parents.n_cases)
 
 
-def gp_evaluate(pop: Population, stream=None, chunk_nodes=0, warps_per_cta=0, window_entries=0):
-    if chunk_nodes or warps_per_cta or window_entries:
-        o = gp_eval_options(int(chunk_nodes), int(warps_per_cta), int(window_entries))
+def gp_evaluate(pop: Population, stream=None, chunk_nodes=0, warps_per_cta=0, window_entries=0,
+                upper_window_entries=0):
+    if chunk_nodes or warps_per_cta or window_entries or upper_window_entries:
+        o = gp_eval_options(int(chunk_nodes), int(warps_per_cta), int(window_entries),
+                            int(upper_window_entries))
         st = lib().gp_evaluate_ex(pop._h, C.byref(o), _stream(stream))
     else:
         st = lib().gp_evaluate(pop._h, _stream(stream))
