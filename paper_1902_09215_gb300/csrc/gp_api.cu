@@ -2,6 +2,7 @@
 // upper-tree level planner and kernel launches.
 #include <algorithm>
 #include <atomic>
+#include <deque>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -92,6 +93,82 @@ int lanes_for(uint32_t n_cases)
     if (n_cases <= 32) return 16;
     if (n_cases <= 48) return 24;
     return 32;
+}
+
+// Pinned host staging for the small per-call tables (work items, crossover
+// records, extent queries), so their copies are truly asynchronous.  A ring
+// of pinned bytes; each region is fenced by an event recorded after the copy
+// that reads it, and a region is reused only after its event completed.
+class PinnedRing {
+  public:
+    static PinnedRing &get() {
+        static PinnedRing r;
+        return r;
+    }
+    // Copy `bytes` from host `src` to device `dst` on stream s via the ring
+    // (falls back to a direct copy for large or unavailable staging).
+    cudaError_t h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+        if (bytes == 0) return cudaSuccess;
+        std::lock_guard<std::mutex> lk(mu_);
+        if (!base_ && !init()) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+        if (bytes > kCap / 4) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+        size_t off = (head_ + 255) & ~size_t(255);
+        if (off + bytes > kCap) off = 0;
+        // drop regions whose copies finished; wait for live ones that overlap
+        while (!live_.empty() && cudaEventQuery(live_.front().ev) == cudaSuccess) {
+            free_ev_.push_back(live_.front().ev);
+            live_.pop_front();
+        }
+        for (auto r = live_.begin(); r != live_.end();) {
+            if (r->off < off + bytes && off < r->off + r->len) {
+                cudaEventSynchronize(r->ev);
+                free_ev_.push_back(r->ev);
+                r = live_.erase(r);
+            } else {
+                ++r;
+            }
+        }
+        std::memcpy(base_ + off, src, bytes);
+        cudaError_t e = cudaMemcpyAsync(dst, base_ + off, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        cudaEvent_t ev;
+        if (!free_ev_.empty()) {
+            ev = free_ev_.back();
+            free_ev_.pop_back();
+        } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            return cudaStreamSynchronize(s);
+        }
+        cudaEventRecord(ev, s);
+        live_.push_back(Region{off, bytes, ev});
+        head_ = off + bytes;
+        return cudaSuccess;
+    }
+
+  private:
+    static constexpr size_t kCap = (size_t)64 << 20;
+    struct Region {
+        size_t off, len;
+        cudaEvent_t ev;
+    };
+    bool init() {
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, kCap, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        base_ = static_cast<char *>(p);
+        return true;
+    }
+    std::mutex mu_;
+    char *base_ = nullptr;
+    size_t head_ = 0;
+    std::deque<Region> live_;
+    std::vector<cudaEvent_t> free_ev_;
+};
+
+cudaError_t h2d(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return PinnedRing::get().h2d(dst, src, bytes, s);
 }
 
 // Device allocations freed together (stream-ordered).
@@ -194,16 +271,13 @@ gp_status alloc_population(gp_population *P, cudaStream_t s)
     CK(P->mem.alloc((void **)&P->d_x, sizeof(float) * 2 * P->lanes, s));
     CK(P->mem.alloc((void **)&P->d_y, sizeof(float) * 2 * P->lanes, s));
     CK(P->mem.alloc((void **)&P->d_c, sizeof(float) * (P->n_consts + 1), s));
-    CK(cudaMemcpyAsync(P->d_x, P->hx.data(), sizeof(float) * 2 * P->lanes, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(P->d_y, P->hy.data(), sizeof(float) * 2 * P->lanes, cudaMemcpyHostToDevice, s));
-    if (P->n_consts)
-        CK(cudaMemcpyAsync(P->d_c, P->hc.data(), sizeof(float) * P->n_consts, cudaMemcpyHostToDevice, s));
+    CK(h2d(P->d_x, P->hx.data(), sizeof(float) * 2 * P->lanes, s));
+    CK(h2d(P->d_y, P->hy.data(), sizeof(float) * 2 * P->lanes, s));
+    if (P->n_consts) CK(h2d(P->d_c, P->hc.data(), sizeof(float) * P->n_consts, s));
     CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
     if (P->n_trees) {
-        CK(cudaMemcpyAsync(P->d_start, P->h_start.data(), sizeof(uint64_t) * P->n_trees,
-                           cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(P->d_size, P->h_size.data(), sizeof(uint64_t) * P->n_trees,
-                           cudaMemcpyHostToDevice, s));
+        CK(h2d(P->d_start, P->h_start.data(), sizeof(uint64_t) * P->n_trees, s));
+        CK(h2d(P->d_size, P->h_size.data(), sizeof(uint64_t) * P->n_trees, s));
     }
     CK(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
     return GP_OK;
@@ -255,8 +329,8 @@ gp_status run_copy(const uint8_t *src, uint8_t *dst, const std::vector<XoChild> 
     XoTile *d_tiles;
     CK(tmp.alloc((void **)&d_kids, sizeof(XoChild) * kids.size(), s));
     CK(tmp.alloc((void **)&d_tiles, sizeof(XoTile) * tiles.size(), s));
-    CK(cudaMemcpyAsync(d_kids, kids.data(), sizeof(XoChild) * kids.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(XoTile) * tiles.size(), cudaMemcpyHostToDevice, s));
+    CK(h2d(d_kids, kids.data(), sizeof(XoChild) * kids.size(), s));
+    CK(h2d(d_tiles, tiles.data(), sizeof(XoTile) * tiles.size(), s));
     ProfScope ps(GP_KERNEL_COPY, s);
     CK(launch_xo_copy(src, dst, d_kids, d_tiles, (uint32_t)tiles.size(), tile, s));
     return GP_OK;
@@ -286,8 +360,8 @@ gp_status validate_population(gp_population *P, cudaStream_t s, DevBufs &tmp, bo
     CK(tmp.alloc((void **)&d_out, sizeof(ValOut) * chunks.size(), s));
     CK(tmp.alloc((void **)&d_first, sizeof(uint32_t) * first.size(), s));
     CK(tmp.alloc((void **)&d_bad, sizeof(uint32_t), s));
-    CK(cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(EvalItem) * chunks.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_first, first.data(), sizeof(uint32_t) * first.size(), cudaMemcpyHostToDevice, s));
+    CK(h2d(d_chunks, chunks.data(), sizeof(EvalItem) * chunks.size(), s));
+    CK(h2d(d_first, first.data(), sizeof(uint32_t) * first.size(), s));
     CK(cudaMemsetAsync(d_bad, 0, sizeof(uint32_t), s));
     {
         ProfScope ps(GP_KERNEL_VALIDATE, s);
@@ -612,8 +686,7 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
             if (cur_items.empty()) break;
             EvalItem *d_items;
             CK(ws.alloc((void **)&d_items, sizeof(EvalItem) * cur_items.size(), s));
-            CK(cudaMemcpyAsync(d_items, cur_items.data(), sizeof(EvalItem) * cur_items.size(),
-                               cudaMemcpyHostToDevice, s));
+            CK(h2d(d_items, cur_items.data(), sizeof(EvalItem) * cur_items.size(), s));
             uint32_t *u_next = nullptr;
             float2 *pt_next = nullptr;
             std::vector<uint64_t> frag_off;
@@ -659,8 +732,7 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
                 // re-upload the items with their spill areas (fragment fields
                 // written by the scan are kept: only finals changed)
                 for (uint32_t i = n_frag; i < cur_items.size(); ++i)
-                    CK(cudaMemcpyAsync(d_items + i, &cur_items[i], sizeof(EvalItem),
-                                       cudaMemcpyHostToDevice, s));
+                    CK(h2d(d_items + i, &cur_items[i], sizeof(EvalItem), s));
             }
             float2 *d_spill;
             CK(ws.alloc((void **)&d_spill,
@@ -869,7 +941,7 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
             CK(tmp.alloc((void **)&d_end, sizeof(uint64_t) * q.size(), s));
             CK(tmp.alloc((void **)&d_err, sizeof(uint32_t), s));
             CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
-            CK(cudaMemcpyAsync(d_q, q.data(), sizeof(ExtentQuery) * q.size(), cudaMemcpyHostToDevice, s));
+            CK(h2d(d_q, q.data(), sizeof(ExtentQuery) * q.size(), s));
             {
                 ProfScope ps(GP_KERNEL_EXTENT, s);
                 CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_err, s));

@@ -276,7 +276,7 @@ __device__ __forceinline__ int group_u8(uint64_t &tos, uint32_t &t, int q, uint4
 
 
 template <int LANES, typename Code, bool WIDE>
-__device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &it, uint32_t win_sa,
+__device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *itp, uint32_t win_sa,
                                           uint32_t tbl_sa, uint32_t stage_sa, float *errs,
                                           float2 *__restrict__ spill, uint64_t spill_cap, int lane,
                                           uint32_t mask, float y0, float y1)
@@ -285,24 +285,25 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
     const Code *codes0 = static_cast<const Code *>(P.codes);
     const int K = (int)P.window;
     const float d0 = P.div0;
-    const bool is_final = (it.flags & kItemFinal) != 0;
-    const bool fused = (it.flags & kItemFused) != 0;      // chunk of a medium tree
-    const bool rope = WIDE && (it.flags & kItemRope) != 0; // final over a medium tree's slots
+    // Item fields other than its range are re-read when needed (cold paths)
+    // rather than kept live across the interpreter loop; `itp` points to
+    // this warp's shared-memory copy of the item.
+#define IT(f) (itp->f)
+    const uint32_t flags = IT(flags);
+    const bool is_final = (flags & kItemFinal) != 0;
+    const bool fused = (flags & kItemFused) != 0;      // chunk of a medium tree
+    const bool rope = WIDE && (flags & kItemRope) != 0; // final over a medium tree's slots
     const uint32_t tb = tbl_sa + lane * 8u - 4u * S;        // + code * S = leaf table row
     const uint32_t wb = win_sa + lane * 8u;                 // this lane's column of the window
 
     uint64_t tos = 0;                     // top of stack (first argument of the next operator)
     bool have = false;                    // tos holds a value of this item
     uint32_t t = wb;                      // next free window entry (shared address)
-    uint64_t g = 0;                       // entries spilled below the window
+    uint32_t g = 0;                       // entries spilled below the window
     // Fragment output: planned items write at planned offsets; fused chunks
     // right-align their codes in their own slot and number their value
-    // entries from the slot's first entry.
-    const uint64_t e_lo = fused ? it.frag_off * P.fz_cap_codes : it.frag_off;
-    uint64_t ecur = fused ? e_lo + P.fz_cap_codes : it.frag_off + it.frag_len;
-    const uint64_t pt_lo = fused ? it.frag_off * P.fz_cap_pt : it.pt_base;
-    const uint64_t pt_hi = fused ? pt_lo + P.fz_cap_pt : it.pt_base + it.pt_cnt;
-    uint64_t ptn = pt_lo;
+    // entries from the slot's first entry.  Counters of what was emitted:
+    uint32_t n_emit = 0, n_pt = 0;
     bool pt_full = false;                 // a fused chunk ran out of value slots
     uint32_t prev = 0xFFFFFFFFu;          // code at the position right of the current one
     uint32_t fault = 0;                   // kErr* bits; any fault ends the item
@@ -315,14 +316,14 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
         if (WIDE && c >= kPtCode0) return lds64(stage_sa + (buf * 16 + jcur) * S);
         return lds64(tb + c * S);
     };
-    if (rope && P.fz_over[it.tree]) {
+    if (rope && P.fz_over[IT(tree)]) {
         // A chunk of this tree ran out of value slots: queue the tree for a
         // re-evaluation through planned upper-tree levels.
-        if (lane == 0) P.fz_redo[1 + atomicAdd(P.fz_redo, 1u)] = it.tree;
+        if (lane == 0) P.fz_redo[1 + atomicAdd(P.fz_redo, 1u)] = IT(tree);
         return;
     }
     const float2 *pt_src = P.pt_in;       // value entries read by the current range
-    uint64_t rb = it.begin, re = it.end;  // the current range
+    uint64_t rb = IT(begin), re = IT(end);  // the current range
     auto stage = [&](const Group<Code> &grp, int64_t gbase, uint32_t into) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -339,19 +340,23 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
     };
     // Fragment output stays inside the slot reserved for it.
     auto emit = [&](uint32_t code) {
-        if (ecur == e_lo) { fault |= kErrPlan; return; }
-        --ecur;
-        if (lane == 0) (fused ? P.fz_codes : P.u_out)[ecur] = code;
+        const uint64_t cap = fused ? P.fz_cap_codes : IT(frag_len);
+        if (n_emit >= cap) { fault |= kErrPlan; return; }
+        const uint64_t end = fused ? (IT(frag_off) + 1) * P.fz_cap_codes : IT(frag_off) + IT(frag_len);
+        ++n_emit;
+        if (lane == 0) (fused ? P.fz_codes : P.u_out)[end - n_emit] = code;
     };
     auto new_pt = [&](uint64_t v) -> uint32_t {
-        if (ptn >= pt_hi) {
+        const uint32_t cap = fused ? P.fz_cap_pt : IT(pt_cnt);
+        if (n_pt >= cap) {
             if (fused) pt_full = true;    // the tree is re-evaluated without chunk slots
             else fault |= kErrPlan;
             return kPtCode0;
         }
-        (fused ? P.fz_pt : P.pt_out)[ptn * LANES + lane] = upk(v);
+        const uint64_t idx = (fused ? IT(frag_off) * P.fz_cap_pt : IT(pt_base)) + n_pt;
+        (fused ? P.fz_pt : P.pt_out)[idx * LANES + lane] = upk(v);
         // planned fragments number entries globally, fused chunks per slot
-        return (uint32_t)(kPtCode0 + (fused ? ptn++ - pt_lo : ptn++));
+        return (uint32_t)(kPtCode0 + (fused ? n_pt++ : (n_pt++, idx)));
     };
     // Keep room for four pushes in the window, and four pops whenever
     // entries are spilled; the window is refilled / spilled half-way.
@@ -360,7 +365,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
         if (d > dmax) {
             const int sp = (int)(d / S);
             const int h = sp - K / 2;
-            if (g + (uint64_t)h > spill_cap) {
+            if ((uint64_t)g + h > spill_cap) {
                 fault |= kErrSpill;
                 return;
             }
@@ -370,7 +375,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
             t -= h * S;
         } else if (d < 4 * S && g > 0) {
             const int sp = (int)(d / S);
-            const int h = (int)umin64(g, (uint64_t)(K / 2 - sp));
+            const int h = min((int)g, K / 2 - sp);
             for (int i = sp - 1; i >= 0; --i) sts64(wb + (i + h) * S, lds64(wb + i * S));
             for (int i = 0; i < h; ++i) sts64(wb + i * S, pk(spill[(g - h + i) * LANES + lane]));
             g -= h;
@@ -430,11 +435,11 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
     const uint32_t fast_lo = wb + 4 * S;
     // A rope item walks its tree's chunk fragments from the last to the
     // first, each right to left, on one continuous stack.
-    const uint32_t nranges = rope ? it.frag_len : 1;
+    const uint32_t nranges = rope ? IT(frag_len) : 1;
     for (uint32_t r = 0; r < nranges && !fault; ++r) {
     const Code *codes = codes0;
     if (rope) {
-        const uint64_t slot = it.pt_base + (nranges - 1 - r);
+        const uint64_t slot = IT(pt_base) + (nranges - 1 - r);
         codes = reinterpret_cast<const Code *>(P.fz_codes + slot * P.fz_cap_codes);
         re = P.fz_cap_codes;
         rb = re - P.fz_len[slot];
@@ -560,13 +565,13 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
         if constexpr (WIDE) cp_async_wait0();   // staging is idle before the next item
     }
     }
-    if (!rope && it.end <= it.begin && is_final) {
+    if (!rope && IT(end) <= IT(begin) && is_final) {
         fault |= kErrMalformed;
     }
     const int sp = (int)((t - wb) / S);
 
     if (is_final) {
-        const uint32_t tr = it.tree;
+        const uint32_t tr = IT(tree);
         const uint32_t nc = P.n_cases;
         const bool ok = !fault && have && sp == 0 && g == 0;
         if (rope && fault) {              // e.g. deeper than the spill area: redo as planned
@@ -613,15 +618,16 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem &i
     if (have) emit(new_pt(tos));
     if (fused) {
         if (lane == 0) {
-            P.fz_len[it.frag_off] = (uint32_t)(e_lo + P.fz_cap_codes - ecur);
-            if (pt_full) P.fz_over[it.tree] = 1u;
+            P.fz_len[IT(frag_off)] = n_emit;
+            if (pt_full) P.fz_over[IT(tree)] = 1u;
         }
         if (fault && lane == 0) atomicOr(P.err, kErrPlan);
         return;
     }
-    if (fault || ecur != it.frag_off || ptn != it.pt_base + it.pt_cnt) {
+    if (fault || n_emit != IT(frag_len) || n_pt != IT(pt_cnt)) {
         if (lane == 0) atomicOr(P.err, kErrPlan);
     }
+#undef IT
 }
 
 // ---------------------------------------------------------------- kernel
@@ -635,6 +641,8 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     const uint32_t win0 = kLeafRows * S;                    // first window (bytes)
     // Upper-tree kernels: two 16-entry staging buffers per warp after the windows.
     const uint32_t stage0 = win0 + (uint32_t)nwarps * P.window * S;
+    // Then one item copy (64 bytes) per warp.
+    const uint32_t item0 = stage0 + (WIDE ? (uint32_t)nwarps * 32 * S : 0u);
 
     // Leaf table: row 0 is x (per lane, two cases), row r >= 1 constant r-1.
     for (int i = threadIdx.x; i < (int)(kLeafRows * LANES); i += blockDim.x) {
@@ -662,14 +670,20 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
         if (lane == 0) idx = atomicAdd(P.counter, 1u);
         idx = __shfl_sync(mask, idx, 0);
         if (idx >= P.n_items) break;
-        const EvalItem it = P.items[idx];
+        EvalItem *itp = reinterpret_cast<EvalItem *>(smem + item0 + warp * sizeof(EvalItem));
+        __syncwarp(mask);                 // the previous item's readers are done
+        for (int w = lane; w < (int)(sizeof(EvalItem) / 4); w += LANES)   // any lane count
+            reinterpret_cast<uint32_t *>(itp)[w] =
+                __ldg(reinterpret_cast<const uint32_t *>(P.items + idx) + w);
+        __syncwarp(mask);
         float2 *area = myspill;
         uint64_t cap = P.spill_per_warp;
-        if (it.spill_off != kNoSpill) {
-            area = P.spill + it.spill_off * LANES;
-            cap = it.spill_cap;
+        const uint64_t soff = itp->spill_off;
+        if (soff != kNoSpill) {
+            area = P.spill + soff * LANES;
+            cap = itp->spill_cap;
         }
-        eval_item<LANES, Code, WIDE>(P, it, sbase + win_off, sbase,
+        eval_item<LANES, Code, WIDE>(P, itp, sbase + win_off, sbase,
                                      sbase + stage0 + (uint32_t)warp * 32 * S + lane * 8u, errs, area,
                                      cap, lane, mask, y0, y1);
     }
@@ -678,7 +692,8 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
 size_t eval_smem_bytes(int lanes, int warps, int window, bool wide)
 {
     return (size_t)kLeafRows * lanes * sizeof(float2) +
-           (size_t)warps * (window + (wide ? 32 : 0)) * lanes * sizeof(float2);
+           (size_t)warps * (window + (wide ? 32 : 0)) * lanes * sizeof(float2) +
+           (size_t)warps * sizeof(EvalItem);
 }
 
 template <int LANES>
