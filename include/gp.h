@@ -187,6 +187,43 @@ typedef struct gp_kernel_profile {
 gp_status gp_profile_enable(int on);
 gp_status gp_profile_read(gp_kernel_profile *out, int reset);
 
+/* ---- Evaluation without allocation.  The paper has no counterpart: this
+ * serves callers that cannot allocate device memory while they evaluate,
+ * e.g. a loop whose GPU memory is owned by its own allocator, or one that
+ * cannot afford the implicit synchronisation of cudaMalloc / cudaFree. ---- */
+
+#define GP_NOALLOC_MAX_TREES 16384u        /* trees per call                      */
+#define GP_NOALLOC_MAX_TREE_NODES 4096u    /* nodes per tree                      */
+
+/* Evaluate `n_trees` trees like gp_evaluate + gp_fitness, without allocating
+ * anything: no device or host allocation, no stream-ordered pool.  All
+ * scratch (work items, per-tree validation results, a work counter, error
+ * words, the fitness cases and constants) lives in one static device array
+ * inside libgp of about 1.4 MiB (4 KiB + GP_NOALLOC_MAX_TREES x (64 + 24) B),
+ * which every GPU that loads libgp holds until the process exits.  The call
+ * sets every word of it that it reads, so nothing needs to start at zero.
+ *   d_nodes:  device, the trees packed as for gp_create_population
+ *             (offsets[], host, n_trees + 1 entries, offsets[0] = 0); 16-byte
+ *             aligned and readable up to the next multiple of 16 bytes past
+ *             its end, inside one allocation.  Trees are validated (codes
+ *             and stack balance) before anything is evaluated.
+ *   d_fitness [n_trees], d_case_values [n_trees * n_cases], d_hits [n_trees]:
+ *             device outputs, as gp_fitness returns them.
+ * Operand stacks get a 256-entry shared-memory window and no spill area.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  The call
+ * synchronises `cuda_stream` twice, to read the validation count and the
+ * error word.  Every call shares the
+ * array and overwrites it: calls that overlap on the GPU (other host
+ * threads, other streams) race.
+ * Errors: GP_ELIMIT (n_trees > GP_NOALLOC_MAX_TREES, a tree larger than
+ * GP_NOALLOC_MAX_TREE_NODES, or an operand stack deeper than its window),
+ * GP_EINVAL (null, misaligned or too short buffers, bad offsets or problem),
+ * GP_EMALFORMED (a tree is not one prefix tree), GP_ECUDA. */
+gp_status gp_evaluate_noalloc(const gp_problem *problem, uint32_t n_trees, const uint8_t *d_nodes,
+                              const uint64_t *offsets, float *d_fitness, float *d_case_values,
+                              uint32_t *d_hits, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -721,6 +721,18 @@ cudaError_t eval_prepare(int lanes, bool wide, size_t smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Raise (never lower) the kernel's dynamic shared-memory limit to `smem`.
+cudaError_t eval_prepare_at_least(int lanes, bool wide, size_t smem)
+{
+    void *fn = eval_fn_for(lanes, wide);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
                         size_t smem, cudaStream_t s)
 {

@@ -112,6 +112,7 @@ struct ExtentQuery {
 // Launchers (defined in the .cu files; return the launch's error).
 size_t eval_smem_bytes(int lanes, int warps, int window, bool wide);
 cudaError_t eval_prepare(int lanes, bool wide, size_t smem);
+cudaError_t eval_prepare_at_least(int lanes, bool wide, size_t smem);
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
                         size_t smem, cudaStream_t s);
 cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uint32_t n,

@@ -23,8 +23,10 @@ EXPORTED = [
     "gp_create_population", "gp_crossover", "gp_evaluate", "gp_evaluate_ex", "gp_fitness",
     "gp_tree_size", "gp_tree_read", "gp_population_get_info", "gp_destroy_population",
     "gp_status_string", "gp_eval_stats_get", "gp_kernel_launch_count", "gp_profile_enable",
-    "gp_profile_read",
+    "gp_profile_read", "gp_evaluate_noalloc",
 ]
+NOALLOC_MAX_TREES = 16384
+NOALLOC_MAX_TREE_NODES = 4096
 
 
 class gp_problem(C.Structure):
@@ -96,6 +98,7 @@ def lib():
             L.gp_kernel_launch_count.restype = C.c_uint64
             L.gp_profile_enable.argtypes = [C.c_int]
             L.gp_profile_read.argtypes = [P(gp_kernel_profile), C.c_int]
+            L.gp_evaluate_noalloc.argtypes = [P(gp_problem), C.c_uint32, vp, P(C.c_uint64), vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -261,6 +264,20 @@ def gp_profile_read(reset: bool = False) -> dict:
     _check(lib().gp_profile_read(C.byref(p), 1 if reset else 0), "gp_profile_read")
     return {k: {"launches": int(p.launches[i]), "ms": float(p.total_ms[i])}
             for i, k in enumerate(KERNEL_KINDS) if k != "unused"}
+
+
+def gp_evaluate_noalloc(problem: Problem, offsets, d_nodes: int, d_fitness: int, d_case_values: int,
+                        d_hits: int, stream=None):
+    """Evaluate trees already on the device (packed as `offsets` describes)
+    into caller-provided device outputs, without any allocation in libgp.
+    Device arguments are raw addresses (e.g. torch tensor data_ptr())."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = offsets.shape[0] - 1
+    st = lib().gp_evaluate_noalloc(C.byref(problem.struct), n, C.c_void_p(int(d_nodes)),
+                                   _ptr(offsets, C.c_uint64), C.c_void_p(int(d_fitness)),
+                                   C.c_void_p(int(d_case_values)), C.c_void_p(int(d_hits)),
+                                   _stream(stream))
+    _check(st, "gp_evaluate_noalloc")
 
 
 def read_all_trees(pop: Population):
