@@ -108,9 +108,10 @@ gp_status gp_crossover(const gp_population *parents, const gp_xo *ops, uint32_t 
 /* Evaluate every tree on every fitness case (Sec. 2.2 single-pass
  * evaluation, Table gp.details protected division) and reduce each tree to
  * its mean absolute error with a sequential fold in case order (Sec. 2.2,
- * Sec. 3.2) and its hit count.  Asynchronous on `cuda_stream` except for a
- * short synchronisation when a tree is split into chunks and its upper tree
- * must be sized.  Results are read with gp_fitness.
+ * Sec. 3.2) and its hit count.  Asynchronous on `cuda_stream`, except that
+ * trees of more than 32 chunks (chunk_nodes, default 4096) have their upper
+ * trees sized on the device and read back, one short synchronisation per
+ * upper-tree level.  Results are read with gp_fitness.
  * Errors: GP_EINVAL, GP_ENOMEM, GP_ECUDA. */
 gp_status gp_evaluate(gp_population *pop, void *cuda_stream);
 gp_status gp_evaluate_ex(gp_population *pop, const gp_eval_options *opt, void *cuda_stream);

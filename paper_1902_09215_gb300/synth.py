@@ -189,6 +189,152 @@ def population_loguniform(seed: int = 3, count: int = 4000, lo: int = 31, hi: in
     return pack([random_tree(rng, int(n), p_x=p_x) for n in sizes])
 
 
+def deepest_leaf(tree: np.ndarray) -> tuple[int, int]:
+    """(position, depth) of the first deepest leaf of a prefix tree (root
+    depth 0).  A stack of open child slots, each tagged with its depth."""
+    slots = [0]
+    best_pos, best_d = 0, -1
+    for i, c in enumerate(tree.tolist()):
+        d = slots.pop()
+        if c < LEAF_X:
+            slots.append(d + 1)
+            slots.append(d + 1)
+        elif d > best_d:
+            best_pos, best_d = i, d
+    return best_pos, best_d
+
+
+class _Piece:
+    """One grafted tree inside a bloated tree: its codes and, per replaced
+    leaf position, the piece grafted there."""
+    __slots__ = ("codes", "leaves", "kids")
+
+    def __init__(self, codes):
+        self.codes = codes
+        self.leaves = None
+        self.kids = {}
+
+    def leaf_positions(self):
+        if self.leaves is None:
+            self.leaves = np.flatnonzero(self.codes >= LEAF_X)
+        return self.leaves
+
+
+def _write_pieces(root: _Piece, out: np.ndarray, at: int) -> int:
+    """Write the prefix array of a tree of pieces into out[at:], iteratively
+    (chains of grafts nest deeply); returns the end position."""
+    stack = [[root, sorted(root.kids), 0, 0]]
+    while stack:
+        fr = stack[-1]
+        piece, kids, k, frm = fr
+        if k < len(kids):
+            p = kids[k]
+            n = p - frm
+            out[at:at + n] = piece.codes[frm:p]
+            at += n
+            fr[2], fr[3] = k + 1, p + 1
+            child = piece.kids[p]
+            stack.append([child, sorted(child.kids), 0, 0])
+        else:
+            n = piece.codes.shape[0] - frm
+            out[at:at + n] = piece.codes[frm:]
+            at += n
+            stack.pop()
+    return at
+
+
+def _graft_tree(rng, target, pool, donor_hi, chain=None, chain_depth=0):
+    """The pieces of a tree of exactly `target` nodes grown by repeated
+    subtree crossover (Sec. 3.1) whose dad point is the root of a whole
+    donor tree and whose mum point is a leaf of the tree grown so far.
+    Optionally a chain of grafts at the deepest leaf first, until the depth
+    reaches `chain_depth`; then grafts at leaves chosen uniformly over the
+    whole tree, the last one a fresh random tree sized to land on `target`.
+    Returns (root piece, depth reached by the chain)."""
+    pieces, free = [], []
+    size = 0
+
+    def add(piece):
+        pieces.append(piece)
+        free.append(piece.leaf_positions().shape[0])
+
+    reached = 0
+    if chain is not None:
+        trees, deep = chain                         # deep[k] = (position, depth)
+        k = int(rng.integers(0, len(trees)))
+        root = cur = _Piece(trees[k])
+        add(root)
+        size = trees[k].shape[0]
+        base = 0                                    # depth of cur's root
+        while base + deep[k][1] < chain_depth:
+            j = int(rng.integers(0, len(trees)))
+            if size + trees[j].shape[0] - 1 > target:
+                break
+            nxt = _Piece(trees[j])
+            cur.kids[int(deep[k][0])] = nxt
+            free[-1] -= 1
+            add(nxt)
+            base += deep[k][1]
+            cur, k, size = nxt, j, size + trees[j].shape[0] - 1
+        reached = base + deep[k][1]
+    else:
+        need = target
+        first = random_tree(rng, int(need)) if need <= donor_hi else pool[int(rng.integers(0, len(pool)))]
+        root = _Piece(first)
+        add(root)
+        size = first.shape[0]
+    while size < target:
+        need = target - size + 1                    # odd: both sizes are odd
+        d = random_tree(rng, int(need)) if need <= donor_hi else pool[int(rng.integers(0, len(pool)))]
+        cum = np.cumsum(free)
+        r = int(rng.integers(0, int(cum[-1])))
+        j = int(np.searchsorted(cum, r, side="right"))
+        host = pieces[j]
+        leaves = host.leaf_positions()
+        while True:
+            pos = int(leaves[int(rng.integers(0, leaves.shape[0]))])
+            if pos not in host.kids:
+                break
+        piece = _Piece(d)
+        host.kids[pos] = piece
+        free[j] -= 1
+        add(piece)
+        size += d.shape[0] - 1
+    return root, reached
+
+
+def graft_population(seed: int = 4, count: int = 48, lo: int = 10**6, hi: int = 4 * 10**8,
+                     donor_lo: int = 10**5, donor_hi: int = 10**6, n_donors: int = 32,
+                     chain_depth: int = 10**5, chain_lo: int = 2 * 10**4, chain_hi: int = 10**5,
+                     n_chain: int = 8):
+    """Bloated trees: odd sizes log-uniform on [lo, hi], each grown by chains
+    of subtree crossover from a pool of `n_donors` random trees (sizes
+    log-uniform on [donor_lo, donor_hi]).  The largest tree first follows a
+    chain of grafts at the deepest leaf (donors from a second pool, sizes
+    [chain_lo, chain_hi]) until its depth reaches `chain_depth`, which makes
+    it deep and stringy.  Returns (nodes, offsets, info) with info =
+    {"sizes", "deep_tree", "chain_depth"}; the nodes array is written in
+    place, so memory is one copy of the population."""
+    rng = np.random.default_rng(seed)
+    sizes = loguniform_sizes(rng, count, lo, hi)
+    pool = [random_tree(rng, int(n)) for n in loguniform_sizes(rng, n_donors, donor_lo, donor_hi)]
+    chain_trees = [random_tree(rng, int(n)) for n in loguniform_sizes(rng, n_chain, chain_lo, chain_hi)]
+    chain = (chain_trees, [deepest_leaf(t) for t in chain_trees])
+    deep = int(np.argmax(sizes))
+    offsets = np.zeros(count + 1, dtype=np.uint64)
+    np.cumsum(sizes.astype(np.uint64), out=offsets[1:])
+    nodes = np.empty(int(offsets[-1]), dtype=np.uint8)
+    reached = 0
+    for t in range(count):
+        root, r = _graft_tree(rng, int(sizes[t]), pool, donor_hi,
+                              chain if t == deep else None, chain_depth)
+        end = _write_pieces(root, nodes, int(offsets[t]))
+        assert end == int(offsets[t + 1])
+        if t == deep:
+            reached = r
+    return nodes, offsets, {"sizes": sizes, "deep_tree": deep, "chain_depth": reached}
+
+
 def crossover_points(seed: int, sizes: np.ndarray, n_ops: int, n_parents: int | None = None):
     """Uniformly chosen (mum, dad, mum_point, dad_point) records (Sec. 3.1):
     parents uniform over the population, points uniform over all nodes."""
