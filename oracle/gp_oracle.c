@@ -20,6 +20,14 @@
  *   - Sec. 3.2: a hit is a case with |error| within 0.01.
  *   - Sec. 3.1: one child per crossover: mum with the subtree at the mum
  *     point replaced by dad's subtree at the dad point.
+ *   - Table gp.details / Sec. 3.2: generational, non-elitist; both parents
+ *     of every child chosen by tournaments of size 7 on fitness (lower is
+ *     better); both crossover points uniform over all nodes of the parent
+ *     (Sec. 3.1), chosen in a fixed sequential order (Sec. 3.1, last para.).
+ *     The random numbers are a counter-based stream (SplitMix64 of Steele,
+ *     Lea & Flood 2014 indexed by a counter), bounded by Lemire's
+ *     multiply-shift with rejection (ACM TOMACS 2019), so any draw can be
+ *     recomputed from (seed, generation, child, purpose, index).
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math (no contraction of a*b+c,
  * IEEE binary32/binary64 round-to-nearest, subnormals kept).
@@ -388,4 +396,89 @@ int oracle_eval_population(const uint8_t *nodes, const uint64_t *offs, uint32_t 
     }
     pthread_mutex_destroy(&P.mu);
     return P.st;
+}
+
+/* ---- Generation: tournament selection and crossover points ------------- */
+/*
+ * Output i (i = 0, 1, ...) of the SplitMix64 generator seeded with `seed`:
+ * the state after i + 1 steps of the Weyl sequence, passed through the
+ * generator's mixing function.
+ */
+uint64_t oracle_sm64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/*
+ * Counter of one draw: generation g (< 2^24), child c (< 2^28), purpose p
+ * (0 mum tournament, 1 dad tournament, 2 mum point, 3 dad point), index k
+ * within the purpose (< 32: tournament entrant) and attempt a (< 16).
+ */
+static uint64_t draw_counter(uint64_t g, uint64_t c, uint64_t p, uint64_t k, uint64_t a)
+{
+    return (g << 40) | (c << 12) | (p << 9) | (k << 4) | a;
+}
+
+/*
+ * Uniform integer in [0, n), n >= 1: the high word of r * n for the first
+ * attempt whose low word is at least 2^64 mod n (Lemire 2019); the attempts
+ * use counters base, base + 1, ... (at most 16; the last one is taken if
+ * all 16 were rejected, which has probability below 2^-16 even for the
+ * worst n).
+ */
+uint64_t oracle_bounded(uint64_t seed, uint64_t base, uint64_t n)
+{
+    const uint64_t t = (0 - n) % n;
+    unsigned __int128 m = 0;
+    int a;
+    for (a = 0; a < 16; a++) {
+        m = (unsigned __int128)oracle_sm64_at(seed, base + (uint64_t)a) * n;
+        if ((uint64_t)m >= t) break;
+    }
+    return (uint64_t)(m >> 64);
+}
+
+/*
+ * Tournament: `size` entrants drawn uniformly with replacement from the
+ * population; the one with the lowest fitness wins, NaN counting as worst
+ * and ties going to the entrant drawn first.
+ */
+uint32_t oracle_tournament(const float *fitness, uint32_t n_pop, uint64_t seed, uint64_t g,
+                           uint64_t c, uint32_t purpose, uint32_t size)
+{
+    uint32_t best = 0, k;
+    float best_f = 0.0f;
+    for (k = 0; k < size; k++) {
+        const uint32_t e = (uint32_t)oracle_bounded(seed, draw_counter(g, c, purpose, k, 0), n_pop);
+        const float f = isnan(fitness[e]) ? INFINITY : fitness[e];
+        if (k == 0 || f < best_f) {
+            best = e;
+            best_f = f;
+        }
+    }
+    return best;
+}
+
+/*
+ * The crossover records of one generation: for child c = 0 .. n_children-1,
+ * in order, mum and dad by tournament on the parents' fitness, then the mum
+ * point and the dad point, each uniform over the chosen parent's nodes.
+ */
+int oracle_generation(const float *fitness, const uint64_t *sizes, uint32_t n_pop,
+                      uint32_t n_children, uint64_t seed, uint64_t g, uint32_t tsize,
+                      uint32_t *mum, uint32_t *dad, uint64_t *mum_point, uint64_t *dad_point)
+{
+    uint32_t c;
+    if (n_pop == 0 || tsize == 0 || tsize > 32 || g >= (1ull << 24) || n_children > (1u << 28))
+        return OR_EINVAL;
+    for (c = 0; c < n_children; c++) {
+        mum[c] = oracle_tournament(fitness, n_pop, seed, g, c, 0, tsize);
+        dad[c] = oracle_tournament(fitness, n_pop, seed, g, c, 1, tsize);
+        mum_point[c] = oracle_bounded(seed, draw_counter(g, c, 2, 0, 0), sizes[mum[c]]);
+        dad_point[c] = oracle_bounded(seed, draw_counter(g, c, 3, 0, 0), sizes[dad[c]]);
+    }
+    return OR_OK;
 }

@@ -19,6 +19,8 @@ import threading
 
 import numpy as np
 
+_M64 = (1 << 64) - 1
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gp_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
@@ -60,6 +62,15 @@ def lib():
             L.oracle_eval_population.argtypes = [u8p, u64p, C.c_uint32, f32p, f32p, C.c_uint32, f32p,
                                                  C.c_uint32, C.c_float, f32p, f32p, u32p, f64p, f64p,
                                                  C.c_int]
+            L.oracle_sm64_at.argtypes = [C.c_uint64, C.c_uint64]
+            L.oracle_sm64_at.restype = C.c_uint64
+            L.oracle_bounded.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+            L.oracle_bounded.restype = C.c_uint64
+            L.oracle_tournament.argtypes = [f32p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64,
+                                            C.c_uint32, C.c_uint32]
+            L.oracle_tournament.restype = C.c_uint32
+            L.oracle_generation.argtypes = [f32p, u64p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64,
+                                            C.c_uint32, u32p, u32p, u64p, u64p]
             _lib = L
     return _lib
 
@@ -183,3 +194,43 @@ def eval_population(nodes, offsets, x, y, consts, div0: float = 1.0, n_threads: 
     if want_f64:
         r["out64"], r["fitness64"] = out64, fit64
     return r
+
+
+# ---------------------------------------------------------------------------
+# Generation: counter-based draws, tournament selection, crossover records
+# ---------------------------------------------------------------------------
+
+def draw_counter(g: int, c: int, purpose: int, k: int = 0, attempt: int = 0) -> int:
+    """Counter of one draw (generation, child, purpose, index, attempt)."""
+    return (g << 40) | (c << 12) | (purpose << 9) | (k << 4) | attempt
+
+
+def sm64_at(seed: int, i: int) -> int:
+    """Output i of SplitMix64 seeded with `seed`."""
+    return int(lib().oracle_sm64_at(seed & _M64, i & _M64))
+
+
+def bounded(seed: int, base: int, n: int) -> int:
+    """Unbiased draw in [0, n) from the counters base, base+1, ... ."""
+    return int(lib().oracle_bounded(seed & _M64, base & _M64, n))
+
+
+def tournament(fitness, seed: int, g: int, c: int, purpose: int, size: int) -> int:
+    f = _f32(fitness)
+    return int(lib().oracle_tournament(_p(f, C.c_float), f.shape[0], seed & _M64, g, c, purpose, size))
+
+
+def generation_records(fitness, sizes, n_children: int, seed: int, g: int, tsize: int = 7):
+    """(mum, dad, mum_point, dad_point) of every child of generation g."""
+    f = _f32(fitness)
+    sz = np.ascontiguousarray(sizes, dtype=np.uint64)
+    mum = np.empty(n_children, np.uint32)
+    dad = np.empty(n_children, np.uint32)
+    mp = np.empty(n_children, np.uint64)
+    dp = np.empty(n_children, np.uint64)
+    st = lib().oracle_generation(_p(f, C.c_float), _p(sz, C.c_uint64), f.shape[0], n_children,
+                                 seed & _M64, g, tsize, _p(mum, C.c_uint32), _p(dad, C.c_uint32),
+                                 _p(mp, C.c_uint64), _p(dp, C.c_uint64))
+    if st:
+        raise OracleError(f"generation records failed: status {st}")
+    return mum, dad, mp, dp
