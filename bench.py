@@ -404,6 +404,160 @@ def run_reference(args):
     }))
 
 
+# ---------------------------------------------------------------------------
+# batched generations on the device (tournament selection + crossover +
+# evaluation as one captured launch sequence per generation)
+# ---------------------------------------------------------------------------
+
+SEED_GEN = 21
+BATCHED = {
+    "generation4000": (
+        "4000 seeded random prefix trees, odd sizes log-uniform 31..32767 nodes (seed 3), 48 Sextic "
+        "cases, 127 constants; step = one generation on the device: size-7 tournaments for both "
+        "parents of 4000 children, 4000 subtree crossovers at uniform points, evaluation of the children",
+        lambda: synth.population_loguniform(seed=3, count=4000)),
+    "batched": (
+        "4000 parents, odd sizes log-uniform 1e2..1e8 nodes (seed 5; trees above 1e6 grown by crossover "
+        "chains from a pool of 32 random donors of 1e5..1e6 nodes), 48 Sextic cases, 127 constants; "
+        "step = one generation on the device (size-7 tournaments, 4000 crossovers, evaluation)",
+        lambda: synth.graft_population(seed=5, count=4000, lo=100, hi=10**8, donor_lo=10**5,
+                                       donor_hi=10**6, n_donors=32, chain_depth=0)[:2]),
+    "batched-reduced": (
+        "4000 parents, odd sizes log-uniform 1e2..1e6 nodes (seed 5; trees above 1e5 grown by crossover "
+        "chains from 32 random donors of 1e4..1e5 nodes), 48 Sextic cases; step = one generation on "
+        "the device (size-7 tournaments, 4000 crossovers, evaluation)",
+        lambda: synth.graft_population(seed=5, count=4000, lo=100, hi=10**6, donor_lo=10**4,
+                                       donor_hi=10**5, n_donors=32, chain_depth=0)[:2]),
+}
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1902_09215_gb300 import gp
+    gp.lib()
+    desc, make = BATCHED[args.workload]
+    x, y, c = synth.problem(const_seed=CONST_SEED)
+    t0 = time.perf_counter()
+    nodes, offs = make()
+    gen_s = time.perf_counter() - t0
+    n = offs.shape[0] - 1
+    sizes = np.diff(offs.astype(np.int64))
+    used = int(np.sum((sizes + 15) // 16 * 16)) + 64
+    stream = torch.cuda.Stream(dev)
+    prob = gp.Problem(x, y, c)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    arena = int(used * 1.3) + (64 << 20)
+
+    def measure(G, steps):
+        """Generation 0 -> 1 repeated: step (timed), rewind (not timed)."""
+        for _ in range(args.warmup):
+            gp.gp_generation_step(G, 1, stream)
+            gp.gp_generation_rewind(G, stream)
+        ms = []
+        l0 = gp.gp_kernel_launch_count()
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                gp.gp_generation_step(G, 1, stream)
+                b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            gp.gp_generation_rewind(G, stream)
+        launches = gp.gp_kernel_launch_count() - l0
+        return ms, launches
+
+    t0 = time.perf_counter()
+    G = gp.gp_generation_create(prob, nodes, offs, seed=SEED_GEN, chunk_nodes=args.chunk,
+                                arena_bytes=arena, use_graph=True, stream=stream)
+    create_s = time.perf_counter() - t0
+    info0 = gp.gp_generation_get_info(G)
+    with ClockSampler(0) as clk:
+        ms, launches = measure(G, args.steps)
+    gp.gp_generation_step(G, 1, stream)
+    recs = gp.gp_generation_records(G)
+    info1 = gp.gp_generation_get_info(G)
+    child_nodes = int(info1["total_nodes"])
+    # end to end through the API: one generation and the read-back of its fitness
+    gp.gp_generation_rewind(G, stream)
+    te = []
+    for _ in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        gp.gp_generation_step(G, 1, stream)
+        gp.gp_generation_fitness(G)
+        te.append(time.perf_counter() - a)
+        gp.gp_generation_rewind(G, stream)
+    gp.gp_generation_destroy(G)
+    del G
+    torch.cuda.synchronize()
+
+    # the same launch sequence without the graph
+    G = gp.gp_generation_create(prob, nodes, offs, seed=SEED_GEN, chunk_nodes=info0["chunk_nodes"],
+                                arena_bytes=arena, use_graph=False, stream=stream)
+    ms_ng, _ = measure(G, max(3, args.steps // 2))
+    gp.gp_generation_destroy(G)
+    del G
+    torch.cuda.synchronize()
+
+    # host-driven path: the same crossover records through gp_crossover +
+    # gp_evaluate (host synchronisations to size children and upper trees)
+    with torch.cuda.stream(stream):
+        parents = gp.gp_create_population(prob, nodes, offs, stream)
+    xo = gp.make_xo(*recs)
+    ms_plain = []
+    for k in range(max(3, args.steps // 2) + 1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kids = gp.gp_crossover(parents, xo, stream)
+            gp.gp_evaluate(kids, stream)
+            b.record(stream)
+        gp.gp_fitness(kids)
+        if k:                                         # first one warms the pool
+            ms_plain.append(a.elapsed_time(b))
+        del kids
+    del parents
+    torch.cuda.synchronize()
+
+    med = statistics.median(ms)
+    units = child_nodes * len(x)
+    srt = sorted(ms)
+    line = {
+        "metric": "GPops/s (tree nodes x fitness cases per second), batched generation",
+        "value": units / (med / 1e3), "unit": "GPops/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": med, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "trees": n, "parent_nodes": int(offs[-1]), "child_nodes": child_nodes,
+                   "cases": len(x), "seeds": {"run": SEED_GEN, "constants": CONST_SEED},
+                   "l2": "flushed before every timed step (256 MB write, outside the events)",
+                   "chunk_nodes": info0["chunk_nodes"], "levels": info1["levels"],
+                   "kernels_per_generation": info0["kernels_per_generation"],
+                   "arena_bytes": arena, "workspace": [info0["workspace_codes"], info0["workspace_values"]],
+                   "population_build_s": gen_s, "create_s": create_s},
+        "latency_ms": {"p50": med, "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "autotune": {str(k): v for k, v in zip(info0["autotune_chunk"], info0["autotune_ms"]) if k},
+        "clocks": clk.summary(),
+        "e2e": {"value": units / statistics.median(te), "unit": "GPops/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * n, "wall_s_p50": statistics.median(te),
+                "note": "population resident on the device; per step: one generation + fitness read-back"},
+        "gpu_launches": int(launches),
+        "compare": {
+            "device_sequence_no_graph": {"ms_p50": statistics.median(ms_ng),
+                                         "value": units / (statistics.median(ms_ng) / 1e3)},
+            "host_driven_crossover_then_evaluate": {"ms_p50": statistics.median(ms_plain),
+                                                    "value": units / (statistics.median(ms_plain) / 1e3)},
+        },
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,9 +565,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--workload", choices=["step4000"] + sorted(BATCHED), default="step4000",
+                    help="step4000 (default): crossover + evaluation of the 4000-tree population; "
+                         "the others time whole generations made on the device")
+    ap.add_argument("--chunk", type=int, default=0, help="evaluator chunk for the batched workloads (0 = autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload != "step4000":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the step4000 workload only"}))
+            return
+        run_batched(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -188,6 +188,95 @@ typedef struct gp_kernel_profile {
 gp_status gp_profile_enable(int on);
 gp_status gp_profile_read(gp_kernel_profile *out, int reset);
 
+/* ---- Generations on the device (Table gp.details: panmictic, non-elitist,
+ * generational; every child made by one two-parent subtree crossover whose
+ * parents both win tournaments on fitness; Sec. 3.1: crossover points
+ * uniform over all nodes, chosen in a fixed sequential order).
+ *
+ * A gp_generation holds the current population on the device in one of two
+ * buffers and makes each next generation into the other: tournament
+ * selection, crossover points, subtree extents, child layout, the copy and
+ * the evaluation of the children all run on the device, with every count
+ * kept in device memory, so one generation is one fixed launch sequence.
+ * It is captured once as a CUDA graph (one graph per buffer direction) and
+ * replayed.  Draws are a counter-based stream: draw number
+ *     (generation << 40) | (child << 12) | (purpose << 9) | (index << 4) | attempt
+ * of SplitMix64 (Steele, Lea & Flood 2014) seeded with `seed`, with purpose
+ * 0 / 1 = the mum's / dad's tournament (index = entrant), 2 / 3 = the mum /
+ * dad point; a draw in [0, n) is the high word of r*n for the first attempt
+ * whose low word is >= 2^64 mod n (Lemire 2019; the 16th attempt is taken if
+ * all are rejected).  The lowest fitness wins a tournament, NaN ranks
+ * worst, ties go to the entrant drawn first.  Generation g's children use
+ * counters with generation = g (the initial population is generation 0). */
+
+typedef struct gp_generation gp_generation;
+
+typedef struct gp_generation_params {
+    uint64_t seed;               /* seed of the draws                                   */
+    uint32_t tournament_size;    /* 1..32 (7 in the paper)                               */
+    uint32_t chunk_nodes;        /* evaluator chunk (multiple of 16, 256..65536);
+                                    0 = autotuned on the initial population              */
+    uint64_t arena_bytes;        /* capacity of each population buffer; 0 = twice the
+                                    initial population plus slack                        */
+    uint64_t workspace_codes;    /* upper-tree codes per level; 0 = twice what the
+                                    initial population needs, at least 2^20             */
+    uint64_t workspace_values;   /* value-buffer entries per level; 0 = as above        */
+    uint32_t use_graph;          /* nonzero: replay one CUDA graph per generation        */
+    uint32_t max_levels;         /* evaluation levels per generation (2..16; 0 = 8)      */
+} gp_generation_params;
+
+typedef struct gp_generation_info {
+    uint64_t generation;         /* index of the current population                     */
+    uint32_t n_trees;
+    uint32_t chunk_nodes;        /* chunk size in use (chosen by the autotuner if 0)     */
+    uint64_t total_nodes;        /* nodes of the current population                     */
+    uint32_t levels;             /* evaluation levels the last generation used          */
+    uint32_t graph;              /* 1 if generations replay a captured CUDA graph       */
+    uint32_t kernels_per_generation;
+    uint32_t error_generation;   /* generation whose step failed (valid after an error)  */
+    uint64_t arena_bytes, workspace_codes, workspace_values;
+    uint32_t autotune_chunk[8];  /* candidate chunk sizes tried (0 = unused slot)       */
+    float autotune_ms[8];        /* their evaluation time on the initial population     */
+} gp_generation_info;
+
+/* Upload, validate and evaluate the initial population (generation 0) of
+ * `n_trees` trees packed as for gp_create_population, and prepare the
+ * generation step.  Synchronises `cuda_stream`.  The problem's
+ * max_tree_nodes is the paper's node limit: a child larger than it stops the
+ * run (the step that made it reports GP_ELIMIT).
+ * Errors: GP_EINVAL (arguments, n_trees > 2^28), GP_EMALFORMED, GP_ENOMEM,
+ * GP_ECUDA. */
+gp_status gp_generation_create(const gp_problem *problem, const gp_generation_params *params,
+                               uint32_t n_trees, const uint8_t *nodes, const uint64_t *offsets,
+                               void *cuda_stream, gp_generation **out);
+
+/* Make `n` generations, asynchronously on `cuda_stream` (no host
+ * synchronisation).  A generation that fails (node limit, a buffer or
+ * workspace too small) sets a device error that turns the remaining
+ * launches into no-ops, so the population stays at the last complete
+ * generation; the next synchronising call reports it. */
+gp_status gp_generation_step(gp_generation *g, uint32_t n, void *cuda_stream);
+
+/* Undo the last generation step (its parents become current again; their
+ * buffer is untouched by the step).  Only one step can be undone. */
+gp_status gp_generation_rewind(gp_generation *g, void *cuda_stream);
+
+/* Synchronise and copy the current population's results (any pointer may be
+ * null).  Returns the error of a failed step: GP_ELIMIT (node limit),
+ * GP_ENOMEM (population buffer, workspace or item capacity), GP_EMALFORMED,
+ * GP_ECUDA. */
+gp_status gp_generation_fitness(gp_generation *g, float *fitness, float *case_values, uint32_t *hits);
+
+/* Synchronise and copy the crossover records of the last step (n_trees). */
+gp_status gp_generation_records(gp_generation *g, gp_xo *records);
+
+/* Synchronise and copy the current population: offsets [n_trees + 1] and,
+ * if nodes is not null, the packed trees (cap bytes at least the total). */
+gp_status gp_generation_trees(gp_generation *g, uint64_t *offsets, uint8_t *nodes, uint64_t cap);
+
+gp_status gp_generation_get_info(gp_generation *g, gp_generation_info *info);
+void gp_generation_destroy(gp_generation *g);
+
 /* ---- Evaluation without allocation.  The paper has no counterpart: this
  * serves callers that cannot allocate device memory while they evaluate,
  * e.g. a loop whose GPU memory is owned by its own allocator, or one that

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgp.so")
-SOURCES = ["gp_eval.cu", "gp_xo.cu", "gp_api.cu", "gp_noalloc.cu"]
+SOURCES = ["gp_eval.cu", "gp_xo.cu", "gp_api.cu", "gp_noalloc.cu", "gp_gen.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-fmad=false", "-prec-div=true",
                      "-prec-sqrt=true", "-ftz=false", "-Xcompiler", "-fPIC",

@@ -1026,3 +1026,7 @@ gp_status gp_profile_read(gp_kernel_profile *out, int reset)
 }
 
 }  // extern "C"
+
+namespace gpk {
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace gpk

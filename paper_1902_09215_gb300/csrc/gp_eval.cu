@@ -664,12 +664,13 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     const float y0 = P.y[2 * lane], y1 = P.y[2 * lane + 1];
     const uint64_t gw = (uint64_t)blockIdx.x * nwarps + warp;
     float2 *myspill = P.spill + gw * P.spill_per_warp * LANES;
+    const uint32_t n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
 
     for (;;) {
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(P.counter, 1u);
         idx = __shfl_sync(mask, idx, 0);
-        if (idx >= P.n_items) break;
+        if (idx >= n_items) break;
         EvalItem *itp = reinterpret_cast<EvalItem *>(smem + item0 + warp * sizeof(EvalItem));
         __syncwarp(mask);                 // the previous item's readers are done
         for (int w = lane; w < (int)(sizeof(EvalItem) / 4); w += LANES)   // any lane count
@@ -761,11 +762,12 @@ constexpr int64_t kNegInf = -(int64_t(1) << 60);
 // chunk will emit, replaying exactly the evaluator's spine rule.
 template <typename Code>
 __global__ void plan_kernel(const Code *__restrict__ codes, const EvalItem *__restrict__ items,
-                            uint32_t n, PlanOut *__restrict__ out)
+                            uint32_t n, const uint32_t *n_dev, PlanOut *__restrict__ out)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= n) return;
+    if (n_dev) n = min(n, *n_dev);
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += n_warps) {
     const EvalItem it = items[w];
     const uint64_t len = it.end - it.begin;
     const uint64_t seg = (len + 31) / 32;
@@ -826,6 +828,7 @@ __global__ void plan_kernel(const Code *__restrict__ codes, const EvalItem *__re
         o.pad = 0;
         out[w] = o;
     }
+    }
 }
 
 cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uint32_t n,
@@ -834,16 +837,29 @@ cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uin
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const uint32_t blocks = (uint32_t)(((uint64_t)n * 32 + threads - 1) / threads);
-    if (wide) plan_kernel<uint32_t><<<blocks, threads, 0, s>>>((const uint32_t *)codes, items, n, out);
-    else plan_kernel<uint8_t><<<blocks, threads, 0, s>>>((const uint8_t *)codes, items, n, out);
+    if (wide) plan_kernel<uint32_t><<<blocks, threads, 0, s>>>((const uint32_t *)codes, items, n, nullptr, out);
+    else plan_kernel<uint8_t><<<blocks, threads, 0, s>>>((const uint8_t *)codes, items, n, nullptr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_dev(bool wide, const void *codes, const EvalItem *items, uint32_t n_max,
+                            const uint32_t *n_dev, PlanOut *out, int sms, cudaStream_t s)
+{
+    if (n_max == 0) return cudaSuccess;
+    const int threads = 256;
+    const uint64_t want = ((uint64_t)n_max * 32 + threads - 1) / threads;
+    const uint32_t blocks = (uint32_t)umin64(want, (uint64_t)sms * 16);
+    if (wide) plan_kernel<uint32_t><<<blocks, threads, 0, s>>>((const uint32_t *)codes, items, n_max, n_dev, out);
+    else plan_kernel<uint8_t><<<blocks, threads, 0, s>>>((const uint8_t *)codes, items, n_max, n_dev, out);
     return cudaGetLastError();
 }
 
 // Single-CTA exclusive scan of the plan: fragment offsets and value-buffer
 // bases, written into the items; totals = {codes, entries, max stack}.
 __global__ void plan_scan_kernel(EvalItem *items, const PlanOut *plan, uint32_t n,
-                                 uint64_t *frag_off, uint64_t *totals)
+                                 const uint32_t *n_dev, uint64_t *frag_off, uint64_t *totals)
 {
+    if (n_dev) n = *n_dev;
     __shared__ uint64_t sa[1024], sb[1024];
     __shared__ uint32_t smx[1024];
     const uint32_t t = threadIdx.x, T = blockDim.x;
@@ -888,7 +904,14 @@ __global__ void plan_scan_kernel(EvalItem *items, const PlanOut *plan, uint32_t 
 cudaError_t launch_plan_scan(EvalItem *items, const PlanOut *plan, uint32_t n,
                              uint64_t *frag_off, uint64_t *totals, cudaStream_t s)
 {
-    plan_scan_kernel<<<1, 1024, 0, s>>>(items, plan, n, frag_off, totals);
+    plan_scan_kernel<<<1, 1024, 0, s>>>(items, plan, n, nullptr, frag_off, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uint32_t *n_dev,
+                                 uint64_t *frag_off, uint64_t *totals, cudaStream_t s)
+{
+    plan_scan_kernel<<<1, 1024, 0, s>>>(items, plan, 0, n_dev, frag_off, totals);
     return cudaGetLastError();
 }
 

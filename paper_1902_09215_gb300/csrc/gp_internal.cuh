@@ -60,6 +60,7 @@ struct EvalParams {
     const void *codes;             // uint8_t (level 0) or uint32_t (upper levels)
     const EvalItem *items;
     uint32_t n_items;
+    const uint32_t *n_items_dev;   // if set: the item count, read on the device at launch
     uint32_t *counter;             // work counter, zero at launch
     const float *x;                // [2*lanes], padded with zeros
     const float *y;                // [2*lanes], padded with zeros
@@ -109,6 +110,9 @@ struct ExtentQuery {
     uint64_t tree_start, tree_size, point;
 };
 
+// Adds n to the library's count of kernel launches (gp_kernel_launch_count).
+void note_launches(uint64_t n);
+
 // Launchers (defined in the .cu files; return the launch's error).
 size_t eval_smem_bytes(int lanes, int warps, int window, bool wide);
 cudaError_t eval_prepare(int lanes, bool wide, size_t smem);
@@ -120,12 +124,27 @@ cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uin
 cudaError_t launch_plan_scan(EvalItem *items, const PlanOut *plan, uint32_t n,
                              uint64_t *frag_off /*[n+1]*/, uint64_t *totals /*[3]*/,
                              cudaStream_t s);
+// Device-count forms: at most n_max items, the count read from *n_dev on the
+// device (for launch sequences that never return to the host).
+cudaError_t launch_plan_dev(bool wide, const void *codes, const EvalItem *items, uint32_t n_max,
+                            const uint32_t *n_dev, PlanOut *out, int sms, cudaStream_t s);
+cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uint32_t *n_dev,
+                                 uint64_t *frag_off, uint64_t *totals, cudaStream_t s);
 cudaError_t launch_validate(const uint8_t *codes, const EvalItem *chunks, uint32_t n_chunks,
                             uint32_t n_consts, ValOut *out, cudaStream_t s);
 cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,
                                   uint32_t n_trees, uint32_t *bad_count, cudaStream_t s);
 cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n,
                           uint64_t *end, uint32_t *err, cudaStream_t s);
+cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32_t n_max,
+                              const uint32_t *n_dev, uint64_t *end, uint32_t *err, int sms,
+                              cudaStream_t s);
+// Copy of children whose tiles are numbered on the device: child c owns
+// tiles [tile_base[c], tile_base[c+1]); *n_tiles_dev tiles in all.
+cudaError_t launch_xo_copy_dev(const uint8_t *src, uint8_t *dst, const XoChild *children,
+                               const uint32_t *tile_base, uint32_t n_children,
+                               const uint32_t *n_tiles_dev, uint32_t tile_bytes, int sms,
+                               cudaStream_t s);
 cudaError_t launch_xo_copy(const uint8_t *src, uint8_t *dst, const XoChild *children,
                            const XoTile *tiles, uint32_t n_tiles, uint32_t tile_bytes,
                            cudaStream_t s);

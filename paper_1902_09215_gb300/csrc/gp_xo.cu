@@ -12,12 +12,10 @@ namespace gpk {
 // Reading left to right, `need` counts subtrees still to be read: an
 // operator adds one, a leaf removes one; the subtree ends where it reaches
 // zero.  Each step covers 32 lanes x 16 bytes.
-__global__ void extent_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
-                              uint32_t n, uint64_t *__restrict__ end_out, uint32_t *err)
+__device__ __forceinline__ void extent_one(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
+                                           uint32_t w, int lane, uint64_t *__restrict__ end_out,
+                                           uint32_t *err)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= n) return;
     const ExtentQuery Q = q[w];
     const uint64_t tend = Q.tree_start + Q.tree_size;
     uint64_t pos = Q.tree_start + Q.point;
@@ -65,6 +63,25 @@ __global__ void extent_kernel(const uint8_t *__restrict__ arena, const ExtentQue
     }
 }
 
+__global__ void extent_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
+                              uint32_t n, uint64_t *__restrict__ end_out, uint32_t *err)
+{
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    extent_one(arena, q, w, threadIdx.x & 31, end_out, err);
+}
+
+// Same, with the query count read on the device and a grid-stride loop.
+__global__ void extent_dev_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
+                                  uint32_t n_max, const uint32_t *n_dev, uint64_t *__restrict__ end_out,
+                                  uint32_t *err)
+{
+    const uint32_t n = min(n_max, *n_dev);
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += n_warps)
+        extent_one(arena, q, w, threadIdx.x & 31, end_out, err);
+}
+
 cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n,
                           uint64_t *end, uint32_t *err, cudaStream_t s)
 {
@@ -72,6 +89,18 @@ cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n
     const int threads = 256;
     const uint32_t blocks = (uint32_t)(((uint64_t)n * 32 + threads - 1) / threads);
     extent_kernel<<<blocks, threads, 0, s>>>(arena, q, n, end, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32_t n_max,
+                              const uint32_t *n_dev, uint64_t *end, uint32_t *err, int sms,
+                              cudaStream_t s)
+{
+    if (n_max == 0) return cudaSuccess;
+    const int threads = 256;
+    const uint64_t want = ((uint64_t)n_max * 32 + threads - 1) / threads;
+    const uint32_t blocks = (uint32_t)umin64(want, (uint64_t)sms * 16);
+    extent_dev_kernel<<<blocks, threads, 0, s>>>(arena, q, n_max, n_dev, end, err);
     return cudaGetLastError();
 }
 
@@ -93,16 +122,13 @@ __device__ __forceinline__ uint32_t load4_unaligned(const uint8_t *src, uint64_t
 }
 
 // One CTA per tile of one child; every thread writes aligned 32-bit words.
-__global__ void xo_copy_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
-                               const XoChild *__restrict__ children, const XoTile *__restrict__ tiles,
-                               uint32_t tile_bytes)
+__device__ __forceinline__ void copy_tile(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                                          const XoChild &c, uint64_t tbegin, uint32_t tile_bytes)
 {
-    const XoTile T = tiles[blockIdx.x];
-    const XoChild c = children[T.child];
-    const uint64_t tend = umin64(T.begin + tile_bytes, (c.n + 3) & ~3ull);
+    const uint64_t tend = umin64(tbegin + tile_bytes, (c.n + 3) & ~3ull);
     uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + c.dst);
     const uint64_t b1 = c.i, b2 = c.i + c.ld;
-    for (uint64_t p = T.begin + 4ull * threadIdx.x; p < tend; p += 4ull * blockDim.x) {
+    for (uint64_t p = tbegin + 4ull * threadIdx.x; p < tend; p += 4ull * blockDim.x) {
         uint32_t word;
         const uint64_t q = p + 3;
         const bool one_seg = (q < c.n) && ((q < b1) || (p >= b1 && q < b2) || (p >= b2));
@@ -118,12 +144,50 @@ __global__ void xo_copy_kernel(const uint8_t *__restrict__ src, uint8_t *__restr
     }
 }
 
+__global__ void xo_copy_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                               const XoChild *__restrict__ children, const XoTile *__restrict__ tiles,
+                               uint32_t tile_bytes)
+{
+    const XoTile T = tiles[blockIdx.x];
+    copy_tile(src, dst, children[T.child], T.begin, tile_bytes);
+}
+
+// Tiles numbered on the device: a CTA takes tiles t = blockIdx.x, +gridDim.x,
+// ... and finds the owning child by binary search over tile_base.
+__global__ void xo_copy_dev_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                                   const XoChild *__restrict__ children,
+                                   const uint32_t *__restrict__ tile_base, uint32_t n_children,
+                                   const uint32_t *n_tiles_dev, uint32_t tile_bytes)
+{
+    const uint32_t n_tiles = *n_tiles_dev;
+    for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        uint32_t lo = 0, hi = n_children;          // last c with tile_base[c] <= t
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (tile_base[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        copy_tile(src, dst, children[lo], (uint64_t)(t - tile_base[lo]) * tile_bytes, tile_bytes);
+    }
+}
+
 cudaError_t launch_xo_copy(const uint8_t *src, uint8_t *dst, const XoChild *children,
                            const XoTile *tiles, uint32_t n_tiles, uint32_t tile_bytes,
                            cudaStream_t s)
 {
     if (n_tiles == 0) return cudaSuccess;
     xo_copy_kernel<<<n_tiles, 256, 0, s>>>(src, dst, children, tiles, tile_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xo_copy_dev(const uint8_t *src, uint8_t *dst, const XoChild *children,
+                               const uint32_t *tile_base, uint32_t n_children,
+                               const uint32_t *n_tiles_dev, uint32_t tile_bytes, int sms,
+                               cudaStream_t s)
+{
+    if (n_children == 0) return cudaSuccess;
+    xo_copy_dev_kernel<<<sms * 8, 256, 0, s>>>(src, dst, children, tile_base, n_children, n_tiles_dev,
+                                                tile_bytes);
     return cudaGetLastError();
 }
 

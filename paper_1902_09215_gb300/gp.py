@@ -24,6 +24,8 @@ EXPORTED = [
     "gp_tree_size", "gp_tree_read", "gp_population_get_info", "gp_destroy_population",
     "gp_status_string", "gp_eval_stats_get", "gp_kernel_launch_count", "gp_profile_enable",
     "gp_profile_read", "gp_evaluate_noalloc",
+    "gp_generation_create", "gp_generation_step", "gp_generation_rewind", "gp_generation_fitness",
+    "gp_generation_records", "gp_generation_trees", "gp_generation_get_info", "gp_generation_destroy",
 ]
 NOALLOC_MAX_TREES = 16384
 NOALLOC_MAX_TREE_NODES = 4096
@@ -55,6 +57,21 @@ class gp_population_info(C.Structure):
 class gp_eval_stats(C.Structure):
     _fields_ = [("levels", C.c_uint32), ("redone", C.c_uint32), ("items", C.c_uint64),
                 ("upper_codes", C.c_uint64), ("value_entries", C.c_uint64)]
+
+
+class gp_generation_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("tournament_size", C.c_uint32), ("chunk_nodes", C.c_uint32),
+                ("arena_bytes", C.c_uint64), ("workspace_codes", C.c_uint64),
+                ("workspace_values", C.c_uint64), ("use_graph", C.c_uint32), ("max_levels", C.c_uint32)]
+
+
+class gp_generation_info(C.Structure):
+    _fields_ = [("generation", C.c_uint64), ("n_trees", C.c_uint32), ("chunk_nodes", C.c_uint32),
+                ("total_nodes", C.c_uint64), ("levels", C.c_uint32), ("graph", C.c_uint32),
+                ("kernels_per_generation", C.c_uint32), ("error_generation", C.c_uint32),
+                ("arena_bytes", C.c_uint64), ("workspace_codes", C.c_uint64),
+                ("workspace_values", C.c_uint64), ("autotune_chunk", C.c_uint32 * 8),
+                ("autotune_ms", C.c_float * 8)]
 
 
 class gp_kernel_profile(C.Structure):
@@ -99,6 +116,16 @@ def lib():
             L.gp_profile_enable.argtypes = [C.c_int]
             L.gp_profile_read.argtypes = [P(gp_kernel_profile), C.c_int]
             L.gp_evaluate_noalloc.argtypes = [P(gp_problem), C.c_uint32, vp, P(C.c_uint64), vp, vp, vp, vp]
+            L.gp_generation_create.argtypes = [P(gp_problem), P(gp_generation_params), C.c_uint32,
+                                               P(C.c_uint8), P(C.c_uint64), vp, P(vp)]
+            L.gp_generation_step.argtypes = [vp, C.c_uint32, vp]
+            L.gp_generation_rewind.argtypes = [vp, vp]
+            L.gp_generation_fitness.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_uint32)]
+            L.gp_generation_records.argtypes = [vp, P(gp_xo)]
+            L.gp_generation_trees.argtypes = [vp, P(C.c_uint64), P(C.c_uint8), C.c_uint64]
+            L.gp_generation_get_info.argtypes = [vp, P(gp_generation_info)]
+            L.gp_generation_destroy.argtypes = [vp]
+            L.gp_generation_destroy.restype = None
             _lib = L
     return _lib
 
@@ -278,6 +305,89 @@ def gp_evaluate_noalloc(problem: Problem, offsets, d_nodes: int, d_fitness: int,
                                    C.c_void_p(int(d_case_values)), C.c_void_p(int(d_hits)),
                                    _stream(stream))
     _check(st, "gp_evaluate_noalloc")
+
+
+class Generation:
+    """Owns one gp_generation handle (a device-resident evolving population)."""
+
+    def __init__(self, handle, n_trees, n_cases):
+        self._h = handle
+        self.n_trees = n_trees
+        self.n_cases = n_cases
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and _lib is not None:
+            _lib.gp_generation_destroy(h)
+
+
+def gp_generation_create(problem: Problem, nodes, offsets, seed, tournament_size=7, chunk_nodes=0,
+                         arena_bytes=0, workspace_codes=0, workspace_values=0, use_graph=True,
+                         max_levels=0, stream=None) -> Generation:
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = offsets.shape[0] - 1
+    prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), int(chunk_nodes),
+                               int(arena_bytes), int(workspace_codes), int(workspace_values),
+                               1 if use_graph else 0, int(max_levels))
+    h = C.c_void_p()
+    st = lib().gp_generation_create(C.byref(problem.struct), C.byref(prm), n, _ptr(nodes, C.c_uint8),
+                                    _ptr(offsets, C.c_uint64), _stream(stream), C.byref(h))
+    _check(st, "gp_generation_create")
+    return Generation(h, n, problem.n_cases)
+
+
+def gp_generation_step(g: Generation, n=1, stream=None):
+    _check(lib().gp_generation_step(g._h, int(n), _stream(stream)), "gp_generation_step")
+
+
+def gp_generation_rewind(g: Generation, stream=None):
+    _check(lib().gp_generation_rewind(g._h, _stream(stream)), "gp_generation_rewind")
+
+
+def gp_generation_fitness(g: Generation, case_values=False, hits=False):
+    fit = np.empty(g.n_trees, np.float32)
+    vals = np.empty((g.n_trees, g.n_cases), np.float32) if case_values else None
+    h = np.empty(g.n_trees, np.uint32) if hits else None
+    st = lib().gp_generation_fitness(g._h, _ptr(fit, C.c_float),
+                                     _ptr(vals, C.c_float) if vals is not None else None,
+                                     _ptr(h, C.c_uint32) if h is not None else None)
+    _check(st, "gp_generation_fitness")
+    return fit, vals, h
+
+
+def gp_generation_records(g: Generation):
+    recs = (gp_xo * g.n_trees)()
+    _check(lib().gp_generation_records(g._h, recs), "gp_generation_records")
+    mum = np.array([r.mum for r in recs], np.uint32)
+    dad = np.array([r.dad for r in recs], np.uint32)
+    mp = np.array([r.mum_point for r in recs], np.uint64)
+    dp = np.array([r.dad_point for r in recs], np.uint64)
+    return mum, dad, mp, dp
+
+
+def gp_generation_trees(g: Generation):
+    offs = np.empty(g.n_trees + 1, np.uint64)
+    _check(lib().gp_generation_trees(g._h, _ptr(offs, C.c_uint64), None, 0), "gp_generation_trees")
+    nodes = np.empty(max(int(offs[-1]), 1), np.uint8)
+    _check(lib().gp_generation_trees(g._h, _ptr(offs, C.c_uint64), _ptr(nodes, C.c_uint8), nodes.shape[0]),
+           "gp_generation_trees")
+    return nodes[:int(offs[-1])], offs
+
+
+def gp_generation_get_info(g: Generation) -> dict:
+    i = gp_generation_info()
+    _check(lib().gp_generation_get_info(g._h, C.byref(i)), "gp_generation_get_info")
+    d = {k: getattr(i, k) for k, _ in gp_generation_info._fields_}
+    d["autotune_chunk"] = list(i.autotune_chunk)
+    d["autotune_ms"] = list(i.autotune_ms)
+    return d
+
+
+def gp_generation_destroy(g: Generation):
+    h, g._h = g._h, None
+    if h:
+        lib().gp_generation_destroy(h)
 
 
 def read_all_trees(pop: Population):

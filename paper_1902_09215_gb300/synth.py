@@ -209,9 +209,9 @@ class _Piece:
     leaf position, the piece grafted there."""
     __slots__ = ("codes", "leaves", "kids")
 
-    def __init__(self, codes):
+    def __init__(self, codes, leaves=None):
         self.codes = codes
-        self.leaves = None
+        self.leaves = leaves
         self.kids = {}
 
     def leaf_positions(self):
@@ -243,7 +243,7 @@ def _write_pieces(root: _Piece, out: np.ndarray, at: int) -> int:
     return at
 
 
-def _graft_tree(rng, target, pool, donor_hi, chain=None, chain_depth=0):
+def _graft_tree(rng, target, pool, donor_hi, chain=None, chain_depth=0, pool_leaves=None):
     """The pieces of a tree of exactly `target` nodes grown by repeated
     subtree crossover (Sec. 3.1) whose dad point is the root of a whole
     donor tree and whose mum point is a leaf of the tree grown so far.
@@ -285,7 +285,13 @@ def _graft_tree(rng, target, pool, donor_hi, chain=None, chain_depth=0):
         size = first.shape[0]
     while size < target:
         need = target - size + 1                    # odd: both sizes are odd
-        d = random_tree(rng, int(need)) if need <= donor_hi else pool[int(rng.integers(0, len(pool)))]
+        dl = None
+        if need <= donor_hi:
+            d = random_tree(rng, int(need))
+        else:
+            k = int(rng.integers(0, len(pool)))
+            d = pool[k]
+            dl = pool_leaves[k] if pool_leaves is not None else None
         cum = np.cumsum(free)
         r = int(rng.integers(0, int(cum[-1])))
         j = int(np.searchsorted(cum, r, side="right"))
@@ -295,7 +301,7 @@ def _graft_tree(rng, target, pool, donor_hi, chain=None, chain_depth=0):
             pos = int(leaves[int(rng.integers(0, leaves.shape[0]))])
             if pos not in host.kids:
                 break
-        piece = _Piece(d)
+        piece = _Piece(d, dl)
         host.kids[pos] = piece
         free[j] -= 1
         add(piece)
@@ -312,14 +318,18 @@ def graft_population(seed: int = 4, count: int = 48, lo: int = 10**6, hi: int = 
     log-uniform on [donor_lo, donor_hi]).  The largest tree first follows a
     chain of grafts at the deepest leaf (donors from a second pool, sizes
     [chain_lo, chain_hi]) until its depth reaches `chain_depth`, which makes
-    it deep and stringy.  Returns (nodes, offsets, info) with info =
+    it deep and stringy (no chain when chain_depth <= 0).  Returns (nodes,
+    offsets, info) with info =
     {"sizes", "deep_tree", "chain_depth"}; the nodes array is written in
     place, so memory is one copy of the population."""
     rng = np.random.default_rng(seed)
     sizes = loguniform_sizes(rng, count, lo, hi)
     pool = [random_tree(rng, int(n)) for n in loguniform_sizes(rng, n_donors, donor_lo, donor_hi)]
-    chain_trees = [random_tree(rng, int(n)) for n in loguniform_sizes(rng, n_chain, chain_lo, chain_hi)]
-    chain = (chain_trees, [deepest_leaf(t) for t in chain_trees])
+    chain = None
+    if chain_depth > 0:
+        chain_trees = [random_tree(rng, int(n)) for n in loguniform_sizes(rng, n_chain, chain_lo, chain_hi)]
+        chain = (chain_trees, [deepest_leaf(t) for t in chain_trees])
+    pool_leaves = [np.flatnonzero(d >= LEAF_X) for d in pool]
     deep = int(np.argmax(sizes))
     offsets = np.zeros(count + 1, dtype=np.uint64)
     np.cumsum(sizes.astype(np.uint64), out=offsets[1:])
@@ -327,7 +337,8 @@ def graft_population(seed: int = 4, count: int = 48, lo: int = 10**6, hi: int = 
     reached = 0
     for t in range(count):
         root, r = _graft_tree(rng, int(sizes[t]), pool, donor_hi,
-                              chain if t == deep else None, chain_depth)
+                              chain if (t == deep and chain is not None) else None, chain_depth,
+                              pool_leaves)
         end = _write_pieces(root, nodes, int(offsets[t]))
         assert end == int(offsets[t + 1])
         if t == deep:

@@ -1,0 +1,192 @@
+"""GPU parity for generations made on the device: tournament selection and
+crossover points (identical records), children (identical bytes) and their
+evaluation (bit-exact per case, fitness and hits) against the oracle,
+generation after generation; graph replay against plain launches and other
+chunk sizes; rewind; node limit and capacity errors at the generation the
+oracle predicts."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1902_09215_gb300 import synth
+from tests.gpu_util import first_mismatch, gpu, same_f32  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 1
+
+
+def oracle_step(oracle, nodes, offs, fit, seed, g, prob_tables, tsize=7):
+    """Generation g -> g+1 on the CPU: records, children, their evaluation."""
+    x, y, c = prob_tables
+    sizes = np.diff(offs.astype(np.int64)).astype(np.uint64)
+    recs = oracle.generation_records(fit, sizes, sizes.shape[0], seed=seed, g=g, tsize=tsize)
+    kids, koffs = oracle.crossover_population(nodes, offs, *recs)
+    ref = oracle.eval_population(kids, koffs, x, y, c, n_threads=THREADS)
+    return recs, kids, koffs, ref
+
+
+def assert_same_eval(gp, G, ref):
+    fit, vals, hits = gp.gp_generation_fitness(G, case_values=True, hits=True)
+    assert same_f32(vals, ref["out"]), first_mismatch(vals, ref["out"])
+    assert same_f32(fit, ref["fitness"]), first_mismatch(fit, ref["fitness"])
+    assert np.array_equal(hits, ref["hits"])
+
+
+def test_generations_match_oracle(gpu, oracle):
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=3, count=300, lo=31, hi=32767)
+    seed = 21
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, use_graph=True)
+    info = gpu.gp_generation_get_info(G)
+    assert info["graph"] == 1 and info["kernels_per_generation"] > 0
+    assert info["chunk_nodes"] in [k for k in info["autotune_chunk"] if k]
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+    assert_same_eval(gpu, G, ref)
+    for g in range(3):
+        recs, kids, koffs, ref_next = oracle_step(oracle, nodes, offs, ref["fitness"], seed, g, (x, y, c))
+        gpu.gp_generation_step(G)
+        got = gpu.gp_generation_records(G)
+        for a, b, name in zip(got, recs, ("mum", "dad", "mum_point", "dad_point")):
+            assert np.array_equal(a.astype(np.uint64), b.astype(np.uint64)), (g, name)
+        gn, go = gpu.gp_generation_trees(G)
+        assert np.array_equal(go, koffs) and np.array_equal(gn, kids), g
+        assert_same_eval(gpu, G, ref_next)
+        assert gpu.gp_generation_get_info(G)["generation"] == g + 1
+        nodes, offs, ref = kids, koffs, ref_next
+
+
+def test_graph_and_plain_launches_agree(gpu, oracle):
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=5, count=200, lo=31, hi=20001)
+    runs = []
+    for use_graph, chunk in ((False, 1024), (True, 4096), (True, 2048)):
+        G = gpu.gp_generation_create(prob, nodes, offs, seed=7, chunk_nodes=chunk, use_graph=use_graph)
+        gpu.gp_generation_step(G, 3)
+        tn, to = gpu.gp_generation_trees(G)
+        fit, vals, hits = gpu.gp_generation_fitness(G, case_values=True, hits=True)
+        runs.append((tn, to, fit, vals, hits))
+        gpu.gp_generation_destroy(G)
+    for r in runs[1:]:
+        assert np.array_equal(r[0], runs[0][0]) and np.array_equal(r[1], runs[0][1])
+        assert same_f32(r[2], runs[0][2]) and same_f32(r[3], runs[0][3])
+        assert np.array_equal(r[4], runs[0][4])
+
+
+def test_many_levels_large_trees(gpu, oracle):
+    """Trees up to 3e5 nodes with 1024-node chunks: three or more levels."""
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=8, count=40, lo=31, hi=300001)
+    seed = 99
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=1024, use_graph=True)
+    assert gpu.gp_generation_get_info(G)["levels"] >= 3
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+    assert_same_eval(gpu, G, ref)
+    for g in range(2):
+        recs, kids, koffs, ref_next = oracle_step(oracle, nodes, offs, ref["fitness"], seed, g, (x, y, c))
+        gpu.gp_generation_step(G)
+        gn, go = gpu.gp_generation_trees(G)
+        assert np.array_equal(go, koffs) and np.array_equal(gn, kids), g
+        assert_same_eval(gpu, G, ref_next)
+        nodes, offs, ref = kids, koffs, ref_next
+
+
+def test_rewind_repeats_the_step(gpu):
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=9, count=120, lo=31, hi=8191)
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=3, chunk_nodes=2048)
+    gpu.gp_generation_step(G, 2)
+    t2 = gpu.gp_generation_trees(G)
+    f2 = gpu.gp_generation_fitness(G)[0]
+    gpu.gp_generation_rewind(G)
+    assert gpu.gp_generation_get_info(G)["generation"] == 1
+    gpu.gp_generation_step(G)
+    t2b = gpu.gp_generation_trees(G)
+    assert np.array_equal(t2[0], t2b[0]) and np.array_equal(t2[1], t2b[1])
+    assert same_f32(gpu.gp_generation_fitness(G)[0], f2)
+
+
+def sizes_of(offs):
+    return np.diff(offs.astype(np.int64))
+
+
+def test_node_limit_stops_at_the_right_generation(gpu, oracle):
+    """The oracle's run without a limit gives the largest child of every
+    generation; with the limit set to the largest size seen before the first
+    generation that sets a new record, exactly that generation's step fails
+    and the population stays at the generation before it."""
+    x, y, c = synth.problem()
+    nodes, offs = synth.population_small(seed=1, count=100, max_nodes=63)   # small trees grow
+    seed = 5
+    n0, o0 = nodes, offs
+    ref = oracle.eval_population(n0, o0, x, y, c, n_threads=THREADS)
+    record = int(sizes_of(offs).max())
+    fail_at, limit = None, None
+    for g in range(10):
+        recs, kids, koffs, ref_next = oracle_step(oracle, n0, o0, ref["fitness"], seed, g, (x, y, c))
+        m = int(sizes_of(koffs).max())
+        if g >= 1 and m > record:
+            fail_at, limit = g, record
+            break
+        record = max(record, m)
+        n0, o0, ref = kids, koffs, ref_next
+    if fail_at is None:
+        pytest.skip("no generation set a new size record within 10 generations")
+    prob = gpu.Problem(x, y, c, max_tree_nodes=limit)
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=1024)
+    gpu.gp_generation_step(G, fail_at + 3)          # the steps after the failing one do nothing
+    with pytest.raises(gpu.GpError) as e:
+        gpu.gp_generation_fitness(G)
+    assert e.value.status == gpu.GP_ELIMIT
+    info = gpu.gp_generation_get_info(G)
+    assert info["generation"] == fail_at and info["error_generation"] == fail_at
+
+
+def test_population_buffer_too_small(gpu, oracle):
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    for seed in range(1, 40):
+        nodes, offs = synth.population_loguniform(seed=11, count=60, lo=31, hi=4095)
+        used = int(np.sum((sizes_of(offs) + 15) // 16 * 16)) + 64
+        ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+        recs, kids, koffs, _ = oracle_step(oracle, nodes, offs, ref["fitness"], seed, 0, (x, y, c))
+        need = int(np.sum((sizes_of(koffs) + 15) // 16 * 16)) + 64
+        if need > used:
+            break
+    else:
+        pytest.skip("no seed with a larger generation")
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=1024, arena_bytes=need - 1)
+    gpu.gp_generation_step(G)
+    with pytest.raises(gpu.GpError) as e:
+        gpu.gp_generation_fitness(G)
+    assert e.value.status == gpu.GP_ENOMEM
+    assert gpu.gp_generation_get_info(G)["generation"] == 0
+    # the exact size is enough
+    G2 = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=1024, arena_bytes=need)
+    gpu.gp_generation_step(G2)
+    gn, go = gpu.gp_generation_trees(G2)
+    assert np.array_equal(gn, kids) and np.array_equal(go, koffs)
+
+
+def test_generation_rejects_bad_parameters(gpu):
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_small()
+    for kw in (dict(tournament_size=0), dict(tournament_size=33), dict(chunk_nodes=100),
+               dict(chunk_nodes=1000), dict(max_levels=1)):
+        with pytest.raises(gpu.GpError) as e:
+            gpu.gp_generation_create(prob, nodes, offs, seed=1, **kw)
+        assert e.value.status == gpu.GP_EINVAL
+    bad = nodes.copy()
+    bad[0] = 200                                     # undefined code
+    with pytest.raises(gpu.GpError) as e:
+        gpu.gp_generation_create(prob, bad, offs, seed=1)
+    assert e.value.status == gpu.GP_EMALFORMED
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=1, chunk_nodes=256)
+    with pytest.raises(gpu.GpError):
+        gpu.gp_generation_rewind(G)                  # nothing to undo
