@@ -46,6 +46,22 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (the slowest rank sets the job's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def make_workload(rank: int):
     x, y, c = synth.problem(const_seed=CONST_SEED)
     nodes, offs = synth.population_loguniform(seed=SEED_POP + 1000 * rank, count=N_TREES)
@@ -206,13 +222,8 @@ def run_ours(args):
     launches = gp.gp_kernel_launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     keep.clear()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = child_nodes * prob.n_cases * args.steps * world
-    value = units / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
+    value = weak_scaling_value(child_nodes * prob.n_cases * args.steps, world, total_ms)
 
     # ---- evaluation alone and crossover alone (device time), same flushing
     def timed(fn, reps):
@@ -558,6 +569,113 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# serving: many independent runs, continuous batching, HBM-budget admission
+# ---------------------------------------------------------------------------
+
+SERVE_RUNS, SERVE_RATE = 64, 200.0
+
+
+def serving_workload(n_runs, gens):
+    """Populations of U{48..4000} trees drawn from a shared pool of seeded
+    random trees (odd sizes log-uniform 11..1e5)."""
+    rng = np.random.default_rng(6)
+    pool_sizes = synth.loguniform_sizes(rng, 12000, 11, 100001)
+    pool = [synth.random_tree(rng, int(n)) for n in pool_sizes]
+    runs = []
+    for r in range(n_runs):
+        n = int(rng.integers(48, 4001))
+        pick = rng.integers(0, len(pool), size=n)
+        nodes, offs = synth.pack([pool[int(k)] for k in pick])
+        runs.append((nodes, offs, 5000 + r))
+    return runs
+
+
+def serve_session(gp, prob, runs, gens, budget, max_batch_runs, think_mean_s, seed):
+    """Every run: `gens` one-generation requests in a closed loop with an
+    exponential think time before each; runs close when done (admitting the
+    waiting ones).  Returns wall seconds and the server's statistics."""
+    import threading
+    srv = gp.gp_server_create(prob, hbm_budget_bytes=budget, max_runs=len(runs), max_batch_trees=1 << 20,
+                              max_batch_runs=max_batch_runs, chunk_nodes=8192)
+    ids = [gp.gp_server_open_run(srv, n, o, seed=s) for n, o, s in runs]
+    errors = []
+
+    def client(k, rid):
+        rng = np.random.default_rng(seed + k)
+        for _ in range(gens):
+            if think_mean_s > 0:
+                time.sleep(float(rng.exponential(think_mean_s)))
+            r = gp.gp_server_wait(srv, gp.gp_server_submit(srv, rid, 1))
+            if r["status"] != gp.GP_OK:
+                errors.append(r["status"])
+                break
+        gp.gp_server_close_run(srv, rid)
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=client, args=(k, rid)) for k, rid in enumerate(ids)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    wall = time.perf_counter() - t0
+    st = gp.gp_server_get_stats(srv)
+    gp.gp_server_destroy(srv)
+    if errors:
+        raise RuntimeError(f"serving requests failed: {errors[:5]}")
+    return wall, st
+
+
+def run_serving(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1902_09215_gb300 import gp
+    gp.lib()
+    x, y, c = synth.problem(const_seed=CONST_SEED)
+    prob = gp.Problem(x, y, c)
+    gens = args.serve_gens
+    t0 = time.perf_counter()
+    runs = serving_workload(SERVE_RUNS, gens)
+    build_s = time.perf_counter() - t0
+    per_run = [2 * (2 * int(np.sum((np.diff(o.astype(np.int64)) + 15) // 16 * 16)) + 16 * (len(o) - 1) + (1 << 20))
+               for _, o, _ in runs]
+    budget = int(np.sum(per_run) / 4)                 # about a quarter of the runs fit at once
+    think = SERVE_RUNS / SERVE_RATE
+    with ClockSampler(0) as clk:
+        out = {}
+        for name, mbr, th in (("batched", 0, think), ("one_run_per_batch", 1, think),
+                              ("batched_saturated", 0, 0.0), ("one_run_per_batch_saturated", 1, 0.0)):
+            wall, st = serve_session(gp, prob, runs, gens, budget, mbr, th, 11)
+            out[name] = {
+                "wall_s": wall,
+                "GPops_per_s_wall": st["child_nodes"] * len(x) / wall,
+                "GPops_per_s_device": st["child_nodes"] * len(x) / (st["device_ms"] / 1e3),
+                "latency_p50_ms": st["latency_p50_ms"], "latency_p99_ms": st["latency_p99_ms"],
+                "batches": st["batches"], "mean_runs_per_batch": st["mean_runs_per_batch"],
+                "run_generations": st["run_generations"], "child_nodes": st["child_nodes"],
+                "runs_regrown": st["regrown"], "batch_retries": st["retries"],
+            }
+    b = out["batched_saturated"]
+    line = {
+        "metric": "GPops/s (tree nodes x fitness cases per second), served generations; p50/p99 latency",
+        "value": b["GPops_per_s_wall"], "unit": "GPops/s", "n_gpus": 1, "steps": SERVE_RUNS * gens,
+        "warmup": 0, "ms_per_step": 1e3 * b["wall_s"] / (SERVE_RUNS * gens), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{SERVE_RUNS} independent runs, populations U{{48..4000}} trees drawn from a "
+                               "pool of 12000 seeded random trees (odd sizes log-uniform 11..1e5), 48 Sextic "
+                               f"cases; each run makes {gens} generations, one request per generation in a "
+                               f"closed loop (exponential think time, mean {think:.2f} s = Poisson "
+                               f"{SERVE_RATE:.0f}/s in aggregate; none in the saturated phases)",
+                   "hbm_budget_bytes": budget, "runs_fitting_at_once": "about 1/4",
+                   "population_build_s": build_s},
+        "phases": out,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -565,7 +683,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
-    ap.add_argument("--workload", choices=["step4000"] + sorted(BATCHED), default="step4000",
+    ap.add_argument("--serve-gens", type=int, default=10, help="generations per run in the serving workload")
+    ap.add_argument("--workload", choices=["step4000", "serving"] + sorted(BATCHED), default="step4000",
                     help="step4000 (default): crossover + evaluation of the 4000-tree population; "
                          "the others time whole generations made on the device")
     ap.add_argument("--chunk", type=int, default=0, help="evaluator chunk for the batched workloads (0 = autotune)")
@@ -576,7 +695,7 @@ def main():
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the step4000 workload only"}))
             return
-        run_batched(args)
+        run_serving(args) if args.workload == "serving" else run_batched(args)
         return
     if args.impl == "reference":
         run_reference(args)

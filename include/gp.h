@@ -215,7 +215,8 @@ typedef struct gp_generation_params {
     uint64_t seed;               /* seed of the draws                                   */
     uint32_t tournament_size;    /* 1..32 (7 in the paper)                               */
     uint32_t chunk_nodes;        /* evaluator chunk (multiple of 16, 256..65536);
-                                    0 = autotuned on the initial population              */
+                                    0 = autotuned on the initial population: the fastest
+                                    of 1024..8192 (up to 1e8 nodes) or 4096..16384       */
     uint64_t arena_bytes;        /* capacity of each population buffer; 0 = twice the
                                     initial population plus slack                        */
     uint64_t workspace_codes;    /* upper-tree codes per level; 0 = twice what the
@@ -276,6 +277,84 @@ gp_status gp_generation_trees(gp_generation *g, uint64_t *offsets, uint8_t *node
 
 gp_status gp_generation_get_info(gp_generation *g, gp_generation_info *info);
 void gp_generation_destroy(gp_generation *g);
+
+/* ---- Serving: many independent runs on one GPU (continuous batching).
+ *
+ * A gp_server holds many runs (each a population like a gp_generation, all
+ * on the same problem) in one device heap of hbm_budget_bytes.  A run is
+ * admitted when the heap can hold its two population buffers (in the order
+ * runs were opened); until then it waits, its trees kept on the host.
+ * Clients submit generation requests ("advance run r by k generations") from
+ * any thread; a scheduler thread advances, in each iteration, every run with
+ * a pending request that fits the batch limits by one generation, all of
+ * them in one launch sequence (one CUDA graph), so requests that arrive
+ * while a batch runs join the next one.  Results do not depend on which runs
+ * share a batch (each run's draws and trees are its own).  A workspace
+ * overflow in a batch of several runs makes the scheduler retry them in
+ * smaller batches.  A run whose children outgrow its buffers is moved to
+ * buffers twice as large when the heap has room (until then it waits) and
+ * the generation is made again; a run's other failures (node limit)
+ * fail its pending requests with that status. */
+
+typedef struct gp_server gp_server;
+
+typedef struct gp_server_params {
+    uint64_t hbm_budget_bytes;   /* device heap for the runs' population buffers       */
+    uint32_t max_runs;           /* runs held (admitted) at once, 1..4096                */
+    uint32_t max_batch_runs;     /* runs advanced by one batch (0 = max_runs)            */
+    uint32_t max_batch_trees;    /* trees of all runs in one batch                       */
+    uint32_t chunk_nodes;        /* evaluator chunk (0 = 8192)                           */
+    uint64_t max_batch_nodes;    /* nodes of all runs in one batch (workspace sizing)    */
+    uint64_t workspace_codes;    /* 0 = 8% of max_batch_nodes                            */
+    uint64_t workspace_values;   /* 0 = 3% of max_batch_nodes                            */
+    uint32_t use_graph;          /* nonzero: replay one captured CUDA graph per batch    */
+    uint32_t pad;
+} gp_server_params;
+
+typedef struct gp_server_result {
+    uint64_t run_id, request_id;
+    uint64_t generation;         /* the run's generation when the request completed     */
+    float best_fitness;          /* lowest MAE of the population (NaN ranks worst)       */
+    uint32_t best_tree, best_hits;
+    gp_status status;
+    uint64_t total_nodes;        /* nodes of the population                              */
+    double latency_ms;           /* submit -> completion                                 */
+    double queue_ms;             /* submit -> first batch that served it                 */
+} gp_server_result;
+
+typedef struct gp_server_stats {
+    uint64_t batches, run_generations, requests_done, child_nodes;
+    double device_ms;            /* GPU time of all batches (CUDA events)               */
+    double mean_runs_per_batch;
+    double latency_p50_ms, latency_p99_ms;
+    uint64_t heap_bytes, heap_free;
+    uint32_t runs_admitted, runs_waiting;
+    uint64_t most_level_codes;   /* largest upper-tree code count of one level of a batch */
+    uint64_t most_level_values;  /* largest value-entry count of one level of a batch    */
+    uint64_t retries;            /* runs sent back after a workspace overflow            */
+    uint64_t regrown;            /* runs moved to larger buffers after outgrowing theirs */
+} gp_server_stats;
+
+/* Errors: GP_EINVAL, GP_ENOMEM (budget or workspace), GP_ECUDA. */
+gp_status gp_server_create(const gp_problem *problem, const gp_server_params *params, gp_server **out);
+/* Open a run (copies the trees); admitted when its buffers fit the heap.
+ * params: seed, tournament_size, arena_bytes (0 = twice the trees + slack);
+ * the other fields are ignored.  GP_ENOMEM if the run can never fit. */
+gp_status gp_server_open_run(gp_server *s, const gp_generation_params *params, uint32_t n_trees,
+                             const uint8_t *nodes, const uint64_t *offsets, uint64_t *run_id);
+gp_status gp_server_submit(gp_server *s, uint64_t run_id, uint32_t n_generations, uint64_t *request_id);
+/* Wait for a request (timeout_ms < 0: no limit).  GP_ETIMEOUT if it has not
+ * completed; otherwise GP_OK with the result (result->status is the
+ * request's own outcome). */
+gp_status gp_server_wait(gp_server *s, uint64_t request_id, double timeout_ms, gp_server_result *result);
+/* After the run's requests completed: its current population's results / trees. */
+gp_status gp_server_run_fitness(gp_server *s, uint64_t run_id, float *fitness, float *case_values, uint32_t *hits);
+gp_status gp_server_run_trees(gp_server *s, uint64_t run_id, uint64_t *offsets, uint8_t *nodes, uint64_t cap);
+/* Waits for the run's requests, then frees its buffers (waiting runs may
+ * then be admitted). */
+gp_status gp_server_close_run(gp_server *s, uint64_t run_id);
+gp_status gp_server_get_stats(gp_server *s, gp_server_stats *stats);
+void gp_server_destroy(gp_server *s);
 
 /* ---- Evaluation without allocation.  The paper has no counterpart: this
  * serves callers that cannot allocate device memory while they evaluate,

@@ -1,0 +1,1127 @@
+// The generation engine: tournament selection (Table gp.details: size 7,
+// both parents), subtree crossover with uniform points (Sec. 3.1) and the
+// evaluation of the children (Sec. 2.2), for a batch of independent runs
+// whose populations live in one device heap.  Every count of a batch is in
+// device memory, so a batch is a fixed launch sequence (captured once as a
+// CUDA graph); a run's failure (node limit, its buffer too small) stops that
+// run only, a workspace overflow fails the batch and no run advances.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gp_engine.cuh"
+
+using namespace gpk;
+
+namespace gpe {
+namespace {
+
+constexpr uint32_t kTile = 16384;        // copy tile (bytes)
+constexpr uint32_t kScanT = 256;         // threads of the single-CTA scan kernels
+constexpr uint32_t kBuckets = 40;        // final items ordered by floor(log2(size)), largest first
+constexpr uint64_t kHeapLead = 256;      // heap bytes [0, 256): code 4 ('x'), a one-node tree
+                                         // that idle extent queries point at
+
+__device__ __forceinline__ void run_err(RunDev *R, uint32_t bits)
+{
+    if (atomicOr(&R->err, bits) == 0) R->err_gen = R->gen;
+}
+
+// ---- counter-based draws --------------------------------------------------
+
+// Output i of SplitMix64 seeded with `seed` (Steele, Lea & Flood 2014): the
+// (i+1)-th state of its Weyl sequence through the generator's mixer.
+__device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t draw_counter(uint32_t g, uint32_t c, uint32_t purpose, uint32_t k)
+{
+    return ((uint64_t)g << 40) | ((uint64_t)c << 12) | ((uint64_t)purpose << 9) | ((uint64_t)k << 4);
+}
+
+// Uniform in [0, n): Lemire's multiply-shift, rejecting low words below
+// 2^64 mod n; attempts use counters base .. base+15, the last one is kept.
+__device__ uint64_t bounded(uint64_t seed, uint64_t base, uint64_t n)
+{
+    const uint64_t t = (0ull - n) % n;
+    uint64_t hi = 0;
+    for (uint32_t a = 0; a < 16; ++a) {
+        const uint64_t r = sm64_at(seed, base + a);
+        hi = __umul64hi(r, n);
+        if (r * n >= t) break;
+    }
+    return hi;
+}
+
+// Lowest fitness wins; NaN ranks worst; ties go to the entrant drawn first.
+__device__ uint32_t tournament(const float *__restrict__ fit, uint32_t n_pop, uint64_t seed, uint32_t g,
+                               uint32_t c, uint32_t purpose, uint32_t size)
+{
+    uint32_t best = 0;
+    float best_f = 0.0f;
+    for (uint32_t k = 0; k < size; ++k) {
+        const uint32_t e = (uint32_t)bounded(seed, draw_counter(g, c, purpose, k), n_pop);
+        float f = fit[e];
+        if (isnan(f)) f = __int_as_float(0x7f800000);
+        if (k == 0 || f < best_f) {
+            best = e;
+            best_f = f;
+        }
+    }
+    return best;
+}
+
+// Batch slot of global tree g: the last slot whose first tree is <= g.
+__device__ __forceinline__ uint32_t slot_of(const uint32_t *__restrict__ tree_base, uint32_t n_runs, uint32_t g)
+{
+    uint32_t lo = 0, hi = n_runs;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (tree_base[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ---- selection, child layout, copy bookkeeping ---------------------------
+
+__global__ void select_kernel(BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run,
+                              const uint32_t *__restrict__ tree_base, gp_xo *__restrict__ recs,
+                              ExtentQuery *__restrict__ q)
+{
+    const BatchHead h = ctl->head;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h.mode != kModeGenerate) {
+        if (tid == 0) ctl->n_queries = 0;
+        return;
+    }
+    if (tid == 0) ctl->n_queries = 2 * h.n_trees;
+    for (uint32_t g = tid; g < h.n_trees; g += gridDim.x * blockDim.x) {
+        const uint32_t slot = slot_of(tree_base, h.n_runs, g);
+        RunDev *R = runs + slot_run[slot];
+        const uint32_t c = g - tree_base[slot];
+        if (R->err == 0 && R->gen >= (1u << 24) && c == 0) run_err(R, kGErrGen);
+        if (R->err != 0 || R->gen >= (1u << 24)) {
+            recs[g] = gp_xo{0, 0, 0, 0};
+            q[2 * g] = q[2 * g + 1] = ExtentQuery{0, 1, 0};     // the one-node tree at heap offset 0
+            continue;
+        }
+        const RunBuf &P = R->buf[R->cur];
+        gp_xo r;
+        r.mum = tournament(P.fit, R->n, R->seed, R->gen, c, 0, R->tsize);
+        r.dad = tournament(P.fit, R->n, R->seed, R->gen, c, 1, R->tsize);
+        r.mum_point = bounded(R->seed, draw_counter(R->gen, c, 2, 0), P.size[r.mum]);
+        r.dad_point = bounded(R->seed, draw_counter(R->gen, c, 3, 0), P.size[r.dad]);
+        recs[g] = r;
+        q[2 * g] = ExtentQuery{P.start[r.mum], P.size[r.mum], r.mum_point};
+        q[2 * g + 1] = ExtentQuery{P.start[r.dad], P.size[r.dad], r.dad_point};
+    }
+}
+
+// Block-wide inclusive scan of two 64-bit values per thread (kScanT threads).
+__device__ void block_scan2(uint64_t *sa, uint64_t *sb, uint64_t a, uint64_t b)
+{
+    const uint32_t t = threadIdx.x;
+    sa[t] = a;
+    sb[t] = b;
+    __syncthreads();
+    for (uint32_t off = 1; off < kScanT; off <<= 1) {
+        uint64_t va = 0, vb = 0;
+        if (t >= off) {
+            va = sa[t - off];
+            vb = sb[t - off];
+        }
+        __syncthreads();
+        if (t >= off) {
+            sa[t] += va;
+            sb[t] += vb;
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per batch slot.  Generate: child sizes (child = mum[0,i) ++
+// dad[j,e_d) ++ mum[e_m,n_m)), node limit, 16-byte aligned starts in the
+// run's other buffer, copy tiles; the batch's tree table gets the children.
+// Evaluate: the batch's tree table gets the run's current population.
+// A run that has stopped contributes no trees (size 0).
+__global__ void __launch_bounds__(kScanT) children_kernel(
+    BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run, const uint32_t *__restrict__ tree_base,
+    const gp_xo *__restrict__ recs, const uint64_t *__restrict__ ends, XoChild *__restrict__ kids,
+    uint32_t *__restrict__ tile_local, uint32_t *__restrict__ run_tiles, uint64_t *__restrict__ bstart,
+    uint64_t *__restrict__ bsize)
+{
+    __shared__ uint64_t sa[kScanT], sb[kScanT];
+    __shared__ uint32_t s_bad;
+    __shared__ unsigned long long s_nodes;
+    const BatchHead h = ctl->head;
+    const uint32_t slot = blockIdx.x, t = threadIdx.x;
+    if (slot >= h.n_runs) return;
+    RunDev *R = runs + slot_run[slot];
+    const uint32_t base = tree_base[slot], n = R->n;
+    if (t == 0) {
+        s_bad = 0;
+        s_nodes = 0;
+    }
+    __syncthreads();
+    const bool stopped = R->err != 0 || (h.mode == kModeGenerate && ctl->eval_err[1] != 0);
+    if (stopped || h.mode == kModeEvaluate) {
+        const RunBuf &B = R->buf[R->cur];
+        for (uint32_t c = t; c < n; c += kScanT) {
+            bstart[base + c] = stopped ? 0 : B.start[c];
+            bsize[base + c] = stopped ? 0 : B.size[c];
+        }
+        if (t == 0) run_tiles[slot] = 0;
+        return;
+    }
+    const RunBuf &P = R->buf[R->cur];
+    const RunBuf &Cb = R->buf[R->cur ^ 1];
+    const uint32_t per = (n + kScanT - 1) / kScanT;
+    const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
+    uint64_t a = 0, b = 0, nodes = 0;
+    uint32_t bad = 0;
+    for (uint32_t c = lo; c < hi; ++c) {
+        const gp_xo r = recs[base + c];
+        const uint64_t m = r.mum_point + (ends[2 * (base + c) + 1] - r.dad_point) + (P.size[r.mum] - ends[2 * (base + c)]);
+        if (R->max_nodes && m > R->max_nodes) bad |= kGErrLimit;
+        a += (m + 15) & ~15ull;
+        b += (m + kTile - 1) / kTile;
+        nodes += m;
+    }
+    if (bad) atomicOr(&s_bad, bad);
+    atomicAdd(&s_nodes, (unsigned long long)nodes);
+    block_scan2(sa, sb, a, b);
+    const uint64_t tot_a = sa[kScanT - 1], tot_b = sb[kScanT - 1];
+    uint32_t err = s_bad;
+    if (tot_a + 64 > Cb.cap || tot_b >= 0x7fffffffull) err |= kGErrArena;
+    if (err) {
+        for (uint32_t c = t; c < n; c += kScanT) {
+            bstart[base + c] = 0;
+            bsize[base + c] = 0;
+        }
+        if (t == 0) {
+            run_tiles[slot] = 0;
+            run_err(R, err);
+        }
+        return;
+    }
+    uint64_t ra = sa[t] - a, rb = sb[t] - b;
+    for (uint32_t c = lo; c < hi; ++c) {
+        const uint32_t g = base + c;
+        const gp_xo r = recs[g];
+        const uint64_t em = ends[2 * g], ed = ends[2 * g + 1];
+        const uint64_t m = r.mum_point + (ed - r.dad_point) + (P.size[r.mum] - em);
+        XoChild k;
+        k.dst = Cb.lo + ra;
+        k.n = m;
+        k.head_src = P.start[r.mum];
+        k.i = r.mum_point;
+        k.mid_src = P.start[r.dad] + r.dad_point;
+        k.ld = ed - r.dad_point;
+        k.tail_src = P.start[r.mum] + em;    // tail byte p comes from mum[em + p - i - ld]
+        k.pad = 0;
+        kids[g] = k;
+        Cb.start[c] = Cb.lo + ra;
+        Cb.size[c] = m;
+        bstart[g] = Cb.lo + ra;
+        bsize[g] = m;
+        tile_local[g] = (uint32_t)rb;
+        ra += (m + 15) & ~15ull;
+        rb += (m + kTile - 1) / kTile;
+    }
+    if (t == kScanT - 1) {
+        run_tiles[slot] = (uint32_t)tot_b;
+        R->next_nodes = s_nodes;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->child_nodes), s_nodes);
+    }
+}
+
+// Run tile counts -> exclusive offsets (entry n_runs = all tiles).
+__global__ void run_tiles_scan_kernel(BatchCtl *ctl, uint32_t *run_tiles)
+{
+    if (threadIdx.x != 0) return;
+    const uint32_t n = ctl->head.n_runs;
+    uint64_t s = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t v = run_tiles[i];
+        run_tiles[i] = (uint32_t)s;
+        s += v;
+    }
+    run_tiles[n] = (uint32_t)umin64(s, 0x7fffffffull);
+    ctl->n_tiles = ctl->head.mode == kModeGenerate ? run_tiles[n] : 0;
+}
+
+// ---- evaluation levels ----------------------------------------------------
+
+struct LevelArgs {
+    uint32_t level;
+    uint32_t C;                   // chunk (codes)
+    uint32_t cap_items;
+    uint32_t pad;
+    uint64_t spill_base;          // first dedicated spill entry (after the per-warp areas)
+    uint64_t cap_dedicated;       // dedicated spill entries available
+};
+
+__device__ __forceinline__ uint32_t size_bucket(uint64_t len)
+{
+    const uint32_t b = 63u - (uint32_t)__clzll(len | 1ull);
+    return min(b, kBuckets - 1);
+}
+
+// One CTA.  Level 0: every tree of the batch (size 0: none); a tree of at
+// most C nodes is one final item, a larger one is cut into chunks of C.
+// Level k > 0: every tree that had chunks at level k-1 now has an upper
+// tree of codes [frag_off[first chunk], frag_off[one past its last chunk]);
+// it becomes a final item when it fits one chunk or did not at least halve
+// (a final above C gets a dedicated spill area), otherwise it is cut again.
+// Chunk items come first in tree order (their fragments must be contiguous
+// per tree), then finals from the largest size bucket down.
+__global__ void __launch_bounds__(kScanT) items_kernel(
+    BatchCtl *ctl, LevelArgs A, const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
+    const uint64_t *__restrict__ frag_off, uint64_t *__restrict__ t_lo, uint64_t *__restrict__ t_hi,
+    uint64_t *__restrict__ t_prev, uint32_t *__restrict__ t_first, uint32_t *__restrict__ t_state,
+    EvalItem *__restrict__ items)
+{
+    __shared__ uint32_t s_cnt[kBuckets][kScanT];
+    __shared__ uint64_t sa[kScanT], sb[kScanT];
+    __shared__ uint64_t s_base[kBuckets];
+    __shared__ uint32_t s_err;
+    const uint32_t t = threadIdx.x;
+    const uint32_t n = ctl->head.n_trees, C = A.C;
+    if (ctl->err != 0) {
+        if (t == 0) ctl->n_items = ctl->n_chunks = 0;
+        return;
+    }
+    for (uint32_t b = 0; b < kBuckets; ++b) s_cnt[b][t] = 0;
+    const uint32_t per = (n + kScanT - 1) / kScanT;
+    const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
+
+    // phase 1: this level's range of every open tree (all reads of the old
+    // t_first happen before the barrier; phase 3 rewrites it)
+    for (uint32_t i = lo; i < hi; ++i) {
+        if (A.level == 0) {
+            t_lo[i] = bstart[i];
+            t_hi[i] = bstart[i] + bsize[i];
+            t_prev[i] = ~0ull;
+            t_state[i] = bsize[i] != 0;
+        } else if (t_state[i]) {
+            t_lo[i] = frag_off[t_first[i]];
+            t_hi[i] = frag_off[t_first[i + 1]];
+        }
+    }
+    __syncthreads();
+    // phase 2: chunks, dedicated spill and finals per size bucket
+    uint64_t nch = 0, ded = 0;
+    for (uint32_t i = lo; i < hi; ++i) {
+        if (!t_state[i]) continue;
+        const uint64_t len = t_hi[i] - t_lo[i];
+        if (len <= C || 2 * len > t_prev[i]) {
+            ++s_cnt[size_bucket(len)][t];
+            if (len > C) ded += len;
+        } else {
+            nch += (len + C - 1) / C;
+        }
+    }
+    block_scan2(sa, sb, nch, ded);
+    uint64_t ex_ch = sa[t] - nch, ex_ded = sb[t] - ded;
+    const uint64_t tot_ch = sa[kScanT - 1], tot_ded = sb[kScanT - 1];
+    if (t < kBuckets) {                       // per bucket: exclusive prefix over threads
+        uint32_t run = 0;
+        for (uint32_t j = 0; j < kScanT; ++j) {
+            const uint32_t v = s_cnt[t][j];
+            s_cnt[t][j] = run;
+            run += v;
+        }
+        s_base[t] = run;                      // bucket total for now
+    }
+    __syncthreads();
+    if (t == 0) {
+        uint64_t pos = tot_ch;
+        for (int b = (int)kBuckets - 1; b >= 0; --b) {
+            const uint64_t cnt = s_base[b];
+            s_base[b] = pos;
+            pos += cnt;
+        }
+        uint32_t err = 0;
+        ctl->need_dedicated = max(ctl->need_dedicated, tot_ded);
+        if (pos > A.cap_items) err |= kGErrItems;
+        if (tot_ded > A.cap_dedicated) err |= kGErrSpill;
+        if (err) {
+            atomicOr(&ctl->err, err);
+            ctl->n_items = ctl->n_chunks = 0;
+        } else {
+            ctl->n_items = (uint32_t)pos;
+            ctl->n_chunks = (uint32_t)tot_ch;
+            if (pos) ctl->levels = A.level + 1;
+        }
+        s_err = err;
+    }
+    __syncthreads();
+    if (s_err) return;
+    // phase 3: chunk offsets per tree, final items, states
+    for (uint32_t i = lo; i < hi; ++i) {
+        t_first[i] = (uint32_t)ex_ch;
+        if (!t_state[i]) continue;
+        const uint64_t len = t_hi[i] - t_lo[i];
+        if (len <= C || 2 * len > t_prev[i]) {
+            const uint32_t b = size_bucket(len);
+            EvalItem it{};
+            it.begin = t_lo[i];
+            it.end = t_hi[i];
+            it.tree = i;
+            it.flags = kItemFinal;
+            it.spill_off = kNoSpill;
+            if (len > C) {
+                it.spill_off = A.spill_base + ex_ded;
+                it.spill_cap = len;
+                ex_ded += len;
+            }
+            items[s_base[b] + s_cnt[b][t]++] = it;
+            t_state[i] = 0;
+        } else {
+            t_prev[i] = len;
+            ex_ch += (len + C - 1) / C;
+        }
+    }
+    if (t == kScanT - 1) t_first[n] = (uint32_t)tot_ch;
+}
+
+// Chunk items: item i belongs to the last tree whose first chunk is <= i.
+__global__ void fill_chunks_kernel(const BatchCtl *ctl, uint32_t C, const uint32_t *__restrict__ t_first,
+                                   const uint64_t *__restrict__ t_lo, const uint64_t *__restrict__ t_hi,
+                                   EvalItem *__restrict__ items)
+{
+    const uint32_t n = ctl->n_chunks, n_trees = ctl->head.n_trees;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = n_trees;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (t_first[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        EvalItem it{};
+        it.begin = t_lo[lo] + (uint64_t)(i - t_first[lo]) * C;
+        it.end = umin64(t_hi[lo], it.begin + C);
+        it.tree = lo;
+        it.flags = 0;
+        it.spill_off = kNoSpill;
+        items[i] = it;
+    }
+}
+
+// After a level's plan scan: the level's upper-tree codes and value entries
+// must fit the workspace; the code array is zero-padded past its end (the
+// evaluator reads whole 16-code groups).
+__global__ void check_kernel(BatchCtl *ctl, uint64_t cap_codes, uint64_t cap_values, uint32_t *__restrict__ u_out,
+                             uint32_t idx)
+{
+    __shared__ uint32_t s_ok;
+    const uint64_t codes = ctl->totals[0], vals = ctl->totals[1];
+    if (threadIdx.x == 0) {
+        s_ok = 0;
+        if (ctl->err == 0) {
+            if (codes + 48 > cap_codes || vals > cap_values || vals + kPtCode0 >= 0xffffffffull) {
+                atomicOr(&ctl->err, kGErrWork);
+                ctl->n_items = 0;
+            } else {
+                s_ok = 1;
+                ctl->need_codes[idx] = max(ctl->need_codes[idx], codes);
+                ctl->need_values[idx] = max(ctl->need_values[idx], vals);
+            }
+        } else {
+            ctl->n_items = 0;
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const uint64_t end = ((codes + 15) & ~15ull) + 32;
+    for (uint64_t i = codes + threadIdx.x; i < end; i += blockDim.x) u_out[i] = 0;
+}
+
+// Batch errors so far, as one word.
+__device__ __forceinline__ uint32_t batch_errors(const BatchCtl *ctl)
+{
+    return ctl->err | (ctl->eval_err[0] ? kGErrEval : 0u) | (ctl->eval_err[1] ? kGErrExtent : 0u) |
+           (ctl->n_chunks ? kGErrLevels : 0u);
+}
+
+// Evaluation results from the batch's tables into each run's buffer (the
+// children's in Generate mode, the current one in Evaluate mode).
+__global__ void scatter_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run,
+                               const uint32_t *__restrict__ tree_base, const float *__restrict__ bfit,
+                               const float *__restrict__ bvals, const uint32_t *__restrict__ bhits,
+                               uint32_t n_cases)
+{
+    const BatchHead h = ctl->head;
+    if (batch_errors(ctl)) return;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < h.n_trees; g += gridDim.x * blockDim.x) {
+        const uint32_t slot = slot_of(tree_base, h.n_runs, g);
+        const RunDev *R = runs + slot_run[slot];
+        if (R->err) continue;
+        const RunBuf &B = R->buf[h.mode == kModeGenerate ? (R->cur ^ 1) : R->cur];
+        const uint32_t c = g - tree_base[slot];
+        B.fit[c] = bfit[g];
+        B.hits[c] = bhits[g];
+        for (uint32_t k = 0; k < n_cases; ++k) B.vals[(uint64_t)c * n_cases + k] = bvals[(uint64_t)g * n_cases + k];
+    }
+}
+
+// End of a batch: a batch error stops every run in it (no run advances);
+// otherwise each run still going advances one generation (Generate mode).
+__global__ void finish_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run)
+{
+    const BatchHead h = ctl->head;
+    const uint32_t berr = batch_errors(ctl);
+    for (uint32_t s = threadIdx.x; s < h.n_runs; s += blockDim.x) {
+        RunDev *R = runs + slot_run[s];
+        if (R->err) continue;
+        if (berr) {
+            run_err(R, berr);
+            continue;
+        }
+        R->levels = ctl->levels;
+        if (h.mode == kModeGenerate) {
+            R->gen += 1;
+            R->cur ^= 1u;
+            const uint64_t parents = R->nodes;     // kept for a rewind
+            R->nodes = R->next_nodes;
+            R->next_nodes = parents;
+        }
+    }
+}
+
+__global__ void rebase_kernel(uint64_t *__restrict__ start, uint32_t n, uint64_t delta)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        start[t] += delta;                                  // modulo 2^64: moves down as well
+}
+
+__global__ void rewind_kernel(RunDev *R)
+{
+    if (R->err == 0 && R->gen > 0) {
+        R->gen -= 1;
+        R->cur ^= 1u;
+        const uint64_t children = R->nodes;
+        R->nodes = R->next_nodes;
+        R->next_nodes = children;
+    }
+}
+
+#define GK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return gfail(e_);  \
+    } while (0)
+
+gp_status gfail(cudaError_t e)
+{
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA;
+}
+
+gp_status galloc(std::vector<void *> &v, void **p, size_t bytes)
+{
+    *p = nullptr;
+    GK(cudaMalloc(p, bytes ? bytes : 16));
+    v.push_back(*p);
+    return GP_OK;
+}
+
+void gfree(std::vector<void *> &v)
+{
+    for (void *p : v) cudaFree(p);
+    v.clear();
+}
+
+int lanes_of(uint32_t n_cases)
+{
+    return n_cases <= 16 ? 8 : n_cases <= 32 ? 16 : n_cases <= 48 ? 24 : 32;
+}
+
+}  // namespace
+
+// ---- Engine -----------------------------------------------------------------
+
+Engine::~Engine()
+{
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(device);
+    cudaDeviceSynchronize();
+    for (auto &e : exec)
+        if (e) cudaGraphExecDestroy(e);
+    for (auto &r : runs_host) gfree(r.allocs);
+    gfree(work_allocs_);
+    gfree(allocs_);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cudaSetDevice(cur);
+}
+
+gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t max_runs_, uint32_t max_trees_,
+                       uint32_t levels_max_)
+{
+    cudaGetDevice(&device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    n_cases = problem->n_cases;
+    n_consts = problem->n_consts;
+    lanes = lanes_of(n_cases);
+    div0 = problem->protected_div_value;
+    max_runs = max_runs_;
+    max_trees = max_trees_;
+    levels_max = levels_max_;
+    heap_bytes = heap_bytes_;
+    GK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    // launch shape as in gp_evaluate
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    while (W > 1 && eval_smem_bytes(lanes, (int)W, (int)K, false) > (size_t)maxsm) --W;
+    Wu = std::min<uint32_t>(W, 16);
+    while (Wu > 1 && eval_smem_bytes(lanes, (int)Wu, (int)Ku, true) > (size_t)maxsm) --Wu;
+    smem = eval_smem_bytes(lanes, (int)W, (int)K, false);
+    smem_u = eval_smem_bytes(lanes, (int)Wu, (int)Ku, true);
+    if (smem > (size_t)maxsm || smem_u > (size_t)maxsm) return GP_EINVAL;
+    GK(eval_prepare_at_least(lanes, false, smem));
+    GK(eval_prepare_at_least(lanes, true, smem_u));
+
+    auto &v = allocs_;
+    gp_status st;
+    if ((st = galloc(v, (void **)&heap, kHeapLead + heap_bytes + 64))) return st;
+    GK(cudaMemset(heap, 4, kHeapLead));                     // the idle queries' one-node tree
+    free_.assign(1, {kHeapLead, heap_bytes});
+    if ((st = galloc(v, (void **)&runs_dev, sizeof(RunDev) * max_runs))) return st;
+    GK(cudaMemset(runs_dev, 0, sizeof(RunDev) * max_runs));
+    runs_host.assign(max_runs, RunHost{});
+    if ((st = galloc(v, (void **)&ctl, sizeof(BatchCtl)))) return st;
+    GK(cudaMemset(ctl, 0, sizeof(BatchCtl)));
+    const uint64_t T = max_trees;
+    if ((st = galloc(v, (void **)&slot_run_, sizeof(uint32_t) * max_runs))) return st;
+    if ((st = galloc(v, (void **)&tree_base_, sizeof(uint32_t) * (max_runs + 1)))) return st;
+    if ((st = galloc(v, (void **)&run_tiles_, sizeof(uint32_t) * (max_runs + 1)))) return st;
+    if ((st = galloc(v, (void **)&recs_, sizeof(gp_xo) * T))) return st;
+    if ((st = galloc(v, (void **)&q_, sizeof(ExtentQuery) * 2 * T))) return st;
+    if ((st = galloc(v, (void **)&ends_, sizeof(uint64_t) * 2 * T))) return st;
+    if ((st = galloc(v, (void **)&kids_, sizeof(XoChild) * T))) return st;
+    if ((st = galloc(v, (void **)&tile_local_, sizeof(uint32_t) * T))) return st;
+    if ((st = galloc(v, (void **)&bstart_, sizeof(uint64_t) * T))) return st;
+    if ((st = galloc(v, (void **)&bsize_, sizeof(uint64_t) * T))) return st;
+    if ((st = galloc(v, (void **)&bfit_, sizeof(float) * T))) return st;
+    if ((st = galloc(v, (void **)&bvals_, sizeof(float) * T * n_cases))) return st;
+    if ((st = galloc(v, (void **)&bhits_, sizeof(uint32_t) * T))) return st;
+    if ((st = galloc(v, (void **)&t_lo_, sizeof(uint64_t) * T))) return st;
+    if ((st = galloc(v, (void **)&t_hi_, sizeof(uint64_t) * T))) return st;
+    if ((st = galloc(v, (void **)&t_prev_, sizeof(uint64_t) * T))) return st;
+    if ((st = galloc(v, (void **)&t_first_, sizeof(uint32_t) * (T + 1)))) return st;
+    if ((st = galloc(v, (void **)&t_state_, sizeof(uint32_t) * T))) return st;
+    if ((st = galloc(v, (void **)&x_, sizeof(float) * 2 * lanes))) return st;
+    if ((st = galloc(v, (void **)&y_, sizeof(float) * 2 * lanes))) return st;
+    if ((st = galloc(v, (void **)&c_, sizeof(float) * (n_consts + 1)))) return st;
+    std::vector<float> hx(2 * lanes, 0.f), hy(2 * lanes, 0.f);
+    std::memcpy(hx.data(), problem->x, sizeof(float) * n_cases);
+    std::memcpy(hy.data(), problem->y, sizeof(float) * n_cases);
+    GK(cudaMemcpy(x_, hx.data(), sizeof(float) * hx.size(), cudaMemcpyHostToDevice));
+    GK(cudaMemcpy(y_, hy.data(), sizeof(float) * hy.size(), cudaMemcpyHostToDevice));
+    if (n_consts) GK(cudaMemcpy(c_, problem->consts, sizeof(float) * n_consts, cudaMemcpyHostToDevice));
+    return GP_OK;
+}
+
+uint64_t Engine::heap_alloc(uint64_t bytes)
+{
+    bytes = (bytes + 255) & ~255ull;
+    for (size_t i = 0; i < free_.size(); ++i) {
+        if (free_[i].second >= bytes) {
+            const uint64_t off = free_[i].first;
+            free_[i].first += bytes;
+            free_[i].second -= bytes;
+            if (free_[i].second == 0) free_.erase(free_.begin() + (long)i);
+            return off;
+        }
+    }
+    return ~0ull;
+}
+
+void Engine::heap_release(uint64_t off, uint64_t bytes)
+{
+    bytes = (bytes + 255) & ~255ull;
+    auto it = std::lower_bound(free_.begin(), free_.end(), std::make_pair(off, (uint64_t)0));
+    it = free_.insert(it, {off, bytes});
+    // merge with the next and the previous block
+    auto nx = it + 1;
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+        auto pv = it - 1;
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            free_.erase(it);
+        }
+    }
+}
+
+uint64_t Engine::heap_free() const
+{
+    uint64_t s = 0;
+    for (auto &f : free_) s += f.second;
+    return s;
+}
+
+uint64_t Engine::heap_largest_free() const
+{
+    uint64_t m = 0;
+    for (auto &f : free_) m = std::max(m, f.second);
+    return m;
+}
+
+gp_status Engine::open_run(uint32_t n, uint64_t arena_cap, uint64_t seed, uint32_t tsize, uint64_t max_nodes,
+                           uint32_t *run)
+{
+    uint32_t r = 0;
+    while (r < max_runs && runs_host[r].used) ++r;
+    if (r == max_runs || n == 0 || n > max_trees) return r == max_runs ? GP_ENOMEM : GP_EINVAL;
+    // (allocations are rounded up to 256 bytes; the capacity checked is the
+    // one asked for)
+    const uint64_t lo0 = heap_alloc(arena_cap);
+    if (lo0 == ~0ull) return GP_ENOMEM;
+    const uint64_t lo1 = heap_alloc(arena_cap);
+    if (lo1 == ~0ull) {
+        heap_release(lo0, arena_cap);
+        return GP_ENOMEM;
+    }
+    RunHost &H = runs_host[r];
+    H = RunHost{};
+    H.used = true;
+    H.n = n;
+    H.arena_cap = arena_cap;
+    H.lo[0] = lo0;
+    H.lo[1] = lo1;
+    RunDev D{};
+    D.seed = seed;
+    D.max_nodes = max_nodes;
+    D.n = n;
+    D.tsize = tsize;
+    gp_status st = GP_OK;
+    for (int b = 0; b < 2 && !st; ++b) {
+        RunBuf &B = D.buf[b];
+        B.lo = H.lo[b];
+        B.cap = arena_cap;
+        if ((st = galloc(H.allocs, (void **)&B.start, sizeof(uint64_t) * n))) break;
+        if ((st = galloc(H.allocs, (void **)&B.size, sizeof(uint64_t) * n))) break;
+        if ((st = galloc(H.allocs, (void **)&B.fit, sizeof(float) * n))) break;
+        if ((st = galloc(H.allocs, (void **)&B.vals, sizeof(float) * (uint64_t)n * n_cases))) break;
+        if ((st = galloc(H.allocs, (void **)&B.hits, sizeof(uint32_t) * n))) break;
+    }
+    if (!st && cudaMemcpy(runs_dev + r, &D, sizeof(D), cudaMemcpyHostToDevice) != cudaSuccess) st = GP_ECUDA;
+    if (st) {
+        close_run(r);
+        return st;
+    }
+    *run = r;
+    return GP_OK;
+}
+
+void Engine::close_run(uint32_t r)
+{
+    if (r >= max_runs || !runs_host[r].used) return;
+    cudaDeviceSynchronize();
+    RunHost &H = runs_host[r];
+    heap_release(H.lo[0], H.arena_cap);
+    heap_release(H.lo[1], H.arena_cap);
+    gfree(H.allocs);
+    H = RunHost{};
+    RunDev D{};
+    cudaMemcpy(runs_dev + r, &D, sizeof(D), cudaMemcpyHostToDevice);
+}
+
+gp_status Engine::grow_run(uint32_t r, uint64_t arena_cap, cudaStream_t s)
+{
+    if (r >= max_runs || !runs_host[r].used) return GP_EINVAL;
+    RunHost &H = runs_host[r];
+    if (arena_cap <= H.arena_cap) return GP_EINVAL;
+    const uint64_t lo0 = heap_alloc(arena_cap);
+    if (lo0 == ~0ull) return GP_ENOMEM;
+    const uint64_t lo1 = heap_alloc(arena_cap);
+    if (lo1 == ~0ull) {
+        heap_release(lo0, arena_cap);
+        return GP_ENOMEM;
+    }
+    const uint64_t lo[2] = {lo0, lo1};
+    RunDev D{};
+    gp_status st = read_run(r, &D, s);
+    if (st) return st;
+    const uint32_t c = D.cur;
+    GK(cudaMemcpyAsync(heap + lo[c], heap + H.lo[c], H.arena_cap, cudaMemcpyDeviceToDevice, s));
+    rebase_kernel<<<std::max<uint32_t>(1, std::min<uint32_t>((H.n + 255) / 256, sms * 4)), 256, 0, s>>>(
+        D.buf[c].start, H.n, lo[c] - H.lo[c]);
+    GK(cudaGetLastError());
+    for (int b = 0; b < 2; ++b) {
+        D.buf[b].lo = lo[b];
+        D.buf[b].cap = arena_cap;
+    }
+    GK(cudaMemcpyAsync(runs_dev + r, &D, sizeof(D), cudaMemcpyHostToDevice, s));
+    GK(cudaStreamSynchronize(s));
+    heap_release(H.lo[0], H.arena_cap);
+    heap_release(H.lo[1], H.arena_cap);
+    H.lo[0] = lo0;
+    H.lo[1] = lo1;
+    H.arena_cap = arena_cap;
+    return GP_OK;
+}
+
+gp_status Engine::load_run(uint32_t r, const uint8_t *nodes, const uint64_t *offsets, cudaStream_t s)
+{
+    if (r >= max_runs || !runs_host[r].used) return GP_EINVAL;
+    RunHost &H = runs_host[r];
+    const uint32_t n = H.n;
+    std::vector<uint64_t> hstart(n), hsize(n);
+    uint64_t pos = 0;
+    for (uint32_t t = 0; t < n; ++t) {
+        if (offsets[t + 1] <= offsets[t]) return GP_EINVAL;
+        hsize[t] = offsets[t + 1] - offsets[t];
+        hstart[t] = H.lo[0] + pos;
+        pos = (pos + hsize[t] + 15) & ~15ull;
+    }
+    if (pos + 64 > H.arena_cap) return GP_ENOMEM;
+    // upload and validate through the population API, then take its layout
+    // (the same 16-byte aligned starts)
+    gp_problem pr{};
+    std::vector<float> dummy(n_cases, 0.f), cz(n_consts + 1, 0.f);
+    pr.n_cases = n_cases;
+    pr.x = dummy.data();
+    pr.y = dummy.data();
+    pr.n_consts = n_consts;
+    pr.consts = cz.data();
+    pr.protected_div_value = div0;
+    gp_population *tmp = nullptr;
+    gp_status st = gp_create_population(&pr, n, nodes, offsets, s, &tmp);
+    if (st) return st;
+    gp_population_info pi{};
+    gp_population_get_info(tmp, &pi);
+    RunDev D{};
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(heap + H.lo[0], pi.d_nodes, pos, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(&D, runs_dev + r, sizeof(D), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(D.buf[0].start, hstart.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D.buf[0].size, hsize.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice);
+    D.gen = 0;
+    D.cur = 0;
+    D.err = 0;
+    D.err_gen = 0;
+    D.nodes = offsets[n];
+    if (e == cudaSuccess) e = cudaMemcpy(runs_dev + r, &D, sizeof(D), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    gp_destroy_population(tmp);
+    // the upload's buffers went back to the stream-ordered pool, which keeps
+    // freed memory: hand it back so the engine's own allocations can use it
+    cudaMemPool_t pool;
+    if (cudaDeviceSynchronize() == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess)
+        cudaMemPoolTrimTo(pool, 0);
+    return e == cudaSuccess ? GP_OK : gfail(e);
+}
+
+gp_status Engine::set_workspace(uint32_t C, const uint64_t cap_codes[2], const uint64_t cap_values[2],
+                                uint64_t cap_dedicated, uint64_t cap_items)
+{
+    cudaDeviceSynchronize();
+    gfree(work_allocs_);
+    w = Work{};
+    w.C = C;
+    for (int k = 0; k < 2; ++k) {
+        w.cap_codes[k] = cap_codes[k];
+        w.cap_values[k] = cap_values[k];
+    }
+    w.cap_items = cap_items;
+    w.cap_dedicated = cap_dedicated;
+    if (w.cap_items > 0xffffffffull) return GP_ENOMEM;
+    const uint64_t warps = (uint64_t)sms * std::max(W, Wu);
+    w.spill_per_warp = C;
+    w.spill_base = warps * C;
+    auto &v = work_allocs_;
+    gp_status st;
+    if ((st = galloc(v, (void **)&w.items, sizeof(EvalItem) * w.cap_items))) return st;
+    if ((st = galloc(v, (void **)&w.plan, sizeof(PlanOut) * w.cap_items))) return st;
+    if ((st = galloc(v, (void **)&w.frag_off, sizeof(uint64_t) * (w.cap_items + 1)))) return st;
+    for (int k = 0; k < 2; ++k) {
+        if ((st = galloc(v, (void **)&w.codes[k], sizeof(uint32_t) * (cap_codes[k] + 64)))) return st;
+        if ((st = galloc(v, (void **)&w.vals[k], sizeof(float2) * (cap_values[k] * lanes + 1)))) return st;
+    }
+    if ((st = galloc(v, (void **)&w.spill, sizeof(float2) * lanes * (w.spill_base + w.cap_dedicated)))) return st;
+    // the graphs captured the old workspace
+    for (auto &e : exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    return GP_OK;
+}
+
+gp_status Engine::write_head(uint32_t mode, const std::vector<uint32_t> &runs, cudaStream_t s)
+{
+    if (runs.empty() || runs.size() > max_runs) return GP_EINVAL;
+    std::vector<uint32_t> base(runs.size() + 1);
+    uint64_t tot = 0;
+    for (size_t i = 0; i < runs.size(); ++i) {
+        if (runs[i] >= max_runs || !runs_host[runs[i]].used) return GP_EINVAL;
+        base[i] = (uint32_t)tot;
+        tot += runs_host[runs[i]].n;
+    }
+    if (tot > max_trees) return GP_EINVAL;
+    if (mode == last_mode_ && runs == last_runs_) return GP_OK;     // already on the device
+    base[runs.size()] = (uint32_t)tot;
+    BatchHead h{mode, (uint32_t)runs.size(), (uint32_t)tot, 0};
+    // pageable sources: each copy has consumed its source when the call returns
+    GK(cudaMemcpyAsync(&ctl->head, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    GK(cudaMemcpyAsync(slot_run_, runs.data(), sizeof(uint32_t) * runs.size(), cudaMemcpyHostToDevice, s));
+    GK(cudaMemcpyAsync(tree_base_, base.data(), sizeof(uint32_t) * base.size(), cudaMemcpyHostToDevice, s));
+    last_mode_ = mode;
+    last_runs_ = runs;
+    return GP_OK;
+}
+
+gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
+{
+    uint32_t nl = 0;
+    for (uint32_t level = 0; level < levels_max; ++level) {
+        const bool wide = level > 0;
+        const int k = level & 1;
+        LevelArgs A{level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu), 0, w.spill_base,
+                    w.cap_dedicated};
+        items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
+                                          t_state_, w.items);
+        GK(cudaGetLastError());
+        if (sizing) {
+            // a dedicated spill pool too small for this level's oversized
+            // finals: grow it, clear the error and build the level again
+            // (the kernel changes nothing else when it raises that error)
+            BatchCtl c{};
+            GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+            GK(cudaStreamSynchronize(s));
+            if (c.err == kGErrSpill) {
+                const uint64_t nd = std::max<uint64_t>(2 * c.need_dedicated, w.cap_dedicated);
+                void *p = nullptr;
+                GK(cudaMalloc(&p, sizeof(float2) * lanes * (w.spill_base + nd)));
+                work_allocs_.push_back(p);
+                w.spill = (float2 *)p;
+                w.cap_dedicated = nd;
+                A.cap_dedicated = nd;
+                GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
+                items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
+                                                  t_first_, t_state_, w.items);
+                GK(cudaGetLastError());
+            }
+        }
+        fill_chunks_kernel<<<sms * 4, 256, 0, s>>>(ctl, w.C, t_first_, t_lo_, t_hi_, w.items);
+        GK(cudaGetLastError());
+        const void *codes = wide ? (const void *)w.codes[(level - 1) & 1] : (const void *)heap;
+        GK(launch_plan_dev(wide, codes, w.items, (uint32_t)w.cap_items, &ctl->n_chunks, w.plan, sms, s));
+        GK(launch_plan_scan_dev(w.items, w.plan, &ctl->n_chunks, w.frag_off, ctl->totals, s));
+        nl += 4;
+        if (sizing) {
+            uint64_t tot[2];
+            uint32_t err = 0, n_items = 0;
+            GK(cudaMemcpyAsync(tot, ctl->totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
+            GK(cudaMemcpyAsync(&err, &ctl->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+            GK(cudaMemcpyAsync(&n_items, &ctl->n_items, sizeof(n_items), cudaMemcpyDeviceToHost, s));
+            GK(cudaStreamSynchronize(s));
+            if (err || n_items == 0) break;
+            if (tot[0] + 48 > w.cap_codes[k] || tot[1] > w.cap_values[k]) {
+                // grow this level's output buffers; they hold nothing still
+                // needed (the outputs of level - 2)
+                const uint64_t nc = std::max<uint64_t>(w.cap_codes[k], tot[0] + tot[0] / 8 + 1024);
+                const uint64_t nv = std::max<uint64_t>(w.cap_values[k], tot[1] + tot[1] / 8 + 1024);
+                void *pc = nullptr, *pv = nullptr;
+                const char *vb = std::getenv("GP_VERBOSE");
+                if (vb && vb[0] == '1')
+                    std::fprintf(stderr, "engine sizing: level %u needs %llu codes, %llu value entries (%.1f GB)\n",
+                                 level, (unsigned long long)tot[0], (unsigned long long)tot[1],
+                                 (double)nv * lanes * 8 / 1e9);
+                GK(cudaMalloc(&pc, sizeof(uint32_t) * (nc + 64)));
+                work_allocs_.push_back(pc);
+                GK(cudaMalloc(&pv, sizeof(float2) * (nv * lanes + 1)));
+                work_allocs_.push_back(pv);
+                w.codes[k] = (uint32_t *)pc;
+                w.vals[k] = (float2 *)pv;
+                w.cap_codes[k] = nc;
+                w.cap_values[k] = nv;
+            }
+        }
+        check_kernel<<<1, 64, 0, s>>>(ctl, w.cap_codes[k], w.cap_values[k], w.codes[k], (uint32_t)k);
+        GK(cudaGetLastError());
+        EvalParams p{};
+        p.codes = codes;
+        p.items = w.items;
+        p.n_items = (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu);
+        p.n_items_dev = &ctl->n_items;
+        p.counter = &ctl->counter[level];
+        p.x = x_;
+        p.y = y_;
+        p.consts = c_;
+        p.n_cases = n_cases;
+        p.n_consts = n_consts;
+        p.div0 = div0;
+        p.window = wide ? Ku : K;
+        p.pt_in = wide ? w.vals[(level - 1) & 1] : nullptr;
+        p.pt_out = w.vals[k];
+        p.u_out = w.codes[k];
+        p.values = bvals_;
+        p.fitness = bfit_;
+        p.hits = bhits_;
+        p.spill = w.spill;
+        p.spill_per_warp = w.spill_per_warp;
+        p.err = &ctl->eval_err[0];
+        GK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s));
+        nl += 2;
+    }
+    if (launches) *launches += nl;
+    return GP_OK;
+}
+
+gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint32_t *launches)
+{
+    (void)mode;
+    uint32_t nl = 0;
+    GK(cudaMemsetAsync(ctl->counter, 0, sizeof(ctl->counter), s));
+    // err, n_queries, n_tiles, n_items, n_chunks, levels, eval_err[4]
+    GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t) * 10, s));
+    GK(cudaMemsetAsync(&ctl->child_nodes, 0, sizeof(uint64_t), s));
+    const uint32_t blocks = std::max<uint32_t>(1, std::min<uint32_t>((max_trees + 127) / 128, sms * 8));
+    select_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, recs_, q_);
+    GK(cudaGetLastError());
+    GK(launch_extent_dev(heap, q_, 2 * max_trees, &ctl->n_queries, ends_, &ctl->eval_err[1], sms, s));
+    children_kernel<<<max_runs, kScanT, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, recs_, ends_, kids_,
+                                                 tile_local_, run_tiles_, bstart_, bsize_);
+    GK(cudaGetLastError());
+    run_tiles_scan_kernel<<<1, 32, 0, s>>>(ctl, run_tiles_);
+    GK(cudaGetLastError());
+    GK(launch_xo_copy_runs(heap, kids_, tile_local_, tree_base_, run_tiles_, &ctl->head.n_runs, &ctl->n_tiles,
+                           kTile, sms, s));
+    nl += 5;
+    gp_status st = enqueue_eval(s, sizing, &nl);
+    if (st) return st;
+    const uint32_t sblocks = std::max<uint32_t>(1, std::min<uint32_t>((max_trees + 255) / 256, sms * 4));
+    scatter_kernel<<<sblocks, 256, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, bfit_, bvals_, bhits_, n_cases);
+    GK(cudaGetLastError());
+    finish_kernel<<<1, 256, 0, s>>>(ctl, runs_dev, slot_run_);
+    GK(cudaGetLastError());
+    nl += 2;
+    if (launches) *launches = nl;
+    return GP_OK;
+}
+
+gp_status Engine::enqueue(uint32_t mode, const std::vector<uint32_t> &runs, cudaStream_t s, bool sizing,
+                          uint32_t *launches)
+{
+    gp_status st = write_head(mode, runs, s);
+    if (st) return st;
+    return enqueue_body(mode, s, sizing, launches);
+}
+
+gp_status Engine::capture(uint32_t mode)
+{
+    if (mode > 1) return GP_EINVAL;
+    if (exec[mode]) {
+        cudaGraphExecDestroy(exec[mode]);
+        exec[mode] = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    GK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    gp_status st = enqueue_body(mode, cap_stream, false, nullptr);
+    cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    GK(e);
+    e = cudaGraphInstantiate(&exec[mode], graph, 0);
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    uint32_t kernels = 0;
+    if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess) {
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+        }
+    }
+    cudaGraphDestroy(graph);
+    GK(e);
+    kernels_per_batch[mode] = kernels;
+    return GP_OK;
+}
+
+gp_status Engine::launch_graph(uint32_t mode, const std::vector<uint32_t> &runs, cudaStream_t s)
+{
+    if (mode > 1 || !exec[mode]) return GP_EINVAL;
+    gp_status st = write_head(mode, runs, s);
+    if (st) return st;
+    GK(cudaGraphLaunch(exec[mode], s));
+    return GP_OK;
+}
+
+gp_status Engine::read_run(uint32_t r, RunDev *out, cudaStream_t s)
+{
+    if (r >= max_runs) return GP_EINVAL;
+    GK(cudaMemcpyAsync(out, runs_dev + r, sizeof(RunDev), cudaMemcpyDeviceToHost, s));
+    GK(cudaStreamSynchronize(s));
+    return GP_OK;
+}
+
+gp_status Engine::read_ctl(BatchCtl *out, cudaStream_t s)
+{
+    GK(cudaMemcpyAsync(out, ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+    GK(cudaStreamSynchronize(s));
+    return GP_OK;
+}
+
+gp_status Engine::rewind(uint32_t r, cudaStream_t s)
+{
+    if (r >= max_runs) return GP_EINVAL;
+    rewind_kernel<<<1, 1, 0, s>>>(runs_dev + r);
+    GK(cudaGetLastError());
+    return GP_OK;
+}
+
+gp_status Engine::copy_records(gp_xo *out, uint32_t first, uint32_t n)
+{
+    if ((uint64_t)first + n > max_trees) return GP_EINVAL;
+    GK(cudaDeviceSynchronize());
+    GK(cudaMemcpy(out, recs_ + first, sizeof(gp_xo) * n, cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+gp_status Engine::copy_trees(const RunBuf &B, uint32_t n, uint64_t *offsets, uint8_t *nodes, uint64_t cap)
+{
+    std::vector<uint64_t> hs(n), hz(n);
+    GK(cudaDeviceSynchronize());
+    GK(cudaMemcpy(hs.data(), B.start, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+    GK(cudaMemcpy(hz.data(), B.size, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+    offsets[0] = 0;
+    for (uint32_t t = 0; t < n; ++t) offsets[t + 1] = offsets[t] + hz[t];
+    if (!nodes) return GP_OK;
+    if (cap < offsets[n]) return GP_EINVAL;
+    // the trees of a buffer are packed in order with 16-byte aligned starts:
+    // one copy of the whole span, then close the gaps on the host
+    const uint64_t span = n ? hs[n - 1] + hz[n - 1] - hs[0] : 0;
+    std::vector<uint8_t> tmp(span);
+    if (span) GK(cudaMemcpy(tmp.data(), heap + hs[0], span, cudaMemcpyDeviceToHost));
+    for (uint32_t t = 0; t < n; ++t) std::memcpy(nodes + offsets[t], tmp.data() + (hs[t] - hs[0]), hz[t]);
+    return GP_OK;
+}
+
+gp_status Engine::clear_error(uint32_t r, cudaStream_t s)
+{
+    if (r >= max_runs) return GP_EINVAL;
+    GK(cudaMemsetAsync(&runs_dev[r].err, 0, sizeof(uint32_t), s));
+    return GP_OK;
+}
+
+}  // namespace gpe

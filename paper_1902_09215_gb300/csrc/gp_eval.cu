@@ -758,6 +758,27 @@ __device__ __forceinline__ Xfer xfer_after(Xfer first, Xfer then) {
 }
 constexpr int64_t kNegInf = -(int64_t(1) << 60);
 
+// Calls f(code) for the codes at positions hi-1 down to lo, reading whole
+// aligned 16-byte words (code arrays are 16-byte aligned and readable one
+// word past either end of any item).
+template <typename Code, typename F>
+__device__ __forceinline__ void codes_reverse(const Code *__restrict__ codes, uint64_t lo, uint64_t hi, F &&f)
+{
+    constexpr uint32_t PER = 16 / sizeof(Code);
+    if (hi <= lo) return;
+    const uint64_t wlo = lo / PER;
+    for (uint64_t w = (hi - 1) / PER + 1; w-- > wlo;) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(codes) + w);
+        const uint32_t word[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = (int)PER - 1; j >= 0; --j) {
+            const uint64_t p = w * PER + (uint64_t)j;
+            if (p >= lo && p < hi)
+                f(sizeof(Code) == 1 ? (word[j >> 2] >> (8 * (j & 3))) & 0xFFu : word[j & 3]);
+        }
+    }
+}
+
 // One warp per fragment item: counts the codes and value-buffer entries the
 // chunk will emit, replaying exactly the evaluator's spine rule.
 template <typename Code>
@@ -775,11 +796,10 @@ __global__ void plan_kernel(const Code *__restrict__ codes, const EvalItem *__re
     const uint64_t hi = umin64(lo + seg, it.end);
 
     Xfer f{0, kNegInf};
-    for (uint64_t p = hi; p > lo; --p) {
-        const uint32_t c = codes[p - 1];
+    codes_reverse(codes, lo, hi, [&](uint32_t c) {
         if (c >= 4) f = Xfer{f.d + 1, f.c + 1};
         else f = Xfer{f.d - 1, max(f.c - 1, (int64_t)0)};
-    }
+    });
     // suffix composition: G_lane = F_lane after F_{lane+1} after ... F_31
     Xfer G = f;
     for (int off = 1; off < 32; off <<= 1) {
@@ -796,8 +816,7 @@ __global__ void plan_kernel(const Code *__restrict__ codes, const EvalItem *__re
     uint32_t spine = 0, spine1 = 0, spine1_pt = 0;
     int64_t mx = kn;
     uint32_t prev = (hi < it.end) ? (uint32_t)codes[hi] : 0xFFFFFFFFu;
-    for (uint64_t p = hi; p > lo; --p) {
-        const uint32_t c = codes[p - 1];
+    codes_reverse(codes, lo, hi, [&](uint32_t c) {
         if (c >= 4) {
             ++kn;
             mx = max(mx, kn);
@@ -812,7 +831,7 @@ __global__ void plan_kernel(const Code *__restrict__ codes, const EvalItem *__re
             kn = 0;
         }
         prev = c;
-    }
+    });
     const int64_t kn_final = __shfl_sync(0xffffffffu, kn, 0);
     uint32_t a = spine + spine1, bcount = spine1_pt;
     for (int off = 16; off > 0; off >>= 1) {

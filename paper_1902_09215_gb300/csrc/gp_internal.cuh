@@ -141,6 +141,11 @@ cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32
                               cudaStream_t s);
 // Copy of children whose tiles are numbered on the device: child c owns
 // tiles [tile_base[c], tile_base[c+1]); *n_tiles_dev tiles in all.
+// Children of a batch of runs, all in one heap (src = dst = heap).
+cudaError_t launch_xo_copy_runs(uint8_t *heap, const XoChild *kids, const uint32_t *tile_local,
+                                const uint32_t *tree_base, const uint32_t *run_tile_base,
+                                const uint32_t *n_runs_dev, const uint32_t *n_tiles_dev, uint32_t tile_bytes,
+                                int sms, cudaStream_t s);
 cudaError_t launch_xo_copy_dev(const uint8_t *src, uint8_t *dst, const XoChild *children,
                                const uint32_t *tile_base, uint32_t n_children,
                                const uint32_t *n_tiles_dev, uint32_t tile_bytes, int sms,

@@ -180,6 +180,43 @@ cudaError_t launch_xo_copy(const uint8_t *src, uint8_t *dst, const XoChild *chil
     return cudaGetLastError();
 }
 
+// Children of a batch of runs in one heap: tile t belongs to the last run
+// whose first tile is <= t, then to the last of that run's children whose
+// first tile (counted within the run) is <= the tile's index in the run.
+__global__ void xo_copy_runs_kernel(uint8_t *__restrict__ heap, const XoChild *__restrict__ kids,
+                                    const uint32_t *__restrict__ tile_local, const uint32_t *__restrict__ tree_base,
+                                    const uint32_t *__restrict__ run_tile_base, const uint32_t *n_runs_dev,
+                                    const uint32_t *n_tiles_dev, uint32_t tile_bytes)
+{
+    const uint32_t n_tiles = *n_tiles_dev, n_runs = *n_runs_dev;
+    for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        uint32_t lo = 0, hi = n_runs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (run_tile_base[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t lt = t - run_tile_base[lo];
+        uint32_t a = tree_base[lo], b = tree_base[lo + 1];
+        while (b - a > 1) {
+            const uint32_t mid = (a + b) >> 1;
+            if (tile_local[mid] <= lt) a = mid;
+            else b = mid;
+        }
+        copy_tile(heap, heap, kids[a], (uint64_t)(lt - tile_local[a]) * tile_bytes, tile_bytes);
+    }
+}
+
+cudaError_t launch_xo_copy_runs(uint8_t *heap, const XoChild *kids, const uint32_t *tile_local,
+                                const uint32_t *tree_base, const uint32_t *run_tile_base,
+                                const uint32_t *n_runs_dev, const uint32_t *n_tiles_dev, uint32_t tile_bytes,
+                                int sms, cudaStream_t s)
+{
+    xo_copy_runs_kernel<<<sms * 8, 256, 0, s>>>(heap, kids, tile_local, tree_base, run_tile_base, n_runs_dev,
+                                                 n_tiles_dev, tile_bytes);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_xo_copy_dev(const uint8_t *src, uint8_t *dst, const XoChild *children,
                                const uint32_t *tile_base, uint32_t n_children,
                                const uint32_t *n_tiles_dev, uint32_t tile_bytes, int sms,

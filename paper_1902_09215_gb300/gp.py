@@ -26,6 +26,8 @@ EXPORTED = [
     "gp_profile_read", "gp_evaluate_noalloc",
     "gp_generation_create", "gp_generation_step", "gp_generation_rewind", "gp_generation_fitness",
     "gp_generation_records", "gp_generation_trees", "gp_generation_get_info", "gp_generation_destroy",
+    "gp_server_create", "gp_server_open_run", "gp_server_submit", "gp_server_wait", "gp_server_run_fitness",
+    "gp_server_run_trees", "gp_server_close_run", "gp_server_get_stats", "gp_server_destroy",
 ]
 NOALLOC_MAX_TREES = 16384
 NOALLOC_MAX_TREE_NODES = 4096
@@ -72,6 +74,29 @@ class gp_generation_info(C.Structure):
                 ("arena_bytes", C.c_uint64), ("workspace_codes", C.c_uint64),
                 ("workspace_values", C.c_uint64), ("autotune_chunk", C.c_uint32 * 8),
                 ("autotune_ms", C.c_float * 8)]
+
+
+class gp_server_params(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_runs", C.c_uint32), ("max_batch_runs", C.c_uint32),
+                ("max_batch_trees", C.c_uint32), ("chunk_nodes", C.c_uint32), ("max_batch_nodes", C.c_uint64),
+                ("workspace_codes", C.c_uint64), ("workspace_values", C.c_uint64), ("use_graph", C.c_uint32),
+                ("pad", C.c_uint32)]
+
+
+class gp_server_result(C.Structure):
+    _fields_ = [("run_id", C.c_uint64), ("request_id", C.c_uint64), ("generation", C.c_uint64),
+                ("best_fitness", C.c_float), ("best_tree", C.c_uint32), ("best_hits", C.c_uint32),
+                ("status", C.c_int), ("total_nodes", C.c_uint64), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double)]
+
+
+class gp_server_stats(C.Structure):
+    _fields_ = [("batches", C.c_uint64), ("run_generations", C.c_uint64), ("requests_done", C.c_uint64),
+                ("child_nodes", C.c_uint64), ("device_ms", C.c_double), ("mean_runs_per_batch", C.c_double),
+                ("latency_p50_ms", C.c_double), ("latency_p99_ms", C.c_double), ("heap_bytes", C.c_uint64),
+                ("heap_free", C.c_uint64), ("runs_admitted", C.c_uint32), ("runs_waiting", C.c_uint32),
+                ("most_level_codes", C.c_uint64), ("most_level_values", C.c_uint64), ("retries", C.c_uint64),
+                ("regrown", C.c_uint64)]
 
 
 class gp_kernel_profile(C.Structure):
@@ -126,6 +151,17 @@ def lib():
             L.gp_generation_get_info.argtypes = [vp, P(gp_generation_info)]
             L.gp_generation_destroy.argtypes = [vp]
             L.gp_generation_destroy.restype = None
+            L.gp_server_create.argtypes = [P(gp_problem), P(gp_server_params), P(vp)]
+            L.gp_server_open_run.argtypes = [vp, P(gp_generation_params), C.c_uint32, P(C.c_uint8),
+                                             P(C.c_uint64), P(C.c_uint64)]
+            L.gp_server_submit.argtypes = [vp, C.c_uint64, C.c_uint32, P(C.c_uint64)]
+            L.gp_server_wait.argtypes = [vp, C.c_uint64, C.c_double, P(gp_server_result)]
+            L.gp_server_run_fitness.argtypes = [vp, C.c_uint64, P(C.c_float), P(C.c_float), P(C.c_uint32)]
+            L.gp_server_run_trees.argtypes = [vp, C.c_uint64, P(C.c_uint64), P(C.c_uint8), C.c_uint64]
+            L.gp_server_close_run.argtypes = [vp, C.c_uint64]
+            L.gp_server_get_stats.argtypes = [vp, P(gp_server_stats)]
+            L.gp_server_destroy.argtypes = [vp]
+            L.gp_server_destroy.restype = None
             _lib = L
     return _lib
 
@@ -388,6 +424,96 @@ def gp_generation_destroy(g: Generation):
     h, g._h = g._h, None
     if h:
         lib().gp_generation_destroy(h)
+
+
+class Server:
+    """Owns one gp_server handle (a serving loop over many runs)."""
+
+    def __init__(self, handle, n_cases):
+        self._h = handle
+        self.n_cases = n_cases
+        self.problem = None          # kept alive with the server
+        self.run_trees = {}          # run id -> number of trees
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h and _lib is not None:
+            _lib.gp_server_destroy(h)
+
+
+def gp_server_create(problem: Problem, hbm_budget_bytes, max_runs=64, max_batch_trees=1 << 20,
+                     max_batch_runs=0, chunk_nodes=0, max_batch_nodes=0, workspace_codes=0,
+                     workspace_values=0, use_graph=True) -> Server:
+    prm = gp_server_params(int(hbm_budget_bytes), int(max_runs), int(max_batch_runs), int(max_batch_trees),
+                           int(chunk_nodes), int(max_batch_nodes), int(workspace_codes), int(workspace_values),
+                           1 if use_graph else 0, 0)
+    h = C.c_void_p()
+    _check(lib().gp_server_create(C.byref(problem.struct), C.byref(prm), C.byref(h)), "gp_server_create")
+    s = Server(h, problem.n_cases)
+    s.problem = problem
+    return s
+
+
+def gp_server_open_run(srv: Server, nodes, offsets, seed, tournament_size=7, arena_bytes=0) -> int:
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = offsets.shape[0] - 1
+    prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), 0, int(arena_bytes), 0, 0, 0, 0)
+    rid = C.c_uint64()
+    _check(lib().gp_server_open_run(srv._h, C.byref(prm), n, _ptr(nodes, C.c_uint8), _ptr(offsets, C.c_uint64),
+                                    C.byref(rid)), "gp_server_open_run")
+    srv.run_trees[rid.value] = n
+    return rid.value
+
+
+def gp_server_submit(srv: Server, run_id, n_generations=1) -> int:
+    q = C.c_uint64()
+    _check(lib().gp_server_submit(srv._h, int(run_id), int(n_generations), C.byref(q)), "gp_server_submit")
+    return q.value
+
+
+def gp_server_wait(srv: Server, request_id, timeout_ms=-1.0) -> dict:
+    r = gp_server_result()
+    _check(lib().gp_server_wait(srv._h, int(request_id), float(timeout_ms), C.byref(r)), "gp_server_wait")
+    return {k: getattr(r, k) for k, _ in gp_server_result._fields_}
+
+
+def gp_server_run_fitness(srv: Server, run_id, case_values=False, hits=False):
+    n = srv.run_trees[run_id]
+    fit = np.empty(n, np.float32)
+    vals = np.empty((n, srv.n_cases), np.float32) if case_values else None
+    h = np.empty(n, np.uint32) if hits else None
+    _check(lib().gp_server_run_fitness(srv._h, int(run_id), _ptr(fit, C.c_float),
+                                       _ptr(vals, C.c_float) if vals is not None else None,
+                                       _ptr(h, C.c_uint32) if h is not None else None), "gp_server_run_fitness")
+    return fit, vals, h
+
+
+def gp_server_run_trees(srv: Server, run_id):
+    n = srv.run_trees[run_id]
+    offs = np.empty(n + 1, np.uint64)
+    _check(lib().gp_server_run_trees(srv._h, int(run_id), _ptr(offs, C.c_uint64), None, 0), "gp_server_run_trees")
+    nodes = np.empty(max(int(offs[-1]), 1), np.uint8)
+    _check(lib().gp_server_run_trees(srv._h, int(run_id), _ptr(offs, C.c_uint64), _ptr(nodes, C.c_uint8),
+                                     nodes.shape[0]), "gp_server_run_trees")
+    return nodes[:int(offs[-1])], offs
+
+
+def gp_server_close_run(srv: Server, run_id):
+    _check(lib().gp_server_close_run(srv._h, int(run_id)), "gp_server_close_run")
+    srv.run_trees.pop(run_id, None)
+
+
+def gp_server_get_stats(srv: Server) -> dict:
+    st = gp_server_stats()
+    _check(lib().gp_server_get_stats(srv._h, C.byref(st)), "gp_server_get_stats")
+    return {k: getattr(st, k) for k, _ in gp_server_stats._fields_}
+
+
+def gp_server_destroy(srv: Server):
+    h, srv._h = srv._h, None
+    if h:
+        lib().gp_server_destroy(h)
 
 
 def read_all_trees(pop: Population):
