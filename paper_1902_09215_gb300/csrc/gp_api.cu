@@ -545,7 +545,7 @@ namespace {
 // "rope" item per tree then walks the slots in a second launch.
 constexpr uint32_t kFuseMaxChunks = 32;
 
-uint32_t fuse_pt_cap(uint32_t C) { return std::max<uint32_t>(64, C / 16); }
+uint32_t fuse_pt_cap(uint32_t C) { return std::max<uint32_t>(128, C / 8); }
 
 gp_status eval_config(const gp_population *P, const gp_eval_options *opt, EvalCfg *cfg)
 {

@@ -266,7 +266,7 @@ struct LevelArgs {
     uint32_t level;
     uint32_t C;                   // chunk (codes)
     uint32_t cap_items;
-    uint32_t pad;
+    uint32_t last;                // the last level: every open tree becomes a final item
     uint64_t spill_base;          // first dedicated spill entry (after the per-warp areas)
     uint64_t cap_dedicated;       // dedicated spill entries available
 };
@@ -281,8 +281,9 @@ __device__ __forceinline__ uint32_t size_bucket(uint64_t len)
 // most C nodes is one final item, a larger one is cut into chunks of C.
 // Level k > 0: every tree that had chunks at level k-1 now has an upper
 // tree of codes [frag_off[first chunk], frag_off[one past its last chunk]);
-// it becomes a final item when it fits one chunk or did not at least halve
-// (a final above C gets a dedicated spill area), otherwise it is cut again.
+// it becomes a final item when it fits one chunk, did not at least halve, or
+// this is the last level (a final above C gets a dedicated spill area);
+// otherwise it is cut again.
 // Chunk items come first in tree order (their fragments must be contiguous
 // per tree), then finals from the largest size bucket down.
 __global__ void __launch_bounds__(kScanT) items_kernel(
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     for (uint32_t i = lo; i < hi; ++i) {
         if (!t_state[i]) continue;
         const uint64_t len = t_hi[i] - t_lo[i];
-        if (len <= C || 2 * len > t_prev[i]) {
+        if (A.last || len <= C || 2 * len > t_prev[i]) {
             ++s_cnt[size_bucket(len)][t];
             if (len > C) ded += len;
         } else {
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         t_first[i] = (uint32_t)ex_ch;
         if (!t_state[i]) continue;
         const uint64_t len = t_hi[i] - t_lo[i];
-        if (len <= C || 2 * len > t_prev[i]) {
+        if (A.last || len <= C || 2 * len > t_prev[i]) {
             const uint32_t b = size_bucket(len);
             EvalItem it{};
             it.begin = t_lo[i];
@@ -893,8 +894,8 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
     for (uint32_t level = 0; level < levels_max; ++level) {
         const bool wide = level > 0;
         const int k = level & 1;
-        LevelArgs A{level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu), 0, w.spill_base,
-                    w.cap_dedicated};
+        LevelArgs A{level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu),
+                    level + 1 == levels_max ? 1u : 0u, w.spill_base, w.cap_dedicated};
         items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
                                           t_state_, w.items);
         GK(cudaGetLastError());
