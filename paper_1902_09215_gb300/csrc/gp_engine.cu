@@ -21,7 +21,7 @@ namespace gpe {
 namespace {
 
 constexpr uint32_t kTile = 16384;        // copy tile (bytes)
-constexpr uint32_t kScanT = 256;         // threads of the single-CTA scan kernels
+constexpr uint32_t kScanT = 1024;        // threads of the single-CTA scan kernels
 constexpr uint32_t kBuckets = 40;        // final items ordered by floor(log2(size)), largest first
 constexpr uint64_t kHeapLead = 256;      // heap bytes [0, 256): code 4 ('x'), a one-node tree
                                          // that idle extent queries point at
@@ -292,17 +292,22 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     uint64_t *__restrict__ t_prev, uint32_t *__restrict__ t_first, uint32_t *__restrict__ t_state,
     EvalItem *__restrict__ items)
 {
-    __shared__ uint32_t s_cnt[kBuckets][kScanT];
     __shared__ uint64_t sa[kScanT], sb[kScanT];
+    __shared__ uint32_t s_cnt[kBuckets], s_fill[kBuckets];
     __shared__ uint64_t s_base[kBuckets];
     __shared__ uint32_t s_err;
     const uint32_t t = threadIdx.x;
     const uint32_t n = ctl->head.n_trees, C = A.C;
-    if (ctl->err != 0) {
+    // nothing to do: an earlier error, or no tree was cut at the level before
+    if (ctl->err != 0 || (A.level > 0 && ctl->n_chunks == 0)) {
+        __syncthreads();                      // every thread has read n_chunks
         if (t == 0) ctl->n_items = ctl->n_chunks = 0;
         return;
     }
-    for (uint32_t b = 0; b < kBuckets; ++b) s_cnt[b][t] = 0;
+    if (t < kBuckets) {
+        s_cnt[t] = 0;
+        s_fill[t] = 0;
+    }
     const uint32_t per = (n + kScanT - 1) / kScanT;
     const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
 
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         if (!t_state[i]) continue;
         const uint64_t len = t_hi[i] - t_lo[i];
         if (A.last || len <= C || 2 * len > t_prev[i]) {
-            ++s_cnt[size_bucket(len)][t];
+            atomicAdd(&s_cnt[size_bucket(len)], 1u);
             if (len > C) ded += len;
         } else {
             nch += (len + C - 1) / C;
@@ -335,22 +340,11 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     block_scan2(sa, sb, nch, ded);
     uint64_t ex_ch = sa[t] - nch, ex_ded = sb[t] - ded;
     const uint64_t tot_ch = sa[kScanT - 1], tot_ded = sb[kScanT - 1];
-    if (t < kBuckets) {                       // per bucket: exclusive prefix over threads
-        uint32_t run = 0;
-        for (uint32_t j = 0; j < kScanT; ++j) {
-            const uint32_t v = s_cnt[t][j];
-            s_cnt[t][j] = run;
-            run += v;
-        }
-        s_base[t] = run;                      // bucket total for now
-    }
-    __syncthreads();
     if (t == 0) {
-        uint64_t pos = tot_ch;
+        uint64_t pos = tot_ch;                // finals after the chunks, largest bucket first
         for (int b = (int)kBuckets - 1; b >= 0; --b) {
-            const uint64_t cnt = s_base[b];
             s_base[b] = pos;
-            pos += cnt;
+            pos += s_cnt[b];
         }
         uint32_t err = 0;
         ctl->need_dedicated = max(ctl->need_dedicated, tot_ded);
@@ -368,7 +362,8 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     }
     __syncthreads();
     if (s_err) return;
-    // phase 3: chunk offsets per tree, final items, states
+    // phase 3: chunk offsets per tree, final items (any order within a
+    // bucket), states
     for (uint32_t i = lo; i < hi; ++i) {
         t_first[i] = (uint32_t)ex_ch;
         if (!t_state[i]) continue;
@@ -386,7 +381,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
                 it.spill_cap = len;
                 ex_ded += len;
             }
-            items[s_base[b] + s_cnt[b][t]++] = it;
+            items[s_base[b] + atomicAdd(&s_fill[b], 1u)] = it;
             t_state[i] = 0;
         } else {
             t_prev[i] = len;
@@ -464,15 +459,20 @@ __global__ void scatter_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t
 {
     const BatchHead h = ctl->head;
     if (batch_errors(ctl)) return;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < h.n_trees; g += gridDim.x * blockDim.x) {
+    const uint64_t n_el = (uint64_t)h.n_trees * n_cases;    // one per-case value per thread
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_el;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = (uint32_t)(e / n_cases), k = (uint32_t)(e - (uint64_t)g * n_cases);
         const uint32_t slot = slot_of(tree_base, h.n_runs, g);
         const RunDev *R = runs + slot_run[slot];
         if (R->err) continue;
         const RunBuf &B = R->buf[h.mode == kModeGenerate ? (R->cur ^ 1) : R->cur];
         const uint32_t c = g - tree_base[slot];
-        B.fit[c] = bfit[g];
-        B.hits[c] = bhits[g];
-        for (uint32_t k = 0; k < n_cases; ++k) B.vals[(uint64_t)c * n_cases + k] = bvals[(uint64_t)g * n_cases + k];
+        B.vals[(uint64_t)c * n_cases + k] = bvals[e];
+        if (k == 0) {
+            B.fit[c] = bfit[g];
+            B.hits[c] = bhits[g];
+        }
     }
 }
 
@@ -1008,7 +1008,8 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     nl += 5;
     gp_status st = enqueue_eval(s, sizing, &nl);
     if (st) return st;
-    const uint32_t sblocks = std::max<uint32_t>(1, std::min<uint32_t>((max_trees + 255) / 256, sms * 4));
+    const uint32_t sblocks =
+        (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)max_trees * n_cases + 255) / 256, sms * 8));
     scatter_kernel<<<sblocks, 256, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, bfit_, bvals_, bhits_, n_cases);
     GK(cudaGetLastError());
     finish_kernel<<<1, 256, 0, s>>>(ctl, runs_dev, slot_run_);

@@ -644,6 +644,8 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     // Then one item copy (64 bytes) per warp.
     const uint32_t item0 = stage0 + (WIDE ? (uint32_t)nwarps * 32 * S : 0u);
 
+    // (a launch whose device-side item count is zero does no setup at all)
+    if (P.n_items_dev && *P.n_items_dev == 0) return;
     // Leaf table: row 0 is x (per lane, two cases), row r >= 1 constant r-1.
     for (int i = threadIdx.x; i < (int)(kLeafRows * LANES); i += blockDim.x) {
         const int row = i / LANES, l = i - row * LANES;
@@ -879,6 +881,13 @@ __global__ void plan_scan_kernel(EvalItem *items, const PlanOut *plan, uint32_t 
                                  const uint32_t *n_dev, uint64_t *frag_off, uint64_t *totals)
 {
     if (n_dev) n = *n_dev;
+    if (n == 0) {
+        if (threadIdx.x == 0) {
+            frag_off[0] = 0;
+            totals[0] = totals[1] = totals[2] = 0;
+        }
+        return;
+    }
     __shared__ uint64_t sa[1024], sb[1024];
     __shared__ uint32_t smx[1024];
     const uint32_t t = threadIdx.x, T = blockDim.x;
