@@ -300,6 +300,7 @@ def run_ours(args):
         return
 
     cpu = cpu_baseline(nodes, offs, ops, x, y, c, child_nodes) if world == 1 and not args.no_cpu else None
+    batched = batched_compare(gp, prob, nodes, offs, stream, flush, max(10, args.steps // 10)) if world == 1 else None
     step_sorted = sorted(step_ms)
     line = {
         "metric": METRIC,
@@ -343,9 +344,55 @@ def run_ours(args):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if batched:
+        line["batched_vs_plain"] = batched
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_compare(gp, prob, nodes, offs, stream, flush, steps):
+    """The same population, one generation made on the device (tournament
+    selection, crossover, evaluation; one graph launch) against the plain
+    host-driven path (the same crossover records through gp_crossover +
+    gp_evaluate), both timed with CUDA events, L2 flushed before each."""
+    import torch
+    G = gp.gp_generation_create(prob, nodes, offs, seed=21, use_graph=True, stream=stream)
+
+    def time_steps(fn, after):
+        ms = []
+        for _ in range(steps + 3):                    # the first 3 warm up
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                out = fn()
+                b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            after(out)
+        return statistics.median(ms[3:])
+
+    g_ms = time_steps(lambda: gp.gp_generation_step(G, 1, stream), lambda _: gp.gp_generation_rewind(G, stream))
+    gp.gp_generation_step(G, 1, stream)
+    recs = gp.gp_generation_records(G)
+    kid_nodes = int(gp.gp_generation_get_info(G)["total_nodes"])
+    gp.gp_generation_destroy(G)
+    with torch.cuda.stream(stream):
+        parents = gp.gp_create_population(prob, nodes, offs, stream)
+    xo = gp.make_xo(*recs)
+
+    def plain():
+        k = gp.gp_crossover(parents, xo, stream)
+        gp.gp_evaluate(k, stream)
+        return k
+
+    p_ms = time_steps(plain, lambda k: None)
+    units = kid_nodes * prob.n_cases
+    return {"workload": "the same 4000 parents; one generation: size-7 tournaments, 4000 crossovers, evaluation",
+            "batched_graph": {"ms_p50": g_ms, "GPops_per_s": units / (g_ms / 1e3)},
+            "plain_host_driven": {"ms_p50": p_ms, "GPops_per_s": units / (p_ms / 1e3)},
+            "speedup": p_ms / g_ms}
 
 
 def cpu_baseline(nodes, offs, ops, x, y, c, child_nodes):

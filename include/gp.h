@@ -345,15 +345,19 @@ gp_status gp_server_open_run(gp_server *s, const gp_generation_params *params, u
 gp_status gp_server_submit(gp_server *s, uint64_t run_id, uint32_t n_generations, uint64_t *request_id);
 /* Wait for a request (timeout_ms < 0: no limit).  GP_ETIMEOUT if it has not
  * completed; otherwise GP_OK with the result (result->status is the
- * request's own outcome). */
+ * request's own outcome), and the request is forgotten: a second wait on it
+ * returns GP_EINVAL. */
 gp_status gp_server_wait(gp_server *s, uint64_t request_id, double timeout_ms, gp_server_result *result);
 /* After the run's requests completed: its current population's results / trees. */
 gp_status gp_server_run_fitness(gp_server *s, uint64_t run_id, float *fitness, float *case_values, uint32_t *hits);
 gp_status gp_server_run_trees(gp_server *s, uint64_t run_id, uint64_t *offsets, uint8_t *nodes, uint64_t cap);
 /* Waits for the run's requests, then frees its buffers (waiting runs may
- * then be admitted). */
+ * then be admitted).  A run not admitted yet is closed at once and its
+ * requests complete with GP_EINVAL. */
 gp_status gp_server_close_run(gp_server *s, uint64_t run_id);
 gp_status gp_server_get_stats(gp_server *s, gp_server_stats *stats);
+/* Stops the scheduler and frees everything; no other call on the server may
+ * be in progress or follow (clients must have stopped waiting). */
 void gp_server_destroy(gp_server *s);
 
 /* ---- Evaluation without allocation.  The paper has no counterpart: this

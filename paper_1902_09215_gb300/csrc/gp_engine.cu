@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kScanT) children_kernel(
     __syncthreads();
     const bool stopped = R->err != 0 || (h.mode == kModeGenerate && ctl->eval_err[1] != 0);
     if (stopped || h.mode == kModeEvaluate) {
-        const RunBuf &B = R->buf[R->cur];
+        const RunBuf B = R->buf[R->cur];         // by value (see below)
         for (uint32_t c = t; c < n; c += kScanT) {
             bstart[base + c] = stopped ? 0 : B.start[c];
             bsize[base + c] = stopped ? 0 : B.size[c];
@@ -183,16 +183,22 @@ __global__ void __launch_bounds__(kScanT) children_kernel(
         if (t == 0) run_tiles[slot] = 0;
         return;
     }
-    const RunBuf &P = R->buf[R->cur];
-    const RunBuf &Cb = R->buf[R->cur ^ 1];
+    // the run's fields once, by value: the stores below could otherwise
+    // alias them and force a reload after every store
+    const uint32_t cur = R->cur;
+    const RunBuf P = R->buf[cur];
+    const RunBuf Cb = R->buf[cur ^ 1];
+    const uint64_t max_nodes = R->max_nodes;
+    const uint64_t *__restrict__ psize = P.size;
+    const uint64_t *__restrict__ pstart = P.start;
     const uint32_t per = (n + kScanT - 1) / kScanT;
     const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
     uint64_t a = 0, b = 0, nodes = 0;
     uint32_t bad = 0;
     for (uint32_t c = lo; c < hi; ++c) {
         const gp_xo r = recs[base + c];
-        const uint64_t m = r.mum_point + (ends[2 * (base + c) + 1] - r.dad_point) + (P.size[r.mum] - ends[2 * (base + c)]);
-        if (R->max_nodes && m > R->max_nodes) bad |= kGErrLimit;
+        const uint64_t m = r.mum_point + (ends[2 * (base + c) + 1] - r.dad_point) + (psize[r.mum] - ends[2 * (base + c)]);
+        if (max_nodes && m > max_nodes) bad |= kGErrLimit;
         a += (m + 15) & ~15ull;
         b += (m + kTile - 1) / kTile;
         nodes += m;
@@ -219,15 +225,15 @@ __global__ void __launch_bounds__(kScanT) children_kernel(
         const uint32_t g = base + c;
         const gp_xo r = recs[g];
         const uint64_t em = ends[2 * g], ed = ends[2 * g + 1];
-        const uint64_t m = r.mum_point + (ed - r.dad_point) + (P.size[r.mum] - em);
+        const uint64_t m = r.mum_point + (ed - r.dad_point) + (psize[r.mum] - em);
         XoChild k;
         k.dst = Cb.lo + ra;
         k.n = m;
-        k.head_src = P.start[r.mum];
+        k.head_src = pstart[r.mum];
         k.i = r.mum_point;
-        k.mid_src = P.start[r.dad] + r.dad_point;
+        k.mid_src = pstart[r.dad] + r.dad_point;
         k.ld = ed - r.dad_point;
-        k.tail_src = P.start[r.mum] + em;    // tail byte p comes from mum[em + p - i - ld]
+        k.tail_src = pstart[r.mum] + em;     // tail byte p comes from mum[em + p - i - ld]
         k.pad = 0;
         kids[g] = k;
         Cb.start[c] = Cb.lo + ra;

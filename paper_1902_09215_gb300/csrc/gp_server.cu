@@ -407,6 +407,7 @@ gp_status gp_server_wait(gp_server *S, uint64_t request_id, double timeout_ms, g
     else if (!S->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), done))
         return GP_ETIMEOUT;
     if (result) *result = S->reqs[request_id].res;
+    S->reqs.erase(request_id);                      // a completed request is collected once
     return GP_OK;
 }
 
@@ -449,6 +450,14 @@ gp_status gp_server_close_run(gp_server *S, uint64_t run_id)
     if (!S) return GP_EINVAL;
     {
         std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->runs.find(run_id);
+        if (it == S->runs.end()) return GP_EINVAL;
+        if (it->second.state == kWaiting) {          // never admitted: its requests cannot run
+            fail_run(S, it->second, GP_EINVAL);
+            S->runs.erase(it);
+            S->cv_done.notify_all();
+            return GP_OK;
+        }
         if (!wait_idle(S, lk, run_id)) return GP_EINVAL;
         Run &R = S->runs[run_id];
         if (R.state == kReady) S->eng.close_run(R.slot);

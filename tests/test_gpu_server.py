@@ -121,12 +121,15 @@ def test_admission_by_hbm_budget(gpu):
     st = gpu.gp_server_get_stats(srv)
     assert st["runs_admitted"] == 2 and st["runs_waiting"] == 3
     finals = {}
+    done = {0: r0, 1: r1}                             # a request's result is collected once
     for k, rid in enumerate(ids):
-        r = gpu.gp_server_wait(srv, reqs[k])
+        r = done[k] if k in done else gpu.gp_server_wait(srv, reqs[k])
         assert r["status"] == gpu.GP_OK and r["generation"] == 2
         finals[rid] = gpu.gp_server_run_trees(srv, rid)
         gpu.gp_server_close_run(srv, rid)             # frees room for the next
     assert gpu.gp_server_get_stats(srv)["runs_admitted"] == 5
+    with pytest.raises(gpu.GpError):
+        gpu.gp_server_wait(srv, reqs[0])              # already collected
     for rid, (n, o, s) in zip(ids, runs):
         an, ao, *_ = alone(gpu, prob, n, o, s, 2)
         assert np.array_equal(finals[rid][0], an) and np.array_equal(finals[rid][1], ao)
@@ -237,4 +240,22 @@ def test_a_failing_run_leaves_the_others_alone(gpu, oracle):
     with pytest.raises(gpu.GpError) as e:
         gpu.gp_server_submit(srv, bad, 1)
     assert e.value.status == gpu.GP_ELIMIT
+    gpu.gp_server_destroy(srv)
+
+
+def test_closing_a_waiting_run_fails_its_requests(gpu):
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    runs = make_runs(2, hi=4001)
+    arena = 1 << 22
+    srv = gpu.gp_server_create(prob, hbm_budget_bytes=2 * arena + (1 << 20), max_runs=4,
+                               max_batch_trees=1 << 14, chunk_nodes=4096)
+    a = gpu.gp_server_open_run(srv, runs[0][0], runs[0][1], seed=1, arena_bytes=arena)
+    b = gpu.gp_server_open_run(srv, runs[1][0], runs[1][1], seed=2, arena_bytes=arena)   # waits for room
+    qa = gpu.gp_server_submit(srv, a, 1)
+    qb = gpu.gp_server_submit(srv, b, 1)
+    assert gpu.gp_server_wait(srv, qa)["status"] == gpu.GP_OK
+    gpu.gp_server_close_run(srv, b)                   # never admitted
+    assert gpu.gp_server_wait(srv, qb)["status"] == gpu.GP_EINVAL
+    gpu.gp_server_close_run(srv, a)
     gpu.gp_server_destroy(srv)
