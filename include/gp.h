@@ -47,7 +47,8 @@ typedef struct gp_problem {
     uint32_t n_cases;            /* 1..64 fitness cases (the paper uses 48)            */
     const float *x;              /* host [n_cases] inputs                              */
     const float *y;              /* host [n_cases] targets                             */
-    uint32_t n_consts;           /* 0..127 constants, codes 5..5+n_consts-1            */
+    uint32_t n_consts;           /* 0..250 constants, codes 5..5+n_consts-1 (the paper's
+                                    grid has 250)                                        */
     const float *consts;         /* host [n_consts]                                    */
     float protected_div_value;   /* result of a/b when b == 0 (the paper: 1.0f)       */
     uint64_t max_tree_nodes;     /* node limit for crossover children, 0 = none        */

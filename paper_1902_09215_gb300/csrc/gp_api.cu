@@ -216,6 +216,7 @@ cudaError_t prepare_eval_once(int lanes, bool wide, size_t smem)
 
 struct EvalCfg {
     uint32_t C = 0, W = 0, K = 0, Wu = 0, Ku = 0;  // chunk, warps and windows (level 0 / upper)
+    int rows = (int)kLeafRows;                     // leaf table rows: 'x' + the constants
     int lanes = 0, sms = 0;
     size_t smem = 0, smem_u = 0;
 };
@@ -381,7 +382,7 @@ gp_status validate_population(gp_population *P, cudaStream_t s, DevBufs &tmp, bo
 gp_status copy_problem(gp_population *P, const gp_problem *pr)
 {
     if (!pr || pr->n_cases == 0 || pr->n_cases > kMaxCases || !pr->x || !pr->y) return GP_EINVAL;
-    if (pr->n_consts > 127 || (pr->n_consts && !pr->consts)) return GP_EINVAL;
+    if (pr->n_consts > kMaxConsts || (pr->n_consts && !pr->consts)) return GP_EINVAL;
     P->n_cases = pr->n_cases;
     P->lanes = lanes_for(pr->n_cases);
     P->n_consts = pr->n_consts;
@@ -555,21 +556,22 @@ gp_status eval_config(const gp_population *P, const gp_eval_options *opt, EvalCf
     c.K = opt && opt->window_entries ? opt->window_entries : 32;
     // Upper trees hold many pending values (the residual subtrees of every
     // chunk), so their window is deeper.
-    c.Ku = opt && opt->upper_window_entries ? opt->upper_window_entries : std::max<uint32_t>(c.K, 96);
+    c.Ku = opt && opt->upper_window_entries ? opt->upper_window_entries : std::max<uint32_t>(c.K, 128);
     if (c.C % 16 || c.C < 64 || c.C > (1u << 24) || c.W < 1 || c.W > 32 || c.K < 16 || c.K % 2 ||
         c.K > 1024 || c.Ku < 16 || c.Ku % 2 || c.Ku > 1024)
         return GP_EINVAL;
     c.lanes = (int)P->lanes;
+    c.rows = (int)std::max<uint32_t>(1 + P->n_consts, 1);
     c.sms = sm_count(P->device);
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     if (!(opt && opt->warps_per_cta))        // as many warps as shared memory holds
-        while (c.W > 1 && eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false) > (size_t)maxsm) --c.W;
+        while (c.W > 1 && eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false, c.rows) > (size_t)maxsm) --c.W;
     // Upper levels (32-bit codes) run at most 16 warps per SM, with staging.
     c.Wu = std::min<uint32_t>(c.W, 16);
-    while (c.Wu > 1 && eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true) > (size_t)maxsm) --c.Wu;
-    c.smem = eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false);
-    c.smem_u = eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true);
+    while (c.Wu > 1 && eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true, c.rows) > (size_t)maxsm) --c.Wu;
+    c.smem = eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false, c.rows);
+    c.smem_u = eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true, c.rows);
     if (c.smem > (size_t)maxsm || c.smem_u > (size_t)maxsm) return GP_EINVAL;
     *cfg = c;
     return GP_OK;
@@ -748,6 +750,7 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
             p.consts = P->d_c;
             p.n_cases = P->n_cases;
             p.n_consts = P->n_consts;
+            p.leaf_rows = (uint32_t)cfg.rows;
             p.div0 = P->div0;
             p.window = wide ? cfg.Ku : cfg.K;
             p.pt_in = pt_in;

@@ -191,61 +191,63 @@ __global__ void __launch_bounds__(kScanT) children_kernel(
     const uint64_t max_nodes = R->max_nodes;
     const uint64_t *__restrict__ psize = P.size;
     const uint64_t *__restrict__ pstart = P.start;
-    const uint32_t per = (n + kScanT - 1) / kScanT;
-    const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
-    uint64_t a = 0, b = 0, nodes = 0;
+    // rounds of kScanT children, one per thread (independent, coalesced
+    // loads), a block scan per round and a running carry; the outputs of a
+    // run that turns out not to fit are cleared at the end
+    uint64_t carry_a = 0, carry_b = 0, nodes = 0;
     uint32_t bad = 0;
-    for (uint32_t c = lo; c < hi; ++c) {
-        const gp_xo r = recs[base + c];
-        const uint64_t m = r.mum_point + (ends[2 * (base + c) + 1] - r.dad_point) + (psize[r.mum] - ends[2 * (base + c)]);
-        if (max_nodes && m > max_nodes) bad |= kGErrLimit;
-        a += (m + 15) & ~15ull;
-        b += (m + kTile - 1) / kTile;
-        nodes += m;
+    for (uint32_t r0 = 0; r0 < n; r0 += kScanT) {
+        const uint32_t c = r0 + t, g = base + c;
+        uint64_t m = 0, a = 0, b = 0, em = 0, ed = 0;
+        gp_xo r{};
+        if (c < n) {
+            r = recs[g];
+            em = ends[2 * g];
+            ed = ends[2 * g + 1];
+            m = r.mum_point + (ed - r.dad_point) + (psize[r.mum] - em);
+            if (max_nodes && m > max_nodes) bad |= kGErrLimit;
+            a = (m + 15) & ~15ull;
+            b = (m + kTile - 1) / kTile;
+            nodes += m;
+        }
+        block_scan2(sa, sb, a, b);
+        const uint64_t ra = carry_a + sa[t] - a, rb = carry_b + sb[t] - b;
+        if (c < n) {
+            XoChild k;
+            k.dst = Cb.lo + ra;
+            k.n = m;
+            k.head_src = pstart[r.mum];
+            k.i = r.mum_point;
+            k.mid_src = pstart[r.dad] + r.dad_point;
+            k.ld = ed - r.dad_point;
+            k.tail_src = pstart[r.mum] + em;     // tail byte p comes from mum[em + p - i - ld]
+            k.pad = 0;
+            kids[g] = k;
+            Cb.start[c] = Cb.lo + ra;
+            Cb.size[c] = m;
+            bstart[g] = Cb.lo + ra;
+            bsize[g] = m;
+            tile_local[g] = (uint32_t)rb;
+        }
+        carry_a += sa[kScanT - 1];
+        carry_b += sb[kScanT - 1];
+        __syncthreads();                      // sa / sb are rewritten by the next round
     }
     if (bad) atomicOr(&s_bad, bad);
     atomicAdd(&s_nodes, (unsigned long long)nodes);
-    block_scan2(sa, sb, a, b);
-    const uint64_t tot_a = sa[kScanT - 1], tot_b = sb[kScanT - 1];
+    __syncthreads();
     uint32_t err = s_bad;
-    if (tot_a + 64 > Cb.cap || tot_b >= 0x7fffffffull) err |= kGErrArena;
+    if (carry_a + 64 > Cb.cap || carry_b >= 0x7fffffffull) err |= kGErrArena;
     if (err) {
-        for (uint32_t c = t; c < n; c += kScanT) {
-            bstart[base + c] = 0;
-            bsize[base + c] = 0;
-        }
+        for (uint32_t c = t; c < n; c += kScanT) bsize[base + c] = 0;
         if (t == 0) {
             run_tiles[slot] = 0;
             run_err(R, err);
         }
         return;
     }
-    uint64_t ra = sa[t] - a, rb = sb[t] - b;
-    for (uint32_t c = lo; c < hi; ++c) {
-        const uint32_t g = base + c;
-        const gp_xo r = recs[g];
-        const uint64_t em = ends[2 * g], ed = ends[2 * g + 1];
-        const uint64_t m = r.mum_point + (ed - r.dad_point) + (psize[r.mum] - em);
-        XoChild k;
-        k.dst = Cb.lo + ra;
-        k.n = m;
-        k.head_src = pstart[r.mum];
-        k.i = r.mum_point;
-        k.mid_src = pstart[r.dad] + r.dad_point;
-        k.ld = ed - r.dad_point;
-        k.tail_src = pstart[r.mum] + em;     // tail byte p comes from mum[em + p - i - ld]
-        k.pad = 0;
-        kids[g] = k;
-        Cb.start[c] = Cb.lo + ra;
-        Cb.size[c] = m;
-        bstart[g] = Cb.lo + ra;
-        bsize[g] = m;
-        tile_local[g] = (uint32_t)rb;
-        ra += (m + 15) & ~15ull;
-        rb += (m + kTile - 1) / kTile;
-    }
-    if (t == kScanT - 1) {
-        run_tiles[slot] = (uint32_t)tot_b;
+    if (t == 0) {
+        run_tiles[slot] = (uint32_t)carry_b;
         R->next_nodes = s_nodes;
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->child_nodes), s_nodes);
     }
@@ -590,11 +592,12 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     // launch shape as in gp_evaluate
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    while (W > 1 && eval_smem_bytes(lanes, (int)W, (int)K, false) > (size_t)maxsm) --W;
+    rows = (int)std::max<uint32_t>(1 + n_consts, 1);
+    while (W > 1 && eval_smem_bytes(lanes, (int)W, (int)K, false, rows) > (size_t)maxsm) --W;
     Wu = std::min<uint32_t>(W, 16);
-    while (Wu > 1 && eval_smem_bytes(lanes, (int)Wu, (int)Ku, true) > (size_t)maxsm) --Wu;
-    smem = eval_smem_bytes(lanes, (int)W, (int)K, false);
-    smem_u = eval_smem_bytes(lanes, (int)Wu, (int)Ku, true);
+    while (Wu > 1 && eval_smem_bytes(lanes, (int)Wu, (int)Ku, true, rows) > (size_t)maxsm) --Wu;
+    smem = eval_smem_bytes(lanes, (int)W, (int)K, false, rows);
+    smem_u = eval_smem_bytes(lanes, (int)Wu, (int)Ku, true, rows);
     if (smem > (size_t)maxsm || smem_u > (size_t)maxsm) return GP_EINVAL;
     GK(eval_prepare_at_least(lanes, false, smem));
     GK(eval_prepare_at_least(lanes, true, smem_u));
@@ -974,6 +977,7 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
         p.consts = c_;
         p.n_cases = n_cases;
         p.n_consts = n_consts;
+        p.leaf_rows = (uint32_t)rows;
         p.div0 = div0;
         p.window = wide ? Ku : K;
         p.pt_in = wide ? w.vals[(level - 1) & 1] : nullptr;

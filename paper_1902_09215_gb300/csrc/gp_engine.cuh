@@ -139,7 +139,8 @@ class Engine {
     int device = 0, sms = 0, lanes = 0;
     uint32_t n_cases = 0, n_consts = 0, max_runs = 0, max_trees = 0, levels_max = 8;
     float div0 = 1.0f;
-    uint32_t W = 32, K = 32, Wu = 16, Ku = 96;
+    uint32_t W = 32, K = 32, Wu = 16, Ku = 128;
+    int rows = 128;                      // leaf table rows: 'x' + the constants
     size_t smem = 0, smem_u = 0;
     uint64_t heap_bytes = 0;
     uint8_t *heap = nullptr;

@@ -107,8 +107,10 @@ template <> struct Group<uint32_t> {
 };
 
 // Upper-tree variant of the group interpreter: one 32-bit code per operand
-// (%3 + position), leaves >= 132 read the staged value entry of their
-// position in the group (%24 + position * S), other leaves the leaf table.
+// (%3 + position), leaves >= 256 (kPtCode0) read the staged value entry of
+// their position in the group (%24 + position * S), other leaves the leaf
+// table.
+static_assert(kPtCode0 == 256, "the PTX of GP_UNODE compares codes with 256");
 #define GP_UNODE(CREG, J, IDX)                                                   \
     "setp.gt.u32 pl, " CREG ", 3;\n\t"                                         \
     "@pl bra.uni LF" #IDX ";\n\t"                                              \
@@ -125,7 +127,7 @@ template <> struct Group<uint32_t> {
     "sub.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"                          \
     "AD" #IDX ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
     "LF" #IDX ":\n\tst.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %23;\n\t"          \
-    "setp.lt.u32 p, " CREG ", 132;\n\t@p bra.uni TB" #IDX ";\n\t"              \
+    "setp.lt.u32 p, " CREG ", 256;\n\t@p bra.uni TB" #IDX ";\n\t"              \
     "ld.shared.b64 %0, [%24+" #J "*%23];\n\tbra.uni E" #IDX ";\n"                \
     "TB" #IDX ":\n\tmad.lo.u32 a, " CREG ", %23, %19;\n\tld.shared.b64 %0, [a];\n" \
     "E" #IDX ":\n\t"
@@ -638,7 +640,8 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr uint32_t S = LANES * sizeof(float2);
-    const uint32_t win0 = kLeafRows * S;                    // first window (bytes)
+    const uint32_t rows = P.leaf_rows ? P.leaf_rows : kLeafRows;
+    const uint32_t win0 = rows * S;                         // first window (bytes)
     // Upper-tree kernels: two 16-entry staging buffers per warp after the windows.
     const uint32_t stage0 = win0 + (uint32_t)nwarps * P.window * S;
     // Then one item copy (64 bytes) per warp.
@@ -647,7 +650,7 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     // (a launch whose device-side item count is zero does no setup at all)
     if (P.n_items_dev && *P.n_items_dev == 0) return;
     // Leaf table: row 0 is x (per lane, two cases), row r >= 1 constant r-1.
-    for (int i = threadIdx.x; i < (int)(kLeafRows * LANES); i += blockDim.x) {
+    for (int i = threadIdx.x; i < (int)(rows * LANES); i += blockDim.x) {
         const int row = i / LANES, l = i - row * LANES;
         float2 v;
         if (row == 0) v = make_float2(P.x[2 * l], P.x[2 * l + 1]);
@@ -692,9 +695,9 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     }
 }
 
-size_t eval_smem_bytes(int lanes, int warps, int window, bool wide)
+size_t eval_smem_bytes(int lanes, int warps, int window, bool wide, int leaf_rows)
 {
-    return (size_t)kLeafRows * lanes * sizeof(float2) +
+    return (size_t)leaf_rows * lanes * sizeof(float2) +
            (size_t)warps * (window + (wide ? 32 : 0)) * lanes * sizeof(float2) +
            (size_t)warps * sizeof(EvalItem);
 }

@@ -84,7 +84,7 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
 {
     if (!problem || !params || !out || !nodes || !offsets || n_trees == 0 || n_trees > (1u << 28))
         return GP_EINVAL;
-    if (problem->n_cases == 0 || problem->n_cases > gpk::kMaxCases || problem->n_consts > 127) return GP_EINVAL;
+    if (problem->n_cases == 0 || problem->n_cases > gpk::kMaxCases || problem->n_consts > gpk::kMaxConsts) return GP_EINVAL;
     if (params->tournament_size < 1 || params->tournament_size > 32) return GP_EINVAL;
     if (params->chunk_nodes && (params->chunk_nodes % 16 || params->chunk_nodes < 256 ||
                                 params->chunk_nodes > 65536))

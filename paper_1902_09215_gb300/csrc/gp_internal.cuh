@@ -6,8 +6,9 @@
 namespace gpk {
 
 constexpr uint32_t kMaxCases = 64;
-constexpr uint32_t kLeafRows = 128;     // codes 4 ('x') .. 131 (constant 126)
-constexpr uint32_t kPtCode0 = 132;      // upper-tree code >= 132: value-buffer entry code-132
+constexpr uint32_t kMaxConsts = 250;    // constant codes 5 .. 254 (the paper's grid has 250)
+constexpr uint32_t kLeafRows = 128;     // default leaf table: 'x' and 127 constants (codes 4 .. 131)
+constexpr uint32_t kPtCode0 = 256;      // upper-tree code >= 256: value-buffer entry code-256
 constexpr uint32_t kItemFinal = 1u;     // item covers a whole (upper) tree: produce fitness
 constexpr uint32_t kItemFused = 2u;     // chunk of a medium tree, finished by its last chunk
 constexpr uint32_t kItemRope = 4u;      // final item over a medium tree's chunk fragments
@@ -69,7 +70,7 @@ struct EvalParams {
     uint32_t n_consts;
     float div0;
     uint32_t window;               // shared-memory stack entries per warp
-    const float2 *pt_in;           // value buffer read by upper-tree codes >= 132
+    const float2 *pt_in;           // value buffer read by upper-tree codes >= kPtCode0
     float2 *pt_out;                // value buffer written by fragments
     uint32_t *u_out;               // next level's upper-tree codes
     float *values;                 // [n_trees * n_cases]
@@ -87,6 +88,7 @@ struct EvalParams {
     uint32_t *fz_redo;             // [1 + n_trees]: count, then trees to re-evaluate
     uint32_t fz_cap_codes;
     uint32_t fz_cap_pt;
+    uint32_t leaf_rows;            // leaf table rows ('x' + constants); 0 = kLeafRows
 };
 
 struct XoChild {                   // child = M[0,i) ++ D[j,e_d) ++ M[e_m,n_m)
@@ -114,7 +116,7 @@ struct ExtentQuery {
 void note_launches(uint64_t n);
 
 // Launchers (defined in the .cu files; return the launch's error).
-size_t eval_smem_bytes(int lanes, int warps, int window, bool wide);
+size_t eval_smem_bytes(int lanes, int warps, int window, bool wide, int leaf_rows = (int)kLeafRows);
 cudaError_t eval_prepare(int lanes, bool wide, size_t smem);
 cudaError_t eval_prepare_at_least(int lanes, bool wide, size_t smem);
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,

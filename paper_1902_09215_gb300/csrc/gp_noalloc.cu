@@ -36,7 +36,7 @@ struct Ctl {                          // layout of the first kCtlBytes
     uint32_t pad[59];
     float x[kMaxCases];
     float y[kMaxCases];
-    float consts[128];
+    float consts[256];
 };
 static_assert(sizeof(Ctl) <= kCtlBytes, "control block");
 
@@ -108,7 +108,7 @@ extern "C" gp_status gp_evaluate_noalloc(const gp_problem *problem, uint32_t n_t
 {
     if (!problem || problem->n_cases == 0 || problem->n_cases > kMaxCases || !problem->x || !problem->y)
         return GP_EINVAL;
-    if (problem->n_consts > 127 || (problem->n_consts && !problem->consts)) return GP_EINVAL;
+    if (problem->n_consts > kMaxConsts || (problem->n_consts && !problem->consts)) return GP_EINVAL;
     if (n_trees > GP_NOALLOC_MAX_TREES) return GP_ELIMIT;
     if (n_trees == 0) return GP_OK;
     if (!d_nodes || !offsets || !d_fitness || !d_case_values || !d_hits) return GP_EINVAL;
@@ -131,7 +131,7 @@ extern "C" gp_status gp_evaluate_noalloc(const gp_problem *problem, uint32_t n_t
 
     // Problem tables and work items: built in fixed host buffers, copied in.
     const int lanes = noalloc_lanes(problem->n_cases);
-    float tables[2 * kMaxCases + 128] = {};
+    float tables[2 * kMaxCases + 256] = {};
     std::memcpy(tables, problem->x, sizeof(float) * problem->n_cases);
     std::memcpy(tables + kMaxCases, problem->y, sizeof(float) * problem->n_cases);
     if (problem->n_consts) std::memcpy(tables + 2 * kMaxCases, problem->consts, sizeof(float) * problem->n_consts);
@@ -170,8 +170,9 @@ extern "C" gp_status gp_evaluate_noalloc(const gp_problem *problem, uint32_t n_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int warps = 16;
-    while (warps > 1 && eval_smem_bytes(lanes, warps, (int)kWindow, false) > (size_t)maxsm) --warps;
-    const size_t smem = eval_smem_bytes(lanes, warps, (int)kWindow, false);
+    const int rows = (int)(1 + problem->n_consts);
+    while (warps > 1 && eval_smem_bytes(lanes, warps, (int)kWindow, false, rows) > (size_t)maxsm) --warps;
+    const size_t smem = eval_smem_bytes(lanes, warps, (int)kWindow, false, rows);
     if (smem > (size_t)maxsm) return GP_ECUDA;
     if (eval_prepare_at_least(lanes, false, smem) != cudaSuccess) return GP_ECUDA;
 
@@ -185,6 +186,7 @@ extern "C" gp_status gp_evaluate_noalloc(const gp_problem *problem, uint32_t n_t
     p.consts = ctl->consts;
     p.n_cases = problem->n_cases;
     p.n_consts = problem->n_consts;
+    p.leaf_rows = (uint32_t)rows;
     p.div0 = problem->protected_div_value;
     p.window = kWindow;
     p.values = d_case_values;

@@ -304,7 +304,7 @@ extern "C" {
 gp_status gp_server_create(const gp_problem *problem, const gp_server_params *params, gp_server **out)
 {
     if (!problem || !params || !out) return GP_EINVAL;
-    if (problem->n_cases == 0 || problem->n_cases > gpk::kMaxCases || problem->n_consts > 127) return GP_EINVAL;
+    if (problem->n_cases == 0 || problem->n_cases > gpk::kMaxCases || problem->n_consts > gpk::kMaxConsts) return GP_EINVAL;
     gp_server_params p = *params;
     if (p.max_runs == 0 || p.max_runs > 4096 || p.max_batch_trees == 0 || p.hbm_budget_bytes < (1u << 20))
         return GP_EINVAL;

@@ -7,7 +7,8 @@ tests import.  Every generator is seeded and deterministic.
 
 Encoding (one byte per node, prefix / root-first order, Sec. 2.1-2.2):
     0 '+'   1 '-'   2 '*'   3 protected '/'   (arity 2)
-    4 'x'   5..131 constant table entry code-5 (arity 0)
+    4 'x'   5..5+n_consts-1 constant table entry code-5 (arity 0); 127
+            constants by default, up to 250 (the paper's grid, codes 5..254)
 """
 from __future__ import annotations
 
@@ -43,6 +44,14 @@ def constants(seed: int = 2, n: int = N_CONSTS) -> np.ndarray:
     r = splitmix64(seed, n)
     u = (r >> np.uint64(40)).astype(np.float64) * (2.0 ** -24)
     return (2.0 * u - 1.0).astype(np.float32)
+
+
+def paper_grid_population(seed: int = 12, count: int = 300, lo: int = 1, hi: int = 20001):
+    """Random trees over the paper's 250 grid constants (codes up to 254),
+    odd sizes log-uniform on [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    sizes = loguniform_sizes(rng, count, lo, hi)
+    return pack([random_tree(rng, int(n), n_consts=250) for n in sizes])
 
 
 def paper_grid_constants(seed: int = 7, n: int = 250) -> np.ndarray:
@@ -187,6 +196,35 @@ def population_loguniform(seed: int = 3, count: int = 4000, lo: int = 31, hi: in
     rng = np.random.default_rng(seed)
     sizes = loguniform_sizes(rng, count, lo, hi)
     return pack([random_tree(rng, int(n), p_x=p_x) for n in sizes])
+
+
+def ramped_half_and_half(seed: int = 1, count: int = 4000, min_depth: int = 2, max_depth: int = 6,
+                         n_consts: int = N_CONSTS, p_function: float = 2.0 / 3.0, p_x: float = 0.5):
+    """Koza's ramped half-and-half initial population (Table gp.details:
+    4000 trees, depth between 2 and 6): depths cycle over min_depth ..
+    max_depth, and at each depth the trees alternate between the full method
+    (every leaf at that depth) and the grow method (below that depth a node
+    is an operator with probability p_function, else a leaf).  The root is
+    always an operator.  Leaves are x with probability p_x, else a uniform
+    constant; operators are uniform.  Depth counts edges from the root."""
+    rng = np.random.default_rng(seed)
+    depths = list(range(min_depth, max_depth + 1))
+    trees = []
+    for i in range(count):
+        d = depths[i % len(depths)]
+        full = (i // len(depths)) % 2 == 0
+        codes = []
+        stack = [0]                                 # depths of the nodes still to write
+        while stack:
+            depth = stack.pop()
+            leaf = depth == d or (not full and depth > 0 and rng.random() >= p_function)
+            if leaf:
+                codes.append(LEAF_X if rng.random() < p_x else CONST0 + int(rng.integers(0, n_consts)))
+            else:
+                codes.append(int(rng.integers(0, 4)))
+                stack.extend((depth + 1, depth + 1))
+        trees.append(np.array(codes, dtype=np.uint8))
+    return pack(trees)
 
 
 def deepest_leaf(tree: np.ndarray) -> tuple[int, int]:

@@ -190,3 +190,25 @@ def test_generation_rejects_bad_parameters(gpu):
     G = gpu.gp_generation_create(prob, nodes, offs, seed=1, chunk_nodes=256)
     with pytest.raises(gpu.GpError):
         gpu.gp_generation_rewind(G)                  # nothing to undo
+
+
+def test_paper_run_start_ramped_half_and_half(gpu, oracle):
+    """Table gp.details' run: 4000 ramped half-and-half trees (depths 2..6),
+    size-7 tournaments, 100% subtree crossover; five generations, every one
+    identical to the oracle's (records, children, fitness)."""
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.ramped_half_and_half(seed=1, count=4000)
+    seed = 2019
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, use_graph=True)
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+    assert_same_eval(gpu, G, ref)
+    for g in range(5):
+        recs, kids, koffs, ref_next = oracle_step(oracle, nodes, offs, ref["fitness"], seed, g, (x, y, c))
+        gpu.gp_generation_step(G)
+        got = gpu.gp_generation_records(G)
+        assert all(np.array_equal(a.astype(np.uint64), b.astype(np.uint64)) for a, b in zip(got, recs)), g
+        gn, go = gpu.gp_generation_trees(G)
+        assert np.array_equal(go, koffs) and np.array_equal(gn, kids), g
+        assert_same_eval(gpu, G, ref_next)
+        nodes, offs, ref = kids, koffs, ref_next

@@ -322,3 +322,15 @@ def test_population_matches_single_tree_and_threads(oracle):
         assert same_f32(r1["out"][t], o)
         f, h = oracle.mae_f32(o, y)
         assert same_f32(r1["fitness"][t], f) and r1["hits"][t] == h
+
+
+def test_paper_grid_code_range(oracle):
+    """With the paper's 250 constants, codes 5..254 are leaves and 255 is not
+    a code (Sec. 2.1: one byte per node)."""
+    assert oracle.check_tree(np.array([0, 254, 4], np.uint8), n_consts=250)
+    assert not oracle.check_tree(np.array([0, 255, 4], np.uint8), n_consts=250)
+    assert not oracle.check_tree(np.array([0, 132, 4], np.uint8), n_consts=127)
+    x, _, _ = synth.problem()
+    c = synth.paper_grid_constants()
+    out = oracle.eval_tree(np.array([254], np.uint8), x, c)
+    assert np.all(out == c[249])
