@@ -263,6 +263,14 @@ gp_status gp_generation_step(gp_generation *g, uint32_t n, void *cuda_stream);
  * buffer is untouched by the step).  Only one step can be undone. */
 gp_status gp_generation_rewind(gp_generation *g, void *cuda_stream);
 
+/* After a synchronising call reported GP_ENOMEM (the children outgrew the
+ * population buffers, or a level outgrew the evaluator workspace): double
+ * what ran out, clear the error and capture the generation again.  The next
+ * step makes the failed generation again (its draws are the same).
+ * Synchronises.  GP_EINVAL if the run has no such error; GP_ENOMEM if the
+ * device cannot hold the larger buffers. */
+gp_status gp_generation_recover(gp_generation *g, void *cuda_stream);
+
 /* Synchronise and copy the current population's results (any pointer may be
  * null).  Returns the error of a failed step: GP_ELIMIT (node limit),
  * GP_ENOMEM (population buffer, workspace or item capacity), GP_EMALFORMED,

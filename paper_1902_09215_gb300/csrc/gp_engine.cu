@@ -787,6 +787,32 @@ gp_status Engine::grow_run(uint32_t r, uint64_t arena_cap, cudaStream_t s)
     return GP_OK;
 }
 
+gp_status Engine::grow_heap(uint64_t new_bytes)
+{
+    if (new_bytes <= heap_bytes) return GP_EINVAL;
+    GK(cudaDeviceSynchronize());
+    uint8_t *nh = nullptr;
+    GK(cudaMalloc((void **)&nh, kHeapLead + new_bytes + 64));
+    cudaError_t e = cudaMemcpy(nh, heap, kHeapLead + heap_bytes + 64, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(nh);
+        return gfail(e);
+    }
+    for (auto &p : allocs_)
+        if (p == heap) p = nh;
+    cudaFree(heap);
+    heap = nh;
+    heap_release(kHeapLead + heap_bytes, new_bytes - heap_bytes);
+    heap_bytes = new_bytes;
+    forget_head();
+    for (auto &x : exec)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    return GP_OK;
+}
+
 gp_status Engine::load_run(uint32_t r, const uint8_t *nodes, const uint64_t *offsets, cudaStream_t s)
 {
     if (r >= max_runs || !runs_host[r].used) return GP_EINVAL;

@@ -109,6 +109,9 @@ class Engine {
     // Move a run to two larger population buffers (its current population
     // copied, tree offsets rebased); GP_ENOMEM if the heap cannot hold them.
     gp_status grow_run(uint32_t run, uint64_t arena_cap, cudaStream_t s);
+    // Replace the heap by a larger one holding the same bytes at the same
+    // offsets (graphs must be captured again afterwards).
+    gp_status grow_heap(uint64_t heap_bytes);
     // Upload, validate and lay out a run's initial population (generation 0,
     // not evaluated).
     gp_status load_run(uint32_t run, const uint8_t *nodes, const uint64_t *offsets, cudaStream_t s);

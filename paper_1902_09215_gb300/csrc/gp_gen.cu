@@ -249,6 +249,43 @@ gp_status gp_generation_rewind(gp_generation *G, void *cuda_stream)
     return st;
 }
 
+gp_status gp_generation_recover(gp_generation *G, void *cuda_stream)
+{
+    if (!G) return GP_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    Engine &E = G->eng;
+    RunDev R{};
+    gp_status st = E.read_run(G->run, &R, G->last);
+    if (st) return st;
+    const uint32_t room = kGErrArena | kGErrWork | kGErrItems | kGErrSpill;
+    if (!R.err || (R.err & ~room)) return GP_EINVAL;
+    if (R.err & kGErrArena) {
+        const uint64_t cap = 2 * G->info.arena_bytes;
+        const uint64_t need = 2 * ((cap + 255) & ~255ull);
+        if (E.heap_largest_free() < need && (st = E.grow_heap(E.heap_bytes + need))) return st;
+        if ((st = E.grow_run(G->run, cap, s))) return st;
+        G->info.arena_bytes = cap;
+    }
+    if (R.err & (kGErrWork | kGErrItems | kGErrSpill)) {
+        BatchCtl c{};
+        if ((st = E.read_ctl(&c, s))) return st;
+        uint64_t codes[2], vals[2];
+        for (int k = 0; k < 2; ++k) {
+            codes[k] = std::max<uint64_t>(2 * E.w.cap_codes[k], c.need_codes[k] + c.need_codes[k] / 2);
+            vals[k] = std::max<uint64_t>(2 * E.w.cap_values[k], c.need_values[k] + c.need_values[k] / 2);
+        }
+        const uint64_t ded = std::max<uint64_t>(2 * E.w.cap_dedicated, 2 * c.need_dedicated);
+        if ((st = E.set_workspace(E.w.C, codes, vals, ded, 2 * E.w.cap_items))) return st;
+        G->info.workspace_codes = E.w.cap_codes[0] + E.w.cap_codes[1];
+        G->info.workspace_values = E.w.cap_values[0] + E.w.cap_values[1];
+    }
+    if ((st = E.clear_error(G->run, s))) return st;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GP_ECUDA;
+    if (G->use_graph && !E.exec[kModeGenerate] && (st = E.capture(kModeGenerate))) return st;
+    G->last = s;
+    return GP_OK;
+}
+
 gp_status gp_generation_fitness(gp_generation *G, float *fitness, float *case_values, uint32_t *hits)
 {
     if (!G) return GP_EINVAL;

@@ -26,6 +26,7 @@ EXPORTED = [
     "gp_profile_read", "gp_evaluate_noalloc",
     "gp_generation_create", "gp_generation_step", "gp_generation_rewind", "gp_generation_fitness",
     "gp_generation_records", "gp_generation_trees", "gp_generation_get_info", "gp_generation_destroy",
+    "gp_generation_recover",
     "gp_server_create", "gp_server_open_run", "gp_server_submit", "gp_server_wait", "gp_server_run_fitness",
     "gp_server_run_trees", "gp_server_close_run", "gp_server_get_stats", "gp_server_destroy",
 ]
@@ -145,6 +146,7 @@ def lib():
                                                P(C.c_uint8), P(C.c_uint64), vp, P(vp)]
             L.gp_generation_step.argtypes = [vp, C.c_uint32, vp]
             L.gp_generation_rewind.argtypes = [vp, vp]
+            L.gp_generation_recover.argtypes = [vp, vp]
             L.gp_generation_fitness.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_uint32)]
             L.gp_generation_records.argtypes = [vp, P(gp_xo)]
             L.gp_generation_trees.argtypes = [vp, P(C.c_uint64), P(C.c_uint8), C.c_uint64]
@@ -379,6 +381,10 @@ def gp_generation_step(g: Generation, n=1, stream=None):
 
 def gp_generation_rewind(g: Generation, stream=None):
     _check(lib().gp_generation_rewind(g._h, _stream(stream)), "gp_generation_rewind")
+
+
+def gp_generation_recover(g: Generation, stream=None):
+    _check(lib().gp_generation_recover(g._h, _stream(stream)), "gp_generation_recover")
 
 
 def gp_generation_fitness(g: Generation, case_values=False, hits=False):

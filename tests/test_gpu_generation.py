@@ -166,6 +166,14 @@ def test_population_buffer_too_small(gpu, oracle):
         gpu.gp_generation_fitness(G)
     assert e.value.status == gpu.GP_ENOMEM
     assert gpu.gp_generation_get_info(G)["generation"] == 0
+    # recovery: larger buffers, the same generation made again
+    gpu.gp_generation_recover(G)
+    gpu.gp_generation_step(G)
+    gn, go = gpu.gp_generation_trees(G)
+    assert np.array_equal(gn, kids) and np.array_equal(go, koffs)
+    assert gpu.gp_generation_get_info(G)["arena_bytes"] == 2 * (need - 1)
+    with pytest.raises(gpu.GpError):
+        gpu.gp_generation_recover(G)                 # nothing to recover from
     # the exact size is enough
     G2 = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=1024, arena_bytes=need)
     gpu.gp_generation_step(G2)
