@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         }
         uint32_t err = 0;
         ctl->need_dedicated = max(ctl->need_dedicated, tot_ded);
+        ctl->need_items = max(ctl->need_items, pos);
         if (pos > A.cap_items) err |= kGErrItems;
         if (tot_ded > A.cap_dedicated) err |= kGErrSpill;
         if (err) {
@@ -433,13 +434,14 @@ __global__ void check_kernel(BatchCtl *ctl, uint64_t cap_codes, uint64_t cap_val
     if (threadIdx.x == 0) {
         s_ok = 0;
         if (ctl->err == 0) {
+            // recorded whether or not they fit: a recovery sizes from them
+            ctl->need_codes[idx] = max(ctl->need_codes[idx], codes);
+            ctl->need_values[idx] = max(ctl->need_values[idx], vals);
             if (codes + 48 > cap_codes || vals > cap_values || vals + kPtCode0 >= 0xffffffffull) {
                 atomicOr(&ctl->err, kGErrWork);
                 ctl->n_items = 0;
             } else {
                 s_ok = 1;
-                ctl->need_codes[idx] = max(ctl->need_codes[idx], codes);
-                ctl->need_values[idx] = max(ctl->need_values[idx], vals);
             }
         } else {
             ctl->n_items = 0;
@@ -1007,6 +1009,7 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
         p.div0 = div0;
         p.window = wide ? Ku : K;
         p.pt_in = wide ? w.vals[(level - 1) & 1] : nullptr;
+        p.pt_in_cap = wide ? w.cap_values[(level - 1) & 1] : 0;
         p.pt_out = w.vals[k];
         p.u_out = w.codes[k];
         p.values = bvals_;

@@ -67,7 +67,7 @@ struct BatchCtl {
     uint32_t n_queries, n_tiles, n_items, n_chunks, levels;
     uint32_t eval_err[4];                // [0] evaluator error word, [1] extent error word
     uint64_t totals[4];                  // plan scan totals of the current level
-    uint64_t need_codes[2], need_values[2], need_dedicated;   // sizing records
+    uint64_t need_codes[2], need_values[2], need_dedicated, need_items;   // sizing records (largest seen)
     uint64_t child_nodes;                // nodes of all children made by this batch
     uint32_t counter[64];                // evaluator work counters, one per level
 };

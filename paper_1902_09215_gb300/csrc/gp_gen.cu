@@ -269,13 +269,22 @@ gp_status gp_generation_recover(gp_generation *G, void *cuda_stream)
     if (R.err & (kGErrWork | kGErrItems | kGErrSpill)) {
         BatchCtl c{};
         if ((st = E.read_ctl(&c, s))) return st;
+        // Only what ran out grows: to 1.5x the largest need recorded (the
+        // failing level records its need before it stops), at least double.
+        auto grown = [](uint64_t cap, uint64_t need, uint64_t slack) {
+            return need + slack > cap ? std::max<uint64_t>(2 * cap, need + need / 2 + slack) : cap;
+        };
         uint64_t codes[2], vals[2];
         for (int k = 0; k < 2; ++k) {
-            codes[k] = std::max<uint64_t>(2 * E.w.cap_codes[k], c.need_codes[k] + c.need_codes[k] / 2);
-            vals[k] = std::max<uint64_t>(2 * E.w.cap_values[k], c.need_values[k] + c.need_values[k] / 2);
+            codes[k] = grown(E.w.cap_codes[k], c.need_codes[k], 48);
+            vals[k] = grown(E.w.cap_values[k], c.need_values[k], 0);
         }
-        const uint64_t ded = std::max<uint64_t>(2 * E.w.cap_dedicated, 2 * c.need_dedicated);
-        if ((st = E.set_workspace(E.w.C, codes, vals, ded, 2 * E.w.cap_items))) return st;
+        const uint64_t ded = grown(E.w.cap_dedicated, c.need_dedicated, 0);
+        const uint64_t items = grown(E.w.cap_items, c.need_items, 0);
+        bool same = ded == E.w.cap_dedicated && items == E.w.cap_items;
+        for (int k = 0; k < 2; ++k) same = same && codes[k] == E.w.cap_codes[k] && vals[k] == E.w.cap_values[k];
+        if (same) return GP_EINVAL;              // nothing recorded as short: not a sizing failure
+        if ((st = E.set_workspace(E.w.C, codes, vals, ded, items))) return st;
         G->info.workspace_codes = E.w.cap_codes[0] + E.w.cap_codes[1];
         G->info.workspace_values = E.w.cap_values[0] + E.w.cap_values[1];
     }
