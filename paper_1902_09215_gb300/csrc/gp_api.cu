@@ -675,7 +675,6 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
         const void *codes = P->d_arena;
         bool wide = false;
         const float2 *pt_in = nullptr;
-        uint64_t pt_in_cap = 0, pt_next_cap = 0;     // value entries of pt_in / pt_next
         std::vector<uint64_t> prev_len(big.size());
         for (size_t k = 0; k < big.size(); ++k) prev_len[k] = P->h_size[big[k]];
         std::vector<EvalItem> cur_items = std::move(items);
@@ -719,7 +718,6 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
                 CK(cudaMemsetAsync(u_next + tot[0], 0,
                                    sizeof(uint32_t) * (round_up(tot[0], 16) + 32 - tot[0]), s));
                 CK(ws.alloc((void **)&pt_next, sizeof(float2) * (tot[1] * lanes + 1), s));
-                pt_next_cap = tot[1];
                 P->stats.upper_codes += tot[0];
                 P->stats.value_entries += tot[1];
             }
@@ -756,7 +754,6 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
             p.div0 = P->div0;
             p.window = wide ? cfg.Ku : cfg.K;
             p.pt_in = pt_in;
-            p.pt_in_cap = pt_in_cap;
             p.pt_out = pt_next;
             p.u_out = u_next;
             p.values = P->d_values;
@@ -828,8 +825,6 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
             codes = u_next;
             wide = true;
             pt_in = pt_next;
-            pt_in_cap = pt_next_cap;
-            pt_next_cap = 0;
             ++level;
         }
         return GP_OK;

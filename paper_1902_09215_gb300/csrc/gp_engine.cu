@@ -1009,7 +1009,6 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
         p.div0 = div0;
         p.window = wide ? Ku : K;
         p.pt_in = wide ? w.vals[(level - 1) & 1] : nullptr;
-        p.pt_in_cap = wide ? w.cap_values[(level - 1) & 1] : 0;
         p.pt_out = w.vals[k];
         p.u_out = w.codes[k];
         p.values = bvals_;

@@ -107,10 +107,11 @@ template <> struct Group<uint32_t> {
 };
 
 // Upper-tree variant of the group interpreter: one 32-bit code per operand
-// (%3 + position).  Value-buffer leaves were rewritten, when their entry was
-// staged, into the shared-memory row of that entry counted from the leaf
-// table (row = code - 4), so every leaf is one row read: tb + code * S.
-#define GP_UNODE(CREG, IDX)                                                      \
+// (%3 + position), leaves >= 256 (kPtCode0) read the staged value entry of
+// their position in the group (%24 + position * S), other leaves the leaf
+// table.
+static_assert(kPtCode0 == 256, "the PTX of GP_UNODE compares codes with 256");
+#define GP_UNODE(CREG, J, IDX)                                                   \
     "setp.gt.u32 pl, " CREG ", 3;\n\t"                                         \
     "@pl bra.uni LF" #IDX ";\n\t"                                              \
     "sub.u32 %1, %1, %23;\n\t"                                                 \
@@ -126,27 +127,29 @@ template <> struct Group<uint32_t> {
     "sub.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"                          \
     "AD" #IDX ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
     "LF" #IDX ":\n\tst.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %23;\n\t"          \
-    "mad.lo.u32 a, " CREG ", %23, %19;\n\tld.shared.b64 %0, [a];\n"              \
+    "setp.lt.u32 p, " CREG ", 256;\n\t@p bra.uni TB" #IDX ";\n\t"              \
+    "ld.shared.b64 %0, [%24+" #J "*%23];\n\tbra.uni E" #IDX ";\n"                \
+    "TB" #IDX ":\n\tmad.lo.u32 a, " CREG ", %23, %19;\n\tld.shared.b64 %0, [a];\n" \
     "E" #IDX ":\n\t"
 
-#define GP_UWORD(Q, C3, C2, C1, C0, I0, I1, I2, I3)                              \
+#define GP_UWORD(Q, C3, C2, C1, C0, J3, J2, J1, J0, I0, I1, I2, I3)              \
     "W" #Q ":\n\tsub.u32 dd, %1, %21;\n\tsetp.gt.u32 p, dd, %22;\n\t"               \
     "@p bra.uni X" #Q ";\n\t"                                                     \
-    GP_UNODE(C3, I0) GP_UNODE(C2, I1) GP_UNODE(C1, I2) GP_UNODE(C0, I3)
+    GP_UNODE(C3, J3, I0) GP_UNODE(C2, J2, I1) GP_UNODE(C1, J1, I2) GP_UNODE(C0, J0, I3)
 
 template <uint32_t S>
 __device__ __forceinline__ int group_u32(uint64_t &tos, uint32_t &t, int q, const uint4 *w, uint32_t tb,
-                                         float d0, uint32_t lo, uint32_t span)
+                                         float d0, uint32_t lo, uint32_t span, uint32_t stage)
 {
     asm volatile(
         "{\n\t.reg .pred p, pl;\n\t.reg .b32 a, ret, dd;\n\t.reg .b64 v;\n\t"
         ".reg .f32 tx, ty, bx, by, qx, qy;\n\t"
         "ENT: .branchtargets W0, W1, W2, W3;\n\t"
         "brx.idx.uni %2, ENT;\n"
-        GP_UWORD(3, "%18", "%17", "%16", "%15", 0, 1, 2, 3)
-        GP_UWORD(2, "%14", "%13", "%12", "%11", 4, 5, 6, 7)
-        GP_UWORD(1, "%10", "%9", "%8", "%7", 8, 9, 10, 11)
-        GP_UWORD(0, "%6", "%5", "%4", "%3", 12, 13, 14, 15)
+        GP_UWORD(3, "%18", "%17", "%16", "%15", 15, 14, 13, 12, 0, 1, 2, 3)
+        GP_UWORD(2, "%14", "%13", "%12", "%11", 11, 10, 9, 8, 4, 5, 6, 7)
+        GP_UWORD(1, "%10", "%9", "%8", "%7", 7, 6, 5, 4, 8, 9, 10, 11)
+        GP_UWORD(0, "%6", "%5", "%4", "%3", 3, 2, 1, 0, 12, 13, 14, 15)
         "mov.s32 %2, -1;\n\tbra.uni DONE;\n"
         "X3:\n\tmov.s32 %2, 3;\n\tbra.uni DONE;\n"
         "X2:\n\tmov.s32 %2, 2;\n\tbra.uni DONE;\n"
@@ -162,87 +165,9 @@ __device__ __forceinline__ int group_u32(uint64_t &tos, uint32_t &t, int q, cons
         : "+l"(tos), "+r"(t), "+r"(q)
         : "r"(w[0].x), "r"(w[0].y), "r"(w[0].z), "r"(w[0].w), "r"(w[1].x), "r"(w[1].y), "r"(w[1].z),
           "r"(w[1].w), "r"(w[2].x), "r"(w[2].y), "r"(w[2].z), "r"(w[2].w), "r"(w[3].x), "r"(w[3].y),
-          "r"(w[3].z), "r"(w[3].w), "r"(tb), "f"(d0), "r"(lo), "r"(span), "n"(S));
+          "r"(w[3].z), "r"(w[3].w), "r"(tb), "f"(d0), "r"(lo), "r"(span), "n"(S), "r"(stage));
     return q;
 }
-
-// ---------------------------------------------------------------- bulk staging
-
-// Upper levels read their codes and the value entries those codes name
-// through bulk asynchronous copies (the TMA engine's 1-D form) into
-// shared memory, completed on mbarriers.  Every wait is bounded: a copy
-// that has not landed after kWaitNs nanoseconds is reported (kErrStage)
-// instead of waited for.
-constexpr uint64_t kWaitNs = 1000000000ull;
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
-                 ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    return ok != 0;
-}
-// Waits for the phase of parity `parity` to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
-    }
-}
-// Global -> shared bulk copy of `bytes` (a multiple of 16, both addresses
-// 16-byte aligned), counted on mbarrier `bar`.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-// Orders this thread's earlier shared-memory accesses before later bulk
-// copies into the same bytes.
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t lds32(uint32_t a) {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
-}
-__device__ __forceinline__ uint4 lds128(uint32_t a) {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
-    return v;
-}
-
-// Per-warp staging state of an upper-level warp.  Barriers: kStageAhead
-// value barriers (group g uses g % kStageAhead), then kCodeSlots code-block
-// barriers; `phase` holds the parity each barrier waits for next (bit i).
-struct Stage {
-    uint32_t ring;        // shared address of value entry 0 (lane column added)
-    uint32_t ring_row0;   // leaf-table row code of value entry 0
-    uint32_t codes;       // shared address of the code blocks
-    uint32_t bars;        // shared address of the barriers
-    uint32_t phase;
-    bool broken;          // a wait ran out: this warp takes no more items
-};
 
 // ---------------------------------------------------------------- one item
 
@@ -268,6 +193,14 @@ __device__ __forceinline__ uint64_t lds64(uint32_t a) {
     asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
     return v;
 }
+
+// Asynchronous 8-byte global -> shared copies (value-buffer staging).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
 
 // The group interpreter below keeps the top of stack `tos` in a register and
 // the rest of the operand stack in this lane's column of the shared window;
@@ -346,7 +279,7 @@ __device__ __forceinline__ int group_u8(uint64_t &tos, uint32_t &t, int q, uint4
 
 template <int LANES, typename Code, bool WIDE>
 __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *itp, uint32_t win_sa,
-                                          uint32_t tbl_sa, Stage &stg, float *errs,
+                                          uint32_t tbl_sa, uint32_t stage_sa, float *errs,
                                           float2 *__restrict__ spill, uint64_t spill_cap, int lane,
                                           uint32_t mask, float y0, float y1)
 {
@@ -378,11 +311,13 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
     uint32_t fault = 0;                   // kErr* bits; any fault ends the item
     const uint32_t dmax = (uint32_t)(K - 4) * S;   // room for four pushes below this
 
-    // Leaves: 'x' and constants are leaf-table rows; on upper levels a
-    // value-buffer leaf was rewritten into the row of its staged entry, so
-    // codes 4 .. leaf_lim-1 are the table's own leaves.
-    const uint32_t leaf_lim = 4u + (P.leaf_rows ? P.leaf_rows : kLeafRows);
-    auto leafval = [&](uint32_t c) -> uint64_t { return lds64(tb + c * S); };
+    // Upper trees: value-buffer leaves of the current group were copied to
+    // staging buffer `buf`, slot = position in the group (jcur).
+    uint32_t buf = 0, jcur = 0;
+    auto leafval = [&](uint32_t c) -> uint64_t {
+        if (WIDE && c >= kPtCode0) return lds64(stage_sa + (buf * 16 + jcur) * S);
+        return lds64(tb + c * S);
+    };
     if (rope && P.fz_over[IT(tree)]) {
         // A chunk of this tree ran out of value slots: queue the tree for a
         // re-evaluation through planned upper-tree levels.
@@ -391,6 +326,20 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
     }
     const float2 *pt_src = P.pt_in;       // value entries read by the current range
     uint64_t rb = IT(begin), re = IT(end);  // the current range
+    auto stage = [&](const Group<Code> &grp, int64_t gbase, uint32_t into) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const typename Group<Code>::Sub v = grp.sub(q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t c = Group<Code>::code(v, k);
+                const uint64_t pos = (uint64_t)gbase + 4 * q + k;
+                if (pos >= rb && pos < re && c >= kPtCode0)
+                    cp_async8(stage_sa + (into * 16 + 4 * q + k) * S,
+                              pt_src + (uint64_t)(c - kPtCode0) * LANES + lane);
+            }
+        }
+    };
     // Fragment output stays inside the slot reserved for it.
     auto emit = [&](uint32_t code) {
         const uint64_t cap = fused ? P.fz_cap_codes : IT(frag_len);
@@ -458,7 +407,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
             // other first argument becomes an entry of this level's value
             // buffer (entries of the previous level's buffer are not visible
             // to the next level, so they are copied too).
-            if (have) emit((prev >= 4 && prev < leaf_lim) ? prev : new_pt(tos));
+            if (have) emit((prev >= 4 && prev < kPtCode0) ? prev : new_pt(tos));
             emit(c);
             have = false;
         }
@@ -472,19 +421,16 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
     const uint32_t nranges = rope ? IT(frag_len) : 1;
     for (uint32_t r = 0; r < nranges && !fault; ++r) {
     const Code *codes = codes0;
-    uint64_t pt_lim = P.pt_in_cap;        // entries the current range may name
     if (rope) {
         const uint64_t slot = IT(pt_base) + (nranges - 1 - r);
         codes = reinterpret_cast<const Code *>(P.fz_codes + slot * P.fz_cap_codes);
         re = P.fz_cap_codes;
         rb = re - P.fz_len[slot];
         pt_src = P.fz_pt + slot * P.fz_cap_pt * LANES;
-        pt_lim = P.fz_cap_pt;
     }
     const uint64_t b = rb, e = re;
     if (e <= b) continue;
     if constexpr (!WIDE) {
-        (void)pt_lim;
         int64_t gs = (int64_t)((e - 1) & ~15ull);
         const int64_t glo = (int64_t)(b & ~15ull);
         Group<Code> cur;
@@ -526,125 +472,29 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
             cur = nxt;
         }
     } else {
-        // ---- upper-tree codes: groups i = 0, 1, ... from the right end.
-        // Codes arrive by blocks of kCodeBlk groups (one bulk copy each) into
-        // kCodeSlots rotating block slots; then, up to kStageAhead groups
-        // ahead of the interpreter and as far as the ring has room, every
-        // value-buffer leaf of a group gets the next ring entry, a bulk copy
-        // of its value into it, and its code rewritten to that entry's row.
-        const uint64_t ghi = (e - 1) & ~15ull;
-        const uint32_t ng = (uint32_t)((ghi - (b & ~15ull)) / 16 + 1);
-        const uint32_t nblk = (ng + kCodeBlk - 1) / kCodeBlk;
-        const uint32_t vb = stg.bars, cbar = stg.bars + kStageAhead * 8;
-        uint32_t blk_issued = 0, blk_ready = 0;        // code blocks copied / waited for
-        uint32_t gp = 0;                               // next group to stage
-        uint32_t kp = 0, kc = 0;                       // ring entries staged / consumed
-        uint64_t cnt = 0;                              // entries per staged group (8 bits each)
-        auto group_codes = [&](uint32_t gi) -> uint32_t {   // shared address of group gi's codes
-            return stg.codes + (((gi / kCodeBlk) % kCodeSlots) * kCodeBlk + (kCodeBlk - 1 - gi % kCodeBlk)) * 64u;
-        };
-        auto wait_bar = [&](uint32_t bar, uint32_t bit) {
-            // every lane polls (each sees the copied bytes); the outcome is
-            // made warp-uniform
-            if (!__all_sync(mask, mbar_wait(bar, (stg.phase >> bit) & 1u))) {
-                fault |= kErrStage;
-                stg.broken = true;
-            }
-            stg.phase ^= 1u << bit;
-        };
-        // Copies code blocks into free slots (a slot is free once every
-        // group of its previous block was interpreted).
-        auto issue_codes = [&](uint32_t gi_consumed) {
-            while (blk_issued < nblk && blk_issued < gi_consumed / kCodeBlk + kCodeSlots) {
-                const uint32_t k = blk_issued++;
-                const uint32_t n = umin64(kCodeBlk, ng - k * kCodeBlk);
-                const uint32_t slot = k % kCodeSlots;
-                fence_proxy_async();
-                __syncwarp(mask);
-                if (lane == 0) {
-                    mbar_arrive_tx(cbar + slot * 8, n * 64);
-                    bulk_g2s(stg.codes + (slot * kCodeBlk + kCodeBlk - n) * 64u,
-                             codes + (ghi - 16ull * (k * kCodeBlk + n - 1)), n * 64, cbar + slot * 8);
-                }
-            }
-        };
-        // Stages groups gp.. while they are few enough groups ahead of group
-        // gi and their entries fit the ring.  Lane j (and j + LANES, ...)
-        // looks at code j of the group.
-        constexpr int kRounds = (16 + LANES - 1) / LANES;
-        auto stage_groups = [&](uint32_t gi) {
-            while (gp < ng && gp < gi + kStageAhead && !fault) {
-                const uint32_t k = gp / kCodeBlk;
-                if (k >= blk_ready) {             // first group of a block: its codes landed?
-                    wait_bar(cbar + (k % kCodeSlots) * 8, kStageAhead + k % kCodeSlots);
-                    blk_ready = k + 1;
-                    if (fault) break;
-                }
-                const uint32_t ca = group_codes(gp);
-                uint32_t cj[kRounds];
-                uint32_t m_pt = 0;                // bit j: code j names a value entry
-                bool bad = false;
-#pragma unroll
-                for (int r0 = 0; r0 < kRounds; ++r0) {
-                    const uint32_t j = r0 * LANES + lane;
-                    bool is_pt = false;
-                    cj[r0] = 0;
-                    if (j < 16) {
-                        cj[r0] = lds32(ca + 4u * j);
-                        const uint64_t pos = ghi - 16ull * gp + j;
-                        is_pt = pos >= b && pos < e && cj[r0] >= kPtCode0;
-                        bad = bad || (is_pt && (uint64_t)(cj[r0] - kPtCode0) >= pt_lim);
-                    }
-                    m_pt |= __ballot_sync(mask, is_pt) << (r0 * LANES);
-                }
-                if (__any_sync(mask, bad)) {
-                    fault |= kErrPlan;            // names an entry outside the buffer
-                    break;
-                }
-                m_pt &= 0xFFFFu;
-                const uint32_t m = __popc(m_pt);
-                if (kp - kc + m > kRing) break;  // no room yet: stage it later
-                const uint32_t gb = vb + (gp % kStageAhead) * 8;
-                fence_proxy_async();
-                __syncwarp(mask);
-                if (lane == 0) mbar_arrive_tx(gb, m * S);
-                __syncwarp(mask);
-#pragma unroll
-                for (int r0 = 0; r0 < kRounds; ++r0) {
-                    const uint32_t j = r0 * LANES + lane;
-                    if (j < 16 && ((m_pt >> j) & 1u)) {
-                        const uint32_t slot = (kp + __popc(m_pt & ((1u << j) - 1u))) % kRing;
-                        bulk_g2s(stg.ring + slot * S, pt_src + (uint64_t)(cj[r0] - kPtCode0) * LANES, S, gb);
-                        sts32(ca + 4u * j, stg.ring_row0 + slot);
-                    }
-                }
-                kp += m;
-                const uint32_t sh = 8 * (gp % kStageAhead);
-                cnt = (cnt & ~(0xFFull << sh)) | ((uint64_t)m << sh);
-                ++gp;
-            }
-        };
-        uint32_t gw = 0;                               // groups whose values were waited for
-        for (uint32_t i = 0; i < ng && !fault; ++i) {
-            issue_codes(i);
-            stage_groups(i);
-            if (fault) break;
-            wait_bar(vb + (i % kStageAhead) * 8, i % kStageAhead);   // group i staged (gp > i)
-            gw = i + 1;
-            if (fault) break;
-            __syncwarp(mask);                 // rewritten codes visible to every lane
-            Group<Code> cur;
-            const uint32_t ca = group_codes(i);
-            cur.w[0] = lds128(ca);
-            cur.w[1] = lds128(ca + 16);
-            cur.w[2] = lds128(ca + 32);
-            cur.w[3] = lds128(ca + 48);
-            const uint64_t gs = ghi - 16ull * i;
-            const bool full = gs >= b && gs + 16 <= e;
+        // Upper-tree codes: the value entries a group names are copied
+        // (cp.async) into a staging buffer one group ahead of the
+        // interpreter, the codes themselves are loaded two groups ahead.
+        int64_t gs = (int64_t)((e - 1) & ~15ull);
+        const int64_t glo = (int64_t)(b & ~15ull);
+        Group<Code> cur, nxt;
+        cur.load(codes + gs);
+        if (gs - 16 >= glo) nxt.load(codes + gs - 16);
+        buf = 0;                              // each range starts its own pipeline
+        stage(cur, gs, 0);
+        cp_async_commit();
+        for (; gs >= glo; gs -= 16) {
+            Group<Code> nxt2;
+            if (gs - 32 >= glo) nxt2.load(codes + gs - 32);
+            // Copies for the next group overlap this group's work.
+            if (gs - 16 >= glo) stage(nxt, gs - 16, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait1();
+            const bool full = (uint64_t)gs >= b && (uint64_t)gs + 16 <= e;
             if (full) {
                 int q = 3;
                 for (;;) {
-                    q = group_u32<S>(tos, t, q, cur.w, tb, d0, fast_lo, fast_span);
+                    q = group_u32<S>(tos, t, q, cur.w, tb, d0, fast_lo, fast_span, stage_sa + buf * 16 * S);
                     if (q < 0) break;
                     rebalance();
                     if (fault) break;
@@ -652,7 +502,10 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
                     if (q < 3) prev = Group<Code>::code(cur.sub(q + 1), 0);
                     const typename Group<Code>::Sub v = cur.sub(q);
 #pragma unroll
-                    for (int k = 3; k >= 0; --k) step_checked(Group<Code>::code(v, k));
+                    for (int k = 3; k >= 0; --k) {
+                        jcur = 4 * q + k;
+                        step_checked(Group<Code>::code(v, k));
+                    }
                     if (fault || --q < 0) break;
                 }
                 prev = cur.first();
@@ -664,21 +517,18 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
                     if (fault) break;
 #pragma unroll
                     for (int k = 3; k >= 0; --k) {
-                        const uint64_t pos = gs + 4 * q + k;
+                        const uint64_t pos = (uint64_t)gs + 4 * q + k;
+                        jcur = 4 * q + k;
                         if (pos >= b && pos < e) step_checked(Group<Code>::code(v, k));
                     }
                 }
             }
-            kc += (uint32_t)(cnt >> (8 * (i % kStageAhead))) & 0xFFu;
+            if (fault) break;
+            cur = nxt;
+            nxt = nxt2;
+            buf ^= 1;
         }
-        // Every copy issued must land before the buffers are used again:
-        // wait for staged groups not interpreted and code blocks not read.
-        if (!stg.broken) {
-            for (; gw < gp; ++gw) wait_bar(vb + (gw % kStageAhead) * 8, gw % kStageAhead);
-            for (; blk_ready < blk_issued; ++blk_ready)
-                wait_bar(cbar + (blk_ready % kCodeSlots) * 8, kStageAhead + blk_ready % kCodeSlots);
-        }
-        __syncwarp(mask);
+        cp_async_wait0();                     // staging is idle before the next item
     }
     }
     if (!rope && IT(end) <= IT(begin) && is_final) {
@@ -690,7 +540,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
         const uint32_t tr = IT(tree);
         const uint32_t nc = P.n_cases;
         const bool ok = !fault && have && sp == 0 && g == 0;
-        if (rope && fault && !(fault & kErrStage)) {   // e.g. deeper than the spill area: redo as planned
+        if (rope && fault) {              // e.g. deeper than the spill area: redo as planned
             if (lane == 0) P.fz_redo[1 + atomicAdd(P.fz_redo, 1u)] = tr;
             return;
         }
@@ -756,14 +606,10 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     constexpr uint32_t S = LANES * sizeof(float2);
     const uint32_t rows = P.leaf_rows ? P.leaf_rows : kLeafRows;
     const uint32_t win0 = rows * S;                         // first window (bytes)
-    // Upper-tree kernels, after the windows: one ring of kRing value entries
-    // per warp (rows of S bytes, like the table's), then per warp the code
-    // blocks and the mbarriers.
+    // Upper-tree kernels: two 16-entry staging buffers per warp after the windows.
     const uint32_t stage0 = win0 + (uint32_t)nwarps * P.window * S;
-    const uint32_t codes0 = stage0 + (WIDE ? (uint32_t)nwarps * kRing * S : 0u);
-    const uint32_t bars0 = codes0 + (WIDE ? (uint32_t)nwarps * kCodeSlots * kCodeBlk * 64 : 0u);
     // Then one item copy (64 bytes) per warp.
-    const uint32_t item0 = bars0 + (WIDE ? (uint32_t)nwarps * (kStageAhead + kCodeSlots) * 8 : 0u);
+    const uint32_t item0 = stage0 + (WIDE ? (uint32_t)nwarps * 32 * S : 0u);
 
     // (a launch whose device-side item count is zero does no setup at all)
     if (P.n_items_dev && *P.n_items_dev == 0) return;
@@ -788,18 +634,6 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
     const uint64_t gw = (uint64_t)blockIdx.x * nwarps + warp;
     float2 *myspill = P.spill + gw * P.spill_per_warp * LANES;
     const uint32_t n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
-    Stage stg{};
-    if constexpr (WIDE) {
-        stg.ring = sbase + stage0 + (uint32_t)warp * kRing * S;
-        stg.ring_row0 = (stage0 + (uint32_t)warp * kRing * S) / S + 4u;
-        stg.codes = sbase + codes0 + (uint32_t)warp * kCodeSlots * kCodeBlk * 64;
-        stg.bars = sbase + bars0 + (uint32_t)warp * (kStageAhead + kCodeSlots) * 8;
-        if (lane == 0) {
-            for (uint32_t k = 0; k < kStageAhead + kCodeSlots; ++k) mbar_init(stg.bars + 8 * k, 1);
-            mbar_fence_init();
-        }
-        __syncwarp(mask);
-    }
 
     for (;;) {
         uint32_t idx = 0;
@@ -819,16 +653,17 @@ __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P
             area = P.spill + soff * LANES;
             cap = itp->spill_cap;
         }
-        eval_item<LANES, Code, WIDE>(P, itp, sbase + win_off, sbase, stg, errs, area, cap, lane, mask, y0, y1);
-        if (WIDE && stg.broken) break;    // its staging buffers may still be written
+        eval_item<LANES, Code, WIDE>(P, itp, sbase + win_off, sbase,
+                                     sbase + stage0 + (uint32_t)warp * 32 * S + lane * 8u, errs, area,
+                                     cap, lane, mask, y0, y1);
     }
 }
 
 size_t eval_smem_bytes(int lanes, int warps, int window, bool wide, int leaf_rows)
 {
     return (size_t)leaf_rows * lanes * sizeof(float2) +
-           (size_t)warps * (window + (wide ? kRing : 0)) * lanes * sizeof(float2) +
-           (size_t)warps * ((wide ? kStageBytesPerWarp : 0) + sizeof(EvalItem));
+           (size_t)warps * (window + (wide ? 32 : 0)) * lanes * sizeof(float2) +
+           (size_t)warps * sizeof(EvalItem);
 }
 
 template <int LANES>

@@ -19,16 +19,6 @@ constexpr uint32_t kErrMalformed = 1u;  // final item ended with != 1 value or u
 constexpr uint32_t kErrSpill = 2u;      // operand stack outgrew its spill area
 constexpr uint32_t kErrPlan = 4u;       // fragment emitted a different shape than planned
 constexpr uint32_t kErrExtent = 8u;     // subtree extent walked off the end of a tree
-constexpr uint32_t kErrStage = 16u;     // a bulk copy of upper-tree codes or values never landed
-
-// Upper-tree staging (32-bit code levels): per warp, a ring of kRing value
-// entries and kCodeSlots blocks of kCodeBlk 16-code groups filled by bulk
-// copies, with value entries staged up to kStageAhead groups ahead.
-constexpr uint32_t kRing = 48;
-constexpr uint32_t kStageAhead = 8;
-constexpr uint32_t kCodeBlk = 4;
-constexpr uint32_t kCodeSlots = 4;
-constexpr uint32_t kStageBytesPerWarp = kCodeSlots * kCodeBlk * 64 + (kStageAhead + kCodeSlots) * 8;
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
@@ -99,7 +89,6 @@ struct EvalParams {
     uint32_t fz_cap_codes;
     uint32_t fz_cap_pt;
     uint32_t leaf_rows;            // leaf table rows ('x' + constants); 0 = kLeafRows
-    uint64_t pt_in_cap;            // entries readable in pt_in (upper levels)
 };
 
 struct XoChild {                   // child = M[0,i) ++ D[j,e_d) ++ M[e_m,n_m)
