@@ -256,29 +256,49 @@ uint64_t population_bytes(uint64_t arena, uint32_t n_trees, uint32_t n_cases)
 }
 
 // Allocate a population's device memory for the given layout (trees not
-// copied yet) and upload the problem tables.
+// copied yet) and upload the problem tables.  Two allocations: the tree
+// arena, and one block carved into every per-tree array and the tables
+// (fewer API calls per population: children are made every generation).
 gp_status alloc_population(gp_population *P, cudaStream_t s)
 {
     P->stream = s;
     CK(P->mem.alloc((void **)&P->d_arena, P->arena_bytes, s));
-    CK(P->mem.alloc((void **)&P->d_start, sizeof(uint64_t) * (P->n_trees + 1), s));
-    CK(P->mem.alloc((void **)&P->d_size, sizeof(uint64_t) * (P->n_trees + 1), s));
-    CK(P->mem.alloc((void **)&P->d_fitness, sizeof(float) * (P->n_trees + 1), s));
-    CK(P->mem.alloc((void **)&P->d_values, sizeof(float) * ((uint64_t)P->n_trees * P->n_cases + 1), s));
-    CK(P->mem.alloc((void **)&P->d_hits, sizeof(uint32_t) * (P->n_trees + 1), s));
-    CK(P->mem.alloc((void **)&P->d_err, sizeof(uint32_t) * 4, s));
-    CK(P->mem.alloc((void **)&P->d_redo, sizeof(uint32_t) * (P->n_trees + 1), s));
-    CK(cudaMemsetAsync(P->d_redo, 0, sizeof(uint32_t), s));
-    CK(P->mem.alloc((void **)&P->d_x, sizeof(float) * 2 * P->lanes, s));
-    CK(P->mem.alloc((void **)&P->d_y, sizeof(float) * 2 * P->lanes, s));
-    CK(P->mem.alloc((void **)&P->d_c, sizeof(float) * (P->n_consts + 1), s));
-    CK(h2d(P->d_x, P->hx.data(), sizeof(float) * 2 * P->lanes, s));
-    CK(h2d(P->d_y, P->hy.data(), sizeof(float) * 2 * P->lanes, s));
-    if (P->n_consts) CK(h2d(P->d_c, P->hc.data(), sizeof(float) * P->n_consts, s));
-    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
+    const uint64_t n1 = (uint64_t)P->n_trees + 1;
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t o = off;
+        off = round_up(off + bytes, 256);
+        return o;
+    };
+    const uint64_t o_pos = take(2 * sizeof(uint64_t) * n1);        // starts, then sizes
+    const uint64_t o_err = take(sizeof(uint32_t) * (4 + n1));       // error words, then redo list
+    const uint64_t o_tab = take(sizeof(float) * (4 * P->lanes + P->n_consts + 1));   // x, y, constants
+    const uint64_t o_fit = take(sizeof(float) * n1);
+    const uint64_t o_hits = take(sizeof(uint32_t) * n1);
+    const uint64_t o_vals = take(sizeof(float) * ((uint64_t)P->n_trees * P->n_cases + 1));
+    uint8_t *blk = nullptr;
+    CK(P->mem.alloc((void **)&blk, off, s));
+    P->d_start = reinterpret_cast<uint64_t *>(blk + o_pos);
+    P->d_size = P->d_start + n1;
+    P->d_err = reinterpret_cast<uint32_t *>(blk + o_err);
+    P->d_redo = P->d_err + 4;
+    P->d_x = reinterpret_cast<float *>(blk + o_tab);
+    P->d_y = P->d_x + 2 * P->lanes;
+    P->d_c = P->d_y + 2 * P->lanes;
+    P->d_fitness = reinterpret_cast<float *>(blk + o_fit);
+    P->d_hits = reinterpret_cast<uint32_t *>(blk + o_hits);
+    P->d_values = reinterpret_cast<float *>(blk + o_vals);
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 5, s));    // error words and redo count
+    std::vector<float> tab(4 * P->lanes + P->n_consts);
+    std::copy(P->hx.begin(), P->hx.begin() + 2 * P->lanes, tab.begin());
+    std::copy(P->hy.begin(), P->hy.begin() + 2 * P->lanes, tab.begin() + 2 * P->lanes);
+    std::copy(P->hc.begin(), P->hc.begin() + P->n_consts, tab.begin() + 4 * P->lanes);
+    CK(h2d(P->d_x, tab.data(), sizeof(float) * tab.size(), s));
     if (P->n_trees) {
-        CK(h2d(P->d_start, P->h_start.data(), sizeof(uint64_t) * P->n_trees, s));
-        CK(h2d(P->d_size, P->h_size.data(), sizeof(uint64_t) * P->n_trees, s));
+        std::vector<uint64_t> pos(2 * n1, 0);
+        std::copy(P->h_start.begin(), P->h_start.end(), pos.begin());
+        std::copy(P->h_size.begin(), P->h_size.end(), pos.begin() + n1);
+        CK(h2d(P->d_start, pos.data(), sizeof(uint64_t) * pos.size(), s));
     }
     CK(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
     return GP_OK;
@@ -326,10 +346,11 @@ gp_status run_copy(const uint8_t *src, uint8_t *dst, const std::vector<XoChild> 
         for (uint64_t b = 0; b < kids[c].n; b += tile) tiles.push_back(XoTile{c, 0, b});
     if (tiles.empty()) return GP_OK;
     if (tiles.size() > 0x7fffffffu) return GP_EINVAL;
-    XoChild *d_kids;
-    XoTile *d_tiles;
-    CK(tmp.alloc((void **)&d_kids, sizeof(XoChild) * kids.size(), s));
-    CK(tmp.alloc((void **)&d_tiles, sizeof(XoTile) * tiles.size(), s));
+    uint8_t *blk;
+    const uint64_t o_tiles = round_up(sizeof(XoChild) * kids.size(), 256);
+    CK(tmp.alloc((void **)&blk, o_tiles + sizeof(XoTile) * tiles.size(), s));
+    XoChild *d_kids = reinterpret_cast<XoChild *>(blk);
+    XoTile *d_tiles = reinterpret_cast<XoTile *>(blk + o_tiles);
     CK(h2d(d_kids, kids.data(), sizeof(XoChild) * kids.size(), s));
     CK(h2d(d_tiles, tiles.data(), sizeof(XoTile) * tiles.size(), s));
     ProfScope ps(GP_KERNEL_COPY, s);
@@ -590,20 +611,37 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
     CK(prepare_eval_once(lanes, true, cfg.smem_u));
     DevBufs ws;
     auto body = [&]() -> gp_status {
+        // Small and medium trees, largest first (ties in the given order):
+        // sorted as 64-bit keys (size complement, position), sizes of both
+        // fit 32 bits.
         std::vector<uint32_t> small, medium, big;
-        for (uint32_t t : trees) {
-            const uint64_t n = P->h_size[t];
-            if (n <= C) small.push_back(t);
-            else if (allow_fused && n <= (uint64_t)kFuseMaxChunks * C) medium.push_back(t);
-            else big.push_back(t);
+        std::vector<uint64_t> ks, km;
+        ks.reserve(trees.size());
+        uint64_t n_chunks = 0;
+        for (uint32_t i = 0; i < (uint32_t)trees.size(); ++i) {
+            const uint64_t n = P->h_size[trees[i]];
+            const uint64_t key = ((0xFFFFFFFFull - n) << 32) | i;
+            if (n <= C) {
+                ks.push_back(key);
+            } else if (allow_fused && n <= (uint64_t)kFuseMaxChunks * C) {
+                km.push_back(key);
+                n_chunks += (n + C - 1) / C;
+            } else {
+                big.push_back(trees[i]);
+                n_chunks += (n + C - 1) / C;
+            }
         }
-        auto by_size = [&](uint32_t a, uint32_t b) { return P->h_size[a] > P->h_size[b]; };
-        std::stable_sort(small.begin(), small.end(), by_size);
-        std::stable_sort(medium.begin(), medium.end(), by_size);
+        std::sort(ks.begin(), ks.end());
+        std::sort(km.begin(), km.end());
+        small.resize(ks.size());
+        medium.resize(km.size());
+        for (size_t k = 0; k < ks.size(); ++k) small[k] = trees[(uint32_t)ks[k]];
+        for (size_t k = 0; k < km.size(); ++k) medium[k] = trees[(uint32_t)km[k]];
 
         // ---- level 0: planned chunks of large trees, fused chunks of medium
         // trees (largest first), whole small trees (largest first)
         std::vector<EvalItem> items;
+        items.reserve(n_chunks + small.size());
         std::vector<uint32_t> first_chunk;          // per large tree: first fragment item
         for (uint32_t t : big) {
             first_chunk.push_back((uint32_t)items.size());
@@ -619,6 +657,7 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
         first_chunk.push_back((uint32_t)items.size());
         const uint32_t n_frag0 = (uint32_t)items.size();
         std::vector<EvalItem> ropes;
+        ropes.reserve(medium.size());
         uint64_t slots = 0;
         for (uint32_t t : medium) {
             const uint32_t m = (uint32_t)((P->h_size[t] + C - 1) / C);
@@ -655,20 +694,27 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
 
         const uint64_t warps_total = (uint64_t)sms * cfg.W;   // >= warps of any level
         const uint64_t spill_per_warp = C;                    // a chunk never holds more
-        uint32_t *d_counter;
-        CK(ws.alloc((void **)&d_counter, sizeof(uint32_t) * 64, s));
-        CK(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t) * 64, s));
-        // fused slots
+        // One block for the level counters and the fused slots: counters and
+        // overflow flags (zeroed together), slot lengths, codes, values.
         const uint32_t pt_cap = fuse_pt_cap(C);
-        uint32_t *fz_codes = nullptr, *fz_len = nullptr, *fz_over = nullptr;
+        uint32_t *d_counter, *fz_codes = nullptr, *fz_len = nullptr, *fz_over = nullptr;
         float2 *fz_pt = nullptr;
-        if (slots) {
-            CK(ws.alloc((void **)&fz_codes, sizeof(uint32_t) * (slots * C + 32), s));
-            CK(ws.alloc((void **)&fz_pt, sizeof(float2) * (slots * pt_cap * lanes + 1), s));
-            CK(ws.alloc((void **)&fz_len, sizeof(uint32_t) * slots, s));
-            CK(ws.alloc((void **)&fz_over, sizeof(uint32_t) * P->n_trees, s));
-            CK(cudaMemsetAsync(fz_over, 0, sizeof(uint32_t) * P->n_trees, s));
-            P->redo_pending = true;
+        {
+            const uint64_t o_over = 256, o_len = round_up(o_over + 4ull * (slots ? P->n_trees : 0), 256);
+            const uint64_t o_codes = round_up(o_len + 4ull * slots, 256);
+            const uint64_t o_pt = round_up(o_codes + (slots ? 4ull * (slots * C + 32) : 0), 256);
+            const uint64_t end = o_pt + (slots ? 8ull * (slots * pt_cap * lanes + 1) : 0);
+            uint8_t *blk;
+            CK(ws.alloc((void **)&blk, end, s));
+            CK(cudaMemsetAsync(blk, 0, o_len, s));
+            d_counter = reinterpret_cast<uint32_t *>(blk);
+            if (slots) {
+                fz_over = reinterpret_cast<uint32_t *>(blk + o_over);
+                fz_len = reinterpret_cast<uint32_t *>(blk + o_len);
+                fz_codes = reinterpret_cast<uint32_t *>(blk + o_codes);
+                fz_pt = reinterpret_cast<float2 *>(blk + o_pt);
+                P->redo_pending = true;
+            }
         }
 
         // level state
@@ -937,22 +983,25 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
                 q[2 * k] = ExtentQuery{M->h_start[ops[k].mum], M->h_size[ops[k].mum], ops[k].mum_point};
                 q[2 * k + 1] = ExtentQuery{M->h_start[ops[k].dad], M->h_size[ops[k].dad], ops[k].dad_point};
             }
-            ExtentQuery *d_q;
-            uint64_t *d_end;
-            uint32_t *d_err;
-            CK(tmp.alloc((void **)&d_q, sizeof(ExtentQuery) * q.size(), s));
-            CK(tmp.alloc((void **)&d_end, sizeof(uint64_t) * q.size(), s));
-            CK(tmp.alloc((void **)&d_err, sizeof(uint32_t), s));
+            // one block: error word, ends, queries
+            const uint64_t o_end = 256, o_q = round_up(o_end + sizeof(uint64_t) * q.size(), 256);
+            uint8_t *blk;
+            CK(tmp.alloc((void **)&blk, o_q + sizeof(ExtentQuery) * q.size(), s));
+            uint32_t *d_err = reinterpret_cast<uint32_t *>(blk);
+            uint64_t *d_end = reinterpret_cast<uint64_t *>(blk + o_end);
+            ExtentQuery *d_q = reinterpret_cast<ExtentQuery *>(blk + o_q);
             CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
             CK(h2d(d_q, q.data(), sizeof(ExtentQuery) * q.size(), s));
             {
                 ProfScope ps(GP_KERNEL_EXTENT, s);
                 CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_err, s));
             }
-            uint32_t err = 0;
-            CK(cudaMemcpyAsync(ends.data(), d_end, sizeof(uint64_t) * q.size(), cudaMemcpyDeviceToHost, s));
-            CK(cudaMemcpyAsync(&err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            // error word and ends in one read-back
+            std::vector<uint64_t> back(32 + q.size());
+            CK(cudaMemcpyAsync(back.data(), blk, o_end + sizeof(uint64_t) * q.size(), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            const uint32_t err = static_cast<uint32_t>(back[0]);
+            std::copy(back.begin() + 32, back.end(), ends.begin());
             if (err) return GP_EMALFORMED;
         }
         for (uint32_t k = 0; k < n_ops; ++k) {
