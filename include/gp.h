@@ -100,9 +100,18 @@ gp_status gp_create_population(const gp_problem *problem, uint32_t n_trees,
 /* Create one child per record (Sec. 3.1; the choice of points is the
  * caller's, made sequentially as in Sec. 2.3, and the copies run on the
  * device).  Children form a new population with the parents' problem; its
- * fitness is not evaluated.  Synchronises once to size the children.
+ * fitness is not evaluated.  Every child has at most
+ * n_mum + n_dad - dad_point - 1 nodes; when no such bound exceeds
+ * problem->max_tree_nodes and their total fits the arena limit (four times
+ * the parents' arena or 256 MiB, at most 16 GiB, and the HBM budget), the
+ * call does not synchronise: the children are sized and laid out on the
+ * device in an arena of that total, and a call that needs their sizes on
+ * the host (gp_tree_size, gp_tree_read, gp_population_get_info, a crossover
+ * with them as parents) waits for the stream and reads them then.
+ * Otherwise it synchronises once to size the children exactly.
  * Errors: GP_EINVAL (index or point out of range), GP_ELIMIT (a child exceeds
- * problem->max_tree_nodes), GP_ENOMEM, GP_ECUDA. */
+ * problem->max_tree_nodes; only a synchronising call can see it),
+ * GP_ENOMEM, GP_ECUDA. */
 gp_status gp_crossover(const gp_population *parents, const gp_xo *ops, uint32_t n_ops,
                        void *cuda_stream, gp_population **children_out);
 
@@ -112,7 +121,10 @@ gp_status gp_crossover(const gp_population *parents, const gp_xo *ops, uint32_t 
  * Sec. 3.2) and its hit count.  Asynchronous on `cuda_stream`, except that
  * trees of more than 32 chunks (chunk_nodes, default 4096) have their upper
  * trees sized on the device and read back, one short synchronisation per
- * upper-tree level.  Results are read with gp_fitness.
+ * upper-tree level.  Children whose sizes are still on the device only and
+ * whose bounds stay within 32 chunks get their work items built on the
+ * device (no synchronisation); otherwise their sizes are read first.
+ * Results are read with gp_fitness.
  * Errors: GP_EINVAL, GP_ENOMEM, GP_ECUDA. */
 gp_status gp_evaluate(gp_population *pop, void *cuda_stream);
 gp_status gp_evaluate_ex(gp_population *pop, const gp_eval_options *opt, void *cuda_stream);
@@ -130,7 +142,9 @@ gp_status gp_evaluate_ex(gp_population *pop, const gp_eval_options *opt, void *c
 gp_status gp_fitness(const gp_population *pop, float *fitness, float *case_values,
                      uint32_t *hits);
 
-/* Node count of tree `tree`.  Errors: GP_EINVAL. */
+/* Node count of tree `tree` (may wait for the stream of a crossover that
+ * made the population without a synchronisation).  Errors: GP_EINVAL,
+ * GP_EMALFORMED (that crossover met a subtree running off its parent). */
 gp_status gp_tree_size(const gp_population *pop, uint32_t tree, uint64_t *n);
 
 /* Copy tree `tree`'s bytes to host `dst` (cap >= its size).  Synchronous.

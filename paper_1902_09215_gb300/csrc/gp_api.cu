@@ -233,6 +233,14 @@ struct gp_population {
     uint32_t n_trees = 0;
     uint64_t total_nodes = 0, arena_bytes = 0;
     std::vector<uint64_t> h_start, h_size;
+    // Children made without a host synchronisation have their layout on the
+    // device only (d_start, d_size) until a call needs it on the host; until
+    // then h_bound holds an upper bound of every tree's size.
+    bool host_layout = true;
+    std::vector<uint64_t> h_bound;
+    uint32_t *d_stat = nullptr;              // [0..2] device-planned evaluation: items, ropes,
+                                             // slots; [3] error of a device-side layout
+    bool stat_pending = false;
     // device
     DevBufs mem;
     uint8_t *d_arena = nullptr;
@@ -271,7 +279,7 @@ gp_status alloc_population(gp_population *P, cudaStream_t s)
         return o;
     };
     const uint64_t o_pos = take(2 * sizeof(uint64_t) * n1);        // starts, then sizes
-    const uint64_t o_err = take(sizeof(uint32_t) * (4 + n1));       // error words, then redo list
+    const uint64_t o_err = take(sizeof(uint32_t) * (8 + n1));       // error words, counts, redo list
     const uint64_t o_tab = take(sizeof(float) * (4 * P->lanes + P->n_consts + 1));   // x, y, constants
     const uint64_t o_fit = take(sizeof(float) * n1);
     const uint64_t o_hits = take(sizeof(uint32_t) * n1);
@@ -281,26 +289,48 @@ gp_status alloc_population(gp_population *P, cudaStream_t s)
     P->d_start = reinterpret_cast<uint64_t *>(blk + o_pos);
     P->d_size = P->d_start + n1;
     P->d_err = reinterpret_cast<uint32_t *>(blk + o_err);
-    P->d_redo = P->d_err + 4;
+    P->d_stat = P->d_err + 4;                // [0..2] planned counts, [3] layout error
+    P->d_redo = P->d_err + 8;
     P->d_x = reinterpret_cast<float *>(blk + o_tab);
     P->d_y = P->d_x + 2 * P->lanes;
     P->d_c = P->d_y + 2 * P->lanes;
     P->d_fitness = reinterpret_cast<float *>(blk + o_fit);
     P->d_hits = reinterpret_cast<uint32_t *>(blk + o_hits);
     P->d_values = reinterpret_cast<float *>(blk + o_vals);
-    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 5, s));    // error words and redo count
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 9, s));    // error words, counts, redo count
     std::vector<float> tab(4 * P->lanes + P->n_consts);
     std::copy(P->hx.begin(), P->hx.begin() + 2 * P->lanes, tab.begin());
     std::copy(P->hy.begin(), P->hy.begin() + 2 * P->lanes, tab.begin() + 2 * P->lanes);
     std::copy(P->hc.begin(), P->hc.begin() + P->n_consts, tab.begin() + 4 * P->lanes);
     CK(h2d(P->d_x, tab.data(), sizeof(float) * tab.size(), s));
-    if (P->n_trees) {
+    if (P->n_trees && P->host_layout) {
         std::vector<uint64_t> pos(2 * n1, 0);
         std::copy(P->h_start.begin(), P->h_start.end(), pos.begin());
         std::copy(P->h_size.begin(), P->h_size.end(), pos.begin() + n1);
         CK(h2d(P->d_start, pos.data(), sizeof(uint64_t) * pos.size(), s));
     }
     CK(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
+    return GP_OK;
+}
+
+// Brings a device-only layout (children made without a synchronisation) to
+// the host: waits for the population's stream, reads starts and sizes.
+gp_status ensure_host_layout(gp_population *P)
+{
+    if (P->host_layout) return GP_OK;
+    const uint64_t n1 = (uint64_t)P->n_trees + 1;
+    std::vector<uint64_t> pos(2 * n1);
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaMemcpy(pos.data(), P->d_start, sizeof(uint64_t) * 2 * n1, cudaMemcpyDeviceToHost));
+    uint32_t lerr = 0;
+    CK(cudaMemcpy(&lerr, P->d_stat + 3, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (lerr) return GP_EMALFORMED;
+    P->h_start.assign(pos.begin(), pos.begin() + P->n_trees);
+    P->h_size.assign(pos.begin() + n1, pos.begin() + n1 + P->n_trees);
+    P->total_nodes = 0;
+    for (uint64_t z : P->h_size) P->total_nodes += z;
+    P->host_layout = true;
+    P->h_bound.clear();
     return GP_OK;
 }
 
@@ -520,25 +550,37 @@ gp_status gp_create_population(const gp_problem *problem, uint32_t n_trees, cons
     return GP_OK;
 }
 
-gp_status gp_tree_size(const gp_population *P, uint32_t tree, uint64_t *n)
+gp_status gp_tree_size(const gp_population *Pc, uint32_t tree, uint64_t *n)
 {
+    gp_population *P = const_cast<gp_population *>(Pc);
     if (!P || !n || tree >= P->n_trees) return GP_EINVAL;
+    DeviceGuard dg(P->device);
+    gp_status st = ensure_host_layout(P);
+    if (st) return st;
     *n = P->h_size[tree];
     return GP_OK;
 }
 
-gp_status gp_tree_read(const gp_population *P, uint32_t tree, uint8_t *dst, uint64_t cap)
+gp_status gp_tree_read(const gp_population *Pc, uint32_t tree, uint8_t *dst, uint64_t cap)
 {
-    if (!P || !dst || tree >= P->n_trees || cap < P->h_size[tree]) return GP_EINVAL;
+    gp_population *P = const_cast<gp_population *>(Pc);
+    if (!P || !dst || tree >= P->n_trees) return GP_EINVAL;
     DeviceGuard dg(P->device);
+    gp_status st = ensure_host_layout(P);
+    if (st) return st;
+    if (cap < P->h_size[tree]) return GP_EINVAL;
     CK(cudaStreamSynchronize(P->stream));
     CK(cudaMemcpy(dst, P->d_arena + P->h_start[tree], P->h_size[tree], cudaMemcpyDeviceToHost));
     return GP_OK;
 }
 
-gp_status gp_population_get_info(const gp_population *P, gp_population_info *info)
+gp_status gp_population_get_info(const gp_population *Pc, gp_population_info *info)
 {
+    gp_population *P = const_cast<gp_population *>(Pc);
     if (!P || !info) return GP_EINVAL;
+    DeviceGuard dg(P->device);
+    gp_status st = ensure_host_layout(P);
+    if (st) return st;
     info->n_trees = P->n_trees;
     info->n_cases = P->n_cases;
     info->total_nodes = P->total_nodes;
@@ -880,6 +922,107 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
     return st;
 }
 
+// Evaluation of a population whose sizes are on the device only and whose
+// bounds keep every tree within kFuseMaxChunks chunks: the level-0 items
+// and the ropes are built on the device (plan0), so nothing returns to the
+// host between the crossover that made the trees and their evaluation.
+// Scratch is sized from the bounds.
+gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t s)
+{
+    const uint32_t C = cfg.C;
+    const int lanes = cfg.lanes, sms = cfg.sms;
+    CK(prepare_eval_once(lanes, false, cfg.smem));
+    CK(prepare_eval_once(lanes, true, cfg.smem_u));
+    uint64_t max_items = 0, max_slots = 0, max_ropes = 0;
+    for (uint64_t b : P->h_bound) {
+        const uint64_t m = (b + C - 1) / C;
+        max_items += m;
+        if (b > C) {
+            max_slots += m;
+            ++max_ropes;
+        }
+    }
+    if (max_items > 0x7fffffffull) return GP_ENOMEM;
+    const uint32_t pt_cap = fuse_pt_cap(C);
+    const uint64_t warps_total = (uint64_t)sms * cfg.W, spill_per_warp = C;
+    DevBufs ws;
+    auto body = [&]() -> gp_status {
+        // counters and counts, overflow flags (zeroed together), slot
+        // lengths, slot codes, slot values, items, ropes, spill
+        uint64_t off = 0;
+        auto take = [&](uint64_t bytes) {
+            const uint64_t o = off;
+            off = round_up(off + bytes, 256);
+            return o;
+        };
+        const uint64_t o_cnt = take(256 + 16 + 4ull * P->n_trees);
+        const uint64_t o_len = take(4ull * max_slots);
+        const uint64_t o_codes = take(4ull * (max_slots * C + 32));
+        const uint64_t o_pt = take(8ull * (max_slots * pt_cap * lanes + 1));
+        const uint64_t o_items = take(sizeof(EvalItem) * max_items);
+        const uint64_t o_ropes = take(sizeof(EvalItem) * (max_ropes + 1));
+        const uint64_t o_spill = take(8ull * lanes * warps_total * spill_per_warp);
+        uint8_t *blk;
+        CK(ws.alloc((void **)&blk, off, s));
+        CK(cudaMemsetAsync(blk + o_cnt, 0, 256 + 16 + 4ull * P->n_trees, s));
+        uint32_t *d_counter = reinterpret_cast<uint32_t *>(blk + o_cnt);
+        uint32_t *d_counts = d_counter + 64;
+        EvalItem *items = reinterpret_cast<EvalItem *>(blk + o_items);
+        EvalItem *ropes = reinterpret_cast<EvalItem *>(blk + o_ropes);
+        CK(launch_plan_level0(P->d_start, P->d_size, P->n_trees, C, items, ropes, d_counts, s));
+        note_launches(1);
+        EvalParams p{};
+        p.codes = P->d_arena;
+        p.items = items;
+        p.n_items = (uint32_t)max_items;
+        p.n_items_dev = d_counts;
+        p.counter = d_counter;
+        p.x = P->d_x;
+        p.y = P->d_y;
+        p.consts = P->d_c;
+        p.n_cases = P->n_cases;
+        p.n_consts = P->n_consts;
+        p.leaf_rows = (uint32_t)cfg.rows;
+        p.div0 = P->div0;
+        p.window = cfg.K;
+        p.values = P->d_values;
+        p.fitness = P->d_fitness;
+        p.hits = P->d_hits;
+        p.spill = reinterpret_cast<float2 *>(blk + o_spill);
+        p.spill_per_warp = spill_per_warp;
+        p.err = P->d_err;
+        if (max_slots) {
+            p.fz_codes = reinterpret_cast<uint32_t *>(blk + o_codes);
+            p.fz_pt = reinterpret_cast<float2 *>(blk + o_pt);
+            p.fz_len = reinterpret_cast<uint32_t *>(blk + o_len);
+            p.fz_over = d_counts + 4;
+            p.fz_redo = P->d_redo;
+            p.fz_cap_codes = C;
+            p.fz_cap_pt = pt_cap;
+        }
+        {
+            ProfScope ps(GP_KERNEL_EVAL, s);
+            CK(launch_eval(lanes, false, p, sms, (int)cfg.W, cfg.smem, s));
+        }
+        if (max_ropes) {
+            p.items = ropes;
+            p.n_items = (uint32_t)max_ropes;
+            p.n_items_dev = d_counts + 1;
+            p.counter = d_counter + 1;
+            p.window = cfg.Ku;
+            ProfScope ps(GP_KERNEL_EVAL_UPPER, s);
+            CK(launch_eval(lanes, true, p, sms, (int)cfg.Wu, cfg.smem_u, s));
+            P->redo_pending = true;
+        }
+        CK(cudaMemcpyAsync(P->d_stat, d_counts, sizeof(uint32_t) * 3, cudaMemcpyDeviceToDevice, s));
+        P->stat_pending = true;
+        return GP_OK;
+    };
+    gp_status st = body();
+    ws.release(s);
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -891,6 +1034,7 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
     cudaStream_t s = Stream(cuda_stream).s;
     P->stream = s;
     P->stats = gp_eval_stats{};
+    P->stat_pending = false;
     P->redo_pending = false;
     if (P->n_trees == 0) {
         CK(cudaEventRecord(P->ev, s));
@@ -903,6 +1047,18 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
     P->cfg = cfg;
     CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
     CK(cudaMemsetAsync(P->d_redo, 0, sizeof(uint32_t), s));
+    if (!P->host_layout) {
+        uint64_t bmax = 0;
+        for (uint64_t b : P->h_bound) bmax = std::max(bmax, b);
+        if (bmax <= (uint64_t)kFuseMaxChunks * cfg.C) {
+            st = eval_device_planned(P, cfg, s);
+            if (st) return st;
+            CK(cudaEventRecord(P->ev, s));
+            P->evaluated = true;
+            return GP_OK;
+        }
+        if ((st = ensure_host_layout(P))) return st;
+    }
     std::vector<uint32_t> all(P->n_trees);
     for (uint32_t t = 0; t < P->n_trees; ++t) all[t] = t;
     st = eval_trees(P, all, cfg, true, s);
@@ -929,14 +1085,18 @@ gp_status gp_fitness(const gp_population *Pc, float *fitness, float *case_values
             std::vector<uint32_t> redo(n);
             CK(cudaMemcpy(redo.data(), P->d_redo + 1, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
             std::sort(redo.begin(), redo.end());
-            gp_status st = eval_trees(P, redo, P->cfg, false, P->stream);
+            gp_status st = ensure_host_layout(P);
+            if (st) return st;
+            st = eval_trees(P, redo, P->cfg, false, P->stream);
             if (st) return st;
             CK(cudaStreamSynchronize(P->stream));
             P->stats.redone = n;
         }
     }
-    uint32_t err = 0;
-    CK(cudaMemcpy(&err, P->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    uint32_t ew[8] = {};
+    CK(cudaMemcpy(ew, P->d_err, sizeof(ew), cudaMemcpyDeviceToHost));
+    const uint32_t err = ew[0];
+    if (ew[7]) return GP_EMALFORMED;             // a child's subtree extent ran off its parent
     if (err & kErrMalformed) return GP_EMALFORMED;
     if (err) return GP_ECUDA;
     if (P->n_trees == 0) return GP_OK;
@@ -948,9 +1108,19 @@ gp_status gp_fitness(const gp_population *Pc, float *fitness, float *case_values
     return GP_OK;
 }
 
-gp_status gp_eval_stats_get(const gp_population *P, gp_eval_stats *out)
+gp_status gp_eval_stats_get(const gp_population *Pc, gp_eval_stats *out)
 {
+    gp_population *P = const_cast<gp_population *>(Pc);
     if (!P || !out) return GP_EINVAL;
+    if (P->stat_pending) {                   // a device-planned evaluation: read its counts
+        DeviceGuard dg(P->device);
+        uint32_t c[4] = {};
+        CK(cudaStreamSynchronize(P->stream));
+        CK(cudaMemcpy(c, P->d_stat, sizeof(c), cudaMemcpyDeviceToHost));
+        P->stats.items = (uint64_t)c[0] + c[1];
+        P->stats.levels = c[1] ? 2u : 1u;
+        P->stat_pending = false;
+    }
     *out = P->stats;
     return GP_OK;
 }
@@ -961,6 +1131,11 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
                        gp_population **children_out)
 {
     if (!M || !children_out || (n_ops && !ops)) return GP_EINVAL;
+    {
+        DeviceGuard dg(M->device);
+        gp_status st = ensure_host_layout(const_cast<gp_population *>(M));   // parents made without a sync
+        if (st) return st;
+    }
     for (uint32_t k = 0; k < n_ops; ++k) {
         const gp_xo &o = ops[k];
         if (o.mum >= M->n_trees || o.dad >= M->n_trees) return GP_EINVAL;
@@ -973,10 +1148,70 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
     copy_problem_from(C, M);
     C->device = M->device;
     C->n_trees = n_ops;
-    C->h_size.resize(n_ops);
     DevBufs tmp;
     std::vector<uint64_t> ends(2 * (size_t)n_ops);
+    // Without a synchronisation when it is safe: every child is at most
+    // n_m + n_d - j - 1 nodes (mum minus at least the node at i, plus dad's
+    // nodes from j on), so an arena sized from those bounds holds the
+    // children laid out on the device, and no child can exceed the node
+    // limit when no bound does.  Otherwise the sizes are read back first.
+    std::vector<uint64_t> bound;
+    uint64_t bound_arena = 64, bound_max = 0;
+    bool async = n_ops > 0;
+    if (async) {
+        bound.resize(n_ops);
+        for (uint32_t k = 0; k < n_ops; ++k) {
+            bound[k] = M->h_size[ops[k].mum] + M->h_size[ops[k].dad] - ops[k].dad_point - 1;
+            bound_max = std::max(bound_max, bound[k]);
+            bound_arena += round_up(bound[k], 16);
+        }
+        const uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(4 * M->arena_bytes, 256ull << 20), 16ull << 30);
+        if ((C->max_tree_nodes && bound_max > C->max_tree_nodes) || bound_arena > cap ||
+            (C->hbm_budget && population_bytes(bound_arena, n_ops, C->n_cases) > C->hbm_budget))
+            async = false;
+    }
+    auto run_async = [&]() -> gp_status {
+        C->host_layout = false;
+        C->h_bound = std::move(bound);
+        C->arena_bytes = bound_arena;
+        gp_status r = alloc_population(C, s);
+        if (r) return r;
+        std::vector<ExtentQuery> q(2 * (size_t)n_ops);
+        for (uint32_t k = 0; k < n_ops; ++k) {
+            q[2 * k] = ExtentQuery{M->h_start[ops[k].mum], M->h_size[ops[k].mum], ops[k].mum_point};
+            q[2 * k + 1] = ExtentQuery{M->h_start[ops[k].dad], M->h_size[ops[k].dad], ops[k].dad_point};
+        }
+        // one block: tile count, ends, queries, copy records, first tiles
+        const uint64_t o_end = 256, o_q = round_up(o_end + sizeof(uint64_t) * q.size(), 256);
+        const uint64_t o_kids = round_up(o_q + sizeof(ExtentQuery) * q.size(), 256);
+        const uint64_t o_tb = round_up(o_kids + sizeof(XoChild) * n_ops, 256);
+        uint8_t *blk;
+        CK(tmp.alloc((void **)&blk, o_tb + sizeof(uint32_t) * (n_ops + 1), s));
+        uint32_t *d_ntiles = reinterpret_cast<uint32_t *>(blk);
+        uint64_t *d_end = reinterpret_cast<uint64_t *>(blk + o_end);
+        ExtentQuery *d_q = reinterpret_cast<ExtentQuery *>(blk + o_q);
+        XoChild *d_kids = reinterpret_cast<XoChild *>(blk + o_kids);
+        uint32_t *d_tb = reinterpret_cast<uint32_t *>(blk + o_tb);
+        uint32_t *d_lerr = C->d_stat + 3;
+        CK(h2d(d_q, q.data(), sizeof(ExtentQuery) * q.size(), s));
+        {
+            ProfScope ps(GP_KERNEL_EXTENT, s);
+            CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_lerr, s));
+        }
+        const uint32_t tile = 16384;
+        CK(launch_xo_layout(d_q, d_end, n_ops, tile, C->arena_bytes, d_kids, C->d_start, C->d_size, d_tb,
+                            d_ntiles, d_lerr, s));
+        {
+            ProfScope ps(GP_KERNEL_COPY, s);
+            CK(launch_xo_copy_dev(M->d_arena, C->d_arena, d_kids, d_tb, n_ops, d_ntiles, tile,
+                                  sm_count(C->device), s));
+        }
+        note_launches(1);                      // the layout kernel (the others are counted by scope)
+        return GP_OK;
+    };
     auto run = [&]() -> gp_status {
+        if (async) return run_async();
+        C->h_size.resize(n_ops);
         if (n_ops) {
             std::vector<ExtentQuery> q(2 * (size_t)n_ops);
             for (uint32_t k = 0; k < n_ops; ++k) {

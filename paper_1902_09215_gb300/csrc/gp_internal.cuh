@@ -132,6 +132,16 @@ cudaError_t launch_plan_dev(bool wide, const void *codes, const EvalItem *items,
                             const uint32_t *n_dev, PlanOut *out, int sms, cudaStream_t s);
 cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uint32_t *n_dev,
                                  uint64_t *frag_off, uint64_t *totals, cudaStream_t s);
+// Level-0 items of trees whose sizes are on the device, all at most
+// kFuseMaxChunks chunks: counts[0] items (fused chunks, then finals),
+// counts[1] ropes (next launch), counts[2] slots.
+cudaError_t launch_plan_level0(const uint64_t *start, const uint64_t *size, uint32_t n, uint32_t C,
+                               EvalItem *items, EvalItem *ropes, uint32_t *counts, cudaStream_t s);
+// Children laid out on the device from their extents: copy records, starts,
+// sizes, per-child first copy tile ([n+1]) and the tile count.
+cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_t n, uint32_t tile_bytes,
+                             uint64_t arena_cap, XoChild *kids, uint64_t *cstart, uint64_t *csize,
+                             uint32_t *tile_base, uint32_t *n_tiles, uint32_t *err, cudaStream_t s);
 cudaError_t launch_validate(const uint8_t *codes, const EvalItem *chunks, uint32_t n_chunks,
                             uint32_t n_consts, ValOut *out, cudaStream_t s);
 cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,

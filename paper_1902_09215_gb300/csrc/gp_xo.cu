@@ -217,6 +217,128 @@ cudaError_t launch_xo_copy_runs(uint8_t *heap, const XoChild *kids, const uint32
     return cudaGetLastError();
 }
 
+// Exclusive scan of a (64-bit, 32-bit) pair over the CTA (a multiple of 32
+// threads, at most 1024), with the block totals.
+__device__ __forceinline__ void block_scan_pair(uint64_t a, uint32_t b, uint64_t &ea, uint32_t &eb,
+                                                uint64_t &ta, uint32_t &tb)
+{
+    __shared__ uint64_t wa[33];
+    __shared__ uint32_t wb[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t ia = a;
+    uint32_t ib = b;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint64_t oa = __shfl_up_sync(0xffffffffu, ia, off);
+        const uint32_t ob = __shfl_up_sync(0xffffffffu, ib, off);
+        if (lane >= off) {
+            ia += oa;
+            ib += ob;
+        }
+    }
+    if (lane == 31) {
+        wa[warp] = ia;
+        wb[warp] = ib;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {              // at most 32 warp totals: a serial pass
+        uint64_t sa = 0;
+        uint32_t sb = 0;
+        for (int w = 0; w < nw; ++w) {
+            const uint64_t x = wa[w];
+            const uint32_t y = wb[w];
+            wa[w] = sa;
+            wb[w] = sb;
+            sa += x;
+            sb += y;
+        }
+        wa[32] = sa;
+        wb[32] = sb;
+    }
+    __syncthreads();
+    ea = wa[warp] + (ia - a);
+    eb = wb[warp] + (ib - b);
+    ta = wa[32];
+    tb = wb[32];
+    __syncthreads();                     // the arrays are reused by the next call
+}
+
+// Children laid out on the device (one CTA): size i + (e_d - j) + (n_m - e_m)
+// from the two extents, 16-byte aligned starts by an exclusive scan, the
+// copy record and the first copy tile of every child.  A child that would
+// end past the arena's capacity (not possible when the capacity was sized
+// from the bound n_m + n_d - j - 1) is not copied and sets kErrExtent.
+__global__ void __launch_bounds__(1024) xo_layout_kernel(const ExtentQuery *__restrict__ q,
+                                                         const uint64_t *__restrict__ ends, uint32_t n,
+                                                         uint32_t tile_bytes, uint64_t arena_cap,
+                                                         XoChild *__restrict__ kids, uint64_t *__restrict__ cstart,
+                                                         uint64_t *__restrict__ csize, uint32_t *__restrict__ tile_base,
+                                                         uint32_t *n_tiles, uint32_t *err)
+{
+    __shared__ uint64_t carry_pos;
+    __shared__ uint32_t carry_t;
+    if (threadIdx.x == 0) {
+        carry_pos = 0;
+        carry_t = 0;
+    }
+    __syncthreads();
+    for (uint32_t base = 0; base < n; base += blockDim.x) {
+        const uint32_t k = base + threadIdx.x;
+        uint64_t size = 0;
+        ExtentQuery qm{}, qd{};
+        uint64_t em = 0, ed = 0;
+        if (k < n) {
+            qm = q[2 * k];
+            qd = q[2 * k + 1];
+            em = ends[2 * k];
+            ed = ends[2 * k + 1];
+            size = qm.point + (ed - qd.point) + (qm.tree_size - em);
+        }
+        const uint64_t alen = (size + 15) & ~15ull;
+        const uint32_t tl = (uint32_t)((size + tile_bytes - 1) / tile_bytes);
+        uint64_t ea, ta;
+        uint32_t eb, tb;
+        block_scan_pair(alen, tl, ea, eb, ta, tb);
+        if (k < n) {
+            const uint64_t start = carry_pos + ea;
+            XoChild c{};
+            c.dst = start;
+            c.n = size;
+            c.head_src = qm.tree_start;
+            c.i = qm.point;
+            c.mid_src = qd.tree_start + qd.point;
+            c.ld = ed - qd.point;
+            c.tail_src = qm.tree_start + em;
+            if (start + alen + 64 > arena_cap) {
+                atomicOr(err, kErrExtent);
+                c.n = 0;
+            }
+            kids[k] = c;
+            cstart[k] = start;
+            csize[k] = size;
+            tile_base[k] = carry_t + eb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_pos += ta;
+            carry_t += tb;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        tile_base[n] = carry_t;
+        *n_tiles = carry_t;
+    }
+}
+
+cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_t n, uint32_t tile_bytes,
+                             uint64_t arena_cap, XoChild *kids, uint64_t *cstart, uint64_t *csize,
+                             uint32_t *tile_base, uint32_t *n_tiles, uint32_t *err, cudaStream_t s)
+{
+    xo_layout_kernel<<<1, 1024, 0, s>>>(q, ends, n, tile_bytes, arena_cap, kids, cstart, csize, tile_base,
+                                        n_tiles, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_xo_copy_dev(const uint8_t *src, uint8_t *dst, const XoChild *children,
                                const uint32_t *tile_base, uint32_t n_children,
                                const uint32_t *n_tiles_dev, uint32_t tile_bytes, int sms,

@@ -80,3 +80,50 @@ def test_bad_points_rejected(gpu):
     assert e.value.status == gpu.GP_EINVAL
     with pytest.raises(gpu.GpError):
         gpu.gp_crossover(pop, (np.array([0]), np.array([999]), np.array([0]), np.array([0])))
+
+
+def test_children_chain_sized_on_the_device(gpu, oracle):
+    """Children whose bounds allow it are laid out on the device without a
+    synchronisation; their sizes reach the host only when a call needs
+    them (parents of the next crossover, tree reads, info).  Three
+    generations, each evaluated with items built on the device, against the
+    oracle's chain."""
+    x, y, c = synth.problem()
+    nodes, offs = synth.population_loguniform(seed=12, count=700, hi=40001)
+    pop = make_pop(gpu, nodes, offs)
+    rn, ro = nodes, offs
+    for g in range(3):
+        ops = synth.crossover_points(30 + g, np.diff(ro.astype(np.int64)), 700)
+        kids = gpu.gp_crossover(pop, ops)
+        gpu.gp_evaluate(kids)
+        fit, vals, hits = gpu.gp_fitness(kids, case_values=True, hits=True)
+        rn, ro = oracle.crossover_population(rn, ro, *ops)
+        ref = oracle.eval_population(rn, ro, x, y, c, n_threads=8)
+        assert same_f32(vals, ref["out"]) and same_f32(fit, ref["fitness"]), g
+        assert np.array_equal(hits, ref["hits"])
+        st = gpu.gp_eval_stats_get(kids)
+        assert st["levels"] == 2 and st["items"] > 700          # chunks of the multi-chunk trees + ropes
+        info = gpu.gp_population_get_info(kids)
+        assert info.total_nodes == int(ro[-1])
+        t = int(np.argmax(np.diff(ro.astype(np.int64))))
+        assert gpu.gp_tree_size(kids, t) == int(ro[t + 1] - ro[t])
+        pop = kids
+
+
+@pytest.mark.parametrize("chunk", [256, 1024])
+def test_children_device_planning_and_host_fallback(gpu, oracle, chunk):
+    """The same children evaluated with chunk sizes for which every bound is
+    within 32 chunks (items built on the device) or not (sizes read back,
+    planned upper levels): identical results either way."""
+    x, y, c = synth.problem()
+    nodes, offs = synth.population_loguniform(seed=13, count=300, hi=9001)
+    pop = make_pop(gpu, nodes, offs)
+    ops = synth.crossover_points(5, np.diff(offs.astype(np.int64)), 300)
+    rn, ro = oracle.crossover_population(nodes, offs, *ops)
+    ref = oracle.eval_population(rn, ro, x, y, c, n_threads=8)
+    kids = gpu.gp_crossover(pop, ops)
+    gpu.gp_evaluate(kids, chunk_nodes=chunk)
+    fit, vals, _ = gpu.gp_fitness(kids, case_values=True)
+    assert same_f32(vals, ref["out"]) and same_f32(fit, ref["fitness"])
+    kn, ko = gpu.read_all_trees(kids)
+    assert np.array_equal(kn, rn) and np.array_equal(ko, ro)
