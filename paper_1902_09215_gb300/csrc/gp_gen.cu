@@ -18,6 +18,8 @@ struct gp_generation {
     Engine eng;
     uint32_t run = 0, n = 0;
     bool use_graph = false;
+    bool auto_levels = false;         // level budget follows the levels generations use
+    uint32_t levels_cap = 8;
     cudaStream_t last = nullptr;      // stream of the last enqueue (the legacy stream is null)
     gp_generation_info info{};
 };
@@ -46,6 +48,20 @@ void order_after_last(gp_generation *G, cudaStream_t s)
     }
 }
 
+// Level budget of a run whose trees grow: a generation that used every
+// level (its last level made all open upper trees final items, however
+// large) widens the budget by two for the next generations, up to the cap.
+gp_status widen_levels(gp_generation *G, uint32_t used)
+{
+    Engine &E = G->eng;
+    if (!G->auto_levels || used < E.levels_max || E.levels_max >= G->levels_cap) return GP_OK;
+    E.levels_max = std::min<uint32_t>(G->levels_cap, E.levels_max + 2);
+    if (!G->use_graph) return GP_OK;
+    gp_status st = E.capture(kModeGenerate);
+    if (!st) G->info.kernels_per_generation = E.kernels_per_batch[kModeGenerate];
+    return st;
+}
+
 // Synchronise and read the run's state; the run's error (if any) as a status.
 gp_status sync_run(gp_generation *G, RunDev *R)
 {
@@ -56,6 +72,7 @@ gp_status sync_run(gp_generation *G, RunDev *R)
     G->info.generation = R->gen;
     G->info.levels = R->levels;
     G->info.error_generation = R->err ? R->err_gen : 0;
+    if (!R->err && (st = widen_levels(G, R->levels))) return st;
     return map_err(R->err, c.eval_err[0]);
 }
 
@@ -200,6 +217,11 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
         if (R.err) return fail(map_err(R.err, 0));
         G->info.levels = R.levels;
     }
+    // Level budget: generation 0's levels and two more (the last level of a
+    // generation finishes every open tree, so any budget is correct; a
+    // generation that uses them all widens it).  A given max_levels is fixed.
+    G->auto_levels = params->max_levels == 0;
+    if (G->auto_levels) E.levels_max = std::min<uint32_t>(G->levels_cap, std::max<uint32_t>(3, G->info.levels + 2));
     step = "graph capture";
     if (G->use_graph && (st = E.capture(kModeGenerate))) return fail(st);
     G->info.n_trees = n_trees;

@@ -95,6 +95,31 @@ def test_many_levels_large_trees(gpu, oracle):
         nodes, offs, ref = kids, koffs, ref_next
 
 
+def test_level_budget_follows_growth(gpu, oracle):
+    """Generation 0 fits one chunk per tree (one level), so the level budget
+    starts at three; children of a few hundred nodes with 256-node chunks
+    reach the last level, which makes every open upper tree a final item
+    (still exact) and widens the budget for the next generations."""
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=17, count=120, lo=101, hi=255)
+    seed = 5
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=256, use_graph=True)
+    k0 = gpu.gp_generation_get_info(G)["kernels_per_generation"]
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+    widened = False
+    for g in range(8):
+        recs, kids, koffs, ref_next = oracle_step(oracle, nodes, offs, ref["fitness"], seed, g, (x, y, c))
+        gpu.gp_generation_step(G)
+        gn, go = gpu.gp_generation_trees(G)
+        assert np.array_equal(go, koffs) and np.array_equal(gn, kids), g
+        assert_same_eval(gpu, G, ref_next)
+        widened = widened or gpu.gp_generation_get_info(G)["kernels_per_generation"] > k0
+        nodes, offs, ref = kids, koffs, ref_next
+    if int(np.diff(offs.astype(np.int64)).max()) > 256 * 27:
+        assert widened
+
+
 def test_rewind_repeats_the_step(gpu):
     x, y, c = synth.problem()
     prob = gpu.Problem(x, y, c)
