@@ -126,9 +126,15 @@ class ClockSampler:
 
 
 def kernel_source_sha():
+    """Hash of what the evaluator kernels compile from: gp_eval.cu and the
+    types and constants of gp_internal.cuh (launcher declarations after them
+    do not change the kernels)."""
+    csrc = os.path.join(ROOT, "paper_1902_09215_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("gp_eval.cu", "gp_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1902_09215_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(csrc, "gp_eval.cu"), "rb").read())
+    hdr = open(os.path.join(csrc, "gp_internal.cuh"), "rb").read()
+    cut = hdr.find(b"// Launchers")
+    h.update(hdr if cut < 0 else hdr[:cut])
     return h.hexdigest()[:16]
 
 
@@ -139,16 +145,20 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the evaluator from the committed ncu summary,
-    only if it was taken on the current kernel source."""
+def recorded_counters():
+    """The level-0 evaluator's ncu record (DRAM bytes and warp instructions
+    per launch), only if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "eval_kernel_traffic.json")
     if not os.path.exists(p):
-        return None
+        return {}
     d = json.load(open(p))
     if d.get("kernel_source_sha") != kernel_source_sha():
-        return None
-    return d.get("dram_bytes_per_launch")
+        return {}
+    return d
+
+
+def recorded_traffic():
+    return recorded_counters().get("dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------
@@ -268,6 +278,16 @@ def run_ours(args):
     alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12           # FP32 lanes x clock, Tops/s
     achieved = n_bin_ops / (eval_launch_ms / 1e3) / 1e12
     traffic = recorded_traffic()
+    # the interpreter's own bound: warp instructions issued (ncu count of the
+    # same launch) against 4 schedulers x SMs x clock
+    inst = recorded_counters().get("warp_instructions")
+    issue = None
+    if inst:
+        ipeak = 4.0 * n_sm * sm_mhz * 1e6
+        issue = {"warp_instructions_per_launch": inst, "achieved_per_s": inst / (eval_launch_ms / 1e3),
+                 "peak_per_s": ipeak, "frac": inst / (eval_launch_ms / 1e3) / ipeak,
+                 "note": "4 warp schedulers x SMs x max clock; the bound the interpreter meets"}
+    tot_ms = sum(v["ms"] for v in prof.values() if v["launches"])
 
     # ---- end to end through the public API from pinned host memory
     pin_nodes = torch.from_numpy(nodes).pin_memory()
@@ -338,8 +358,9 @@ def run_ours(args):
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "peak_note": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_src} max clock); "
                                   "achieved = (n-1)/2 binary ops x 48 cases per tree / mean launch time",
-                     "launch_ms": eval_launch_ms, "launches_profiled": ev0["launches"],
-                     "kernel_share": {k: v["ms"] for k, v in prof.items() if v["launches"]}},
+                     "launch_ms": eval_launch_ms, "launches_profiled": ev0["launches"], "issue": issue,
+                     "kernel_ms_per_launch": {k: v["ms"] / v["launches"] for k, v in prof.items() if v["launches"]},
+                     "kernel_share": {k: v["ms"] / tot_ms for k, v in prof.items() if v["launches"]}},
         "wall_s": wall,
     }
     if cpu:

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgp.so")
-SOURCES = ["gp_eval.cu", "gp_xo.cu", "gp_api.cu", "gp_noalloc.cu", "gp_engine.cu", "gp_gen.cu", "gp_server.cu"]
+SOURCES = ["gp_eval.cu", "gp_plan0.cu", "gp_xo.cu", "gp_api.cu", "gp_noalloc.cu", "gp_engine.cu", "gp_gen.cu",
+           "gp_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-fmad=false", "-prec-div=true",
                      "-prec-sqrt=true", "-ftz=false", "-Xcompiler", "-fPIC",

@@ -955,6 +955,7 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
             off = round_up(off + bytes, 256);
             return o;
         };
+        const uint64_t o_cls = take(4ull * plan_level0_scratch_words());
         const uint64_t o_cnt = take(256 + 16 + 4ull * P->n_trees);
         const uint64_t o_len = take(4ull * max_slots);
         const uint64_t o_codes = take(4ull * (max_slots * C + 32));
@@ -964,13 +965,14 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
         const uint64_t o_spill = take(8ull * lanes * warps_total * spill_per_warp);
         uint8_t *blk;
         CK(ws.alloc((void **)&blk, off, s));
-        CK(cudaMemsetAsync(blk + o_cnt, 0, 256 + 16 + 4ull * P->n_trees, s));
+        CK(cudaMemsetAsync(blk, 0, o_cnt + 256 + 16 + 4ull * P->n_trees, s));   // cursors, counters, flags
         uint32_t *d_counter = reinterpret_cast<uint32_t *>(blk + o_cnt);
         uint32_t *d_counts = d_counter + 64;
         EvalItem *items = reinterpret_cast<EvalItem *>(blk + o_items);
         EvalItem *ropes = reinterpret_cast<EvalItem *>(blk + o_ropes);
-        CK(launch_plan_level0(P->d_start, P->d_size, P->n_trees, C, items, ropes, d_counts, s));
-        note_launches(1);
+        CK(launch_plan_level0(P->d_start, P->d_size, P->n_trees, C, items, ropes, d_counts,
+                              reinterpret_cast<uint32_t *>(blk + o_cls), sms, s));
+        note_launches(3);
         EvalParams p{};
         p.codes = P->d_arena;
         p.items = items;
@@ -1185,8 +1187,11 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
         const uint64_t o_end = 256, o_q = round_up(o_end + sizeof(uint64_t) * q.size(), 256);
         const uint64_t o_kids = round_up(o_q + sizeof(ExtentQuery) * q.size(), 256);
         const uint64_t o_tb = round_up(o_kids + sizeof(XoChild) * n_ops, 256);
+        const uint32_t parts = xo_layout_parts(n_ops);
+        const uint64_t o_pl = round_up(o_tb + sizeof(uint32_t) * (n_ops + 1), 256);
+        const uint64_t o_pt = round_up(o_pl + sizeof(uint64_t) * parts, 256);
         uint8_t *blk;
-        CK(tmp.alloc((void **)&blk, o_tb + sizeof(uint32_t) * (n_ops + 1), s));
+        CK(tmp.alloc((void **)&blk, o_pt + sizeof(uint32_t) * parts, s));
         uint32_t *d_ntiles = reinterpret_cast<uint32_t *>(blk);
         uint64_t *d_end = reinterpret_cast<uint64_t *>(blk + o_end);
         ExtentQuery *d_q = reinterpret_cast<ExtentQuery *>(blk + o_q);
@@ -1200,13 +1205,14 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
         }
         const uint32_t tile = 16384;
         CK(launch_xo_layout(d_q, d_end, n_ops, tile, C->arena_bytes, d_kids, C->d_start, C->d_size, d_tb,
-                            d_ntiles, d_lerr, s));
+                            d_ntiles, reinterpret_cast<uint64_t *>(blk + o_pl),
+                            reinterpret_cast<uint32_t *>(blk + o_pt), d_lerr, s));
         {
             ProfScope ps(GP_KERNEL_COPY, s);
             CK(launch_xo_copy_dev(M->d_arena, C->d_arena, d_kids, d_tb, n_ops, d_ntiles, tile,
                                   sm_count(C->device), s));
         }
-        note_launches(1);                      // the layout kernel (the others are counted by scope)
+        note_launches(3);                      // the layout kernels (the others are counted by scope)
         return GP_OK;
     };
     auto run = [&]() -> gp_status {

@@ -990,105 +990,6 @@ __global__ void validate_trees_kernel(const ValOut *__restrict__ v, const uint32
     if (bad || acc.need > 0 || acc.delta != 1) atomicAdd(bad_count, 1u);
 }
 
-// ---------------------------------------------------------------- device-planned level 0
-
-// Level-0 items of a population whose tree sizes are on the device only and
-// at most max_chunks chunks of C codes (one CTA): the chunks of every
-// multi-chunk tree (fused items, the tree's slots consecutive), then every
-// single-chunk tree as a final item, each group larger trees first by size
-// class (floor of log2); one rope item per multi-chunk tree, larger classes
-// first, for the next launch.  counts: [0] level-0 items, [1] ropes,
-// [2] slots.  Items of one class are in no particular order (the results do
-// not depend on the order).
-__global__ void plan0_kernel(const uint64_t *__restrict__ start, const uint64_t *__restrict__ size, uint32_t n,
-                             uint32_t C, EvalItem *__restrict__ items, EvalItem *__restrict__ ropes,
-                             uint32_t *counts)
-{
-    constexpr int kCls = 64;
-    __shared__ uint32_t c_chunk[kCls], c_small[kCls], c_rope[kCls];
-    __shared__ uint32_t s_slots;
-    for (int i = threadIdx.x; i < kCls; i += blockDim.x) c_chunk[i] = c_small[i] = c_rope[i] = 0;
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-        const uint64_t z = size[t];
-        const int cls = 63 - __clzll((long long)(z | 1));
-        if (z > C) {
-            atomicAdd(&c_chunk[cls], (uint32_t)((z + C - 1) / C));
-            atomicAdd(&c_rope[cls], 1u);
-        } else {
-            atomicAdd(&c_small[cls], 1u);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {              // class bases, larger classes first
-        uint32_t pos = 0, r = 0;
-        for (int c = kCls - 1; c >= 0; --c) {
-            const uint32_t x = c_chunk[c];
-            c_chunk[c] = pos;
-            pos += x;
-        }
-        for (int c = kCls - 1; c >= 0; --c) {
-            const uint32_t x = c_small[c];
-            c_small[c] = pos;
-            pos += x;
-        }
-        for (int c = kCls - 1; c >= 0; --c) {
-            const uint32_t x = c_rope[c];
-            c_rope[c] = r;
-            r += x;
-        }
-        counts[0] = pos;
-        counts[1] = r;
-        s_slots = 0;
-    }
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-        const uint64_t z = size[t], b = start[t];
-        const int cls = 63 - __clzll((long long)(z | 1));
-        if (z > C) {
-            const uint32_t m = (uint32_t)((z + C - 1) / C);
-            const uint32_t p = atomicAdd(&c_chunk[cls], m);
-            const uint32_t slot = atomicAdd(&s_slots, m);
-            for (uint32_t j = 0; j < m; ++j) {
-                EvalItem it{};
-                it.begin = b + (uint64_t)j * C;
-                it.end = b + umin64(z, (uint64_t)(j + 1) * C);
-                it.tree = t;
-                it.flags = kItemFused;
-                it.frag_off = slot + j;
-                it.pt_base = slot;
-                it.frag_len = m;
-                it.spill_off = kNoSpill;
-                items[p + j] = it;
-            }
-            EvalItem r{};
-            r.tree = t;
-            r.flags = kItemFinal | kItemRope;
-            r.pt_base = slot;
-            r.frag_len = m;
-            r.spill_off = kNoSpill;
-            ropes[atomicAdd(&c_rope[cls], 1u)] = r;
-        } else {
-            EvalItem it{};
-            it.begin = b;
-            it.end = b + z;
-            it.tree = t;
-            it.flags = kItemFinal;
-            it.spill_off = kNoSpill;
-            items[atomicAdd(&c_small[cls], 1u)] = it;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) counts[2] = s_slots;
-}
-
-cudaError_t launch_plan_level0(const uint64_t *start, const uint64_t *size, uint32_t n, uint32_t C,
-                               EvalItem *items, EvalItem *ropes, uint32_t *counts, cudaStream_t s)
-{
-    plan0_kernel<<<1, 1024, 0, s>>>(start, size, n, C, items, ropes, counts);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,
                                   uint32_t n_trees, uint32_t *bad_count, cudaStream_t s)
 {

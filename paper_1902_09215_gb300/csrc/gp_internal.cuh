@@ -134,14 +134,20 @@ cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uin
                                  uint64_t *frag_off, uint64_t *totals, cudaStream_t s);
 // Level-0 items of trees whose sizes are on the device, all at most
 // kFuseMaxChunks chunks: counts[0] items (fused chunks, then finals),
-// counts[1] ropes (next launch), counts[2] slots.
+// counts[1] ropes (next launch), counts[2] slots.  Three launches; `cls`:
+// plan_level0_scratch_words() zeroed words.
+uint32_t plan_level0_scratch_words();
 cudaError_t launch_plan_level0(const uint64_t *start, const uint64_t *size, uint32_t n, uint32_t C,
-                               EvalItem *items, EvalItem *ropes, uint32_t *counts, cudaStream_t s);
+                               EvalItem *items, EvalItem *ropes, uint32_t *counts, uint32_t *cls, int sms,
+                               cudaStream_t s);
 // Children laid out on the device from their extents: copy records, starts,
-// sizes, per-child first copy tile ([n+1]) and the tile count.
+// sizes, per-child first copy tile ([n+1]) and the tile count (three
+// launches; part_len / part_tiles: scratch of xo_layout_parts(n) entries).
+uint32_t xo_layout_parts(uint32_t n);
 cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_t n, uint32_t tile_bytes,
                              uint64_t arena_cap, XoChild *kids, uint64_t *cstart, uint64_t *csize,
-                             uint32_t *tile_base, uint32_t *n_tiles, uint32_t *err, cudaStream_t s);
+                             uint32_t *tile_base, uint32_t *n_tiles, uint64_t *part_len, uint32_t *part_tiles,
+                             uint32_t *err, cudaStream_t s);
 cudaError_t launch_validate(const uint8_t *codes, const EvalItem *chunks, uint32_t n_chunks,
                             uint32_t n_consts, ValOut *out, cudaStream_t s);
 cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,

@@ -262,64 +262,67 @@ __device__ __forceinline__ void block_scan_pair(uint64_t a, uint32_t b, uint64_t
     __syncthreads();                     // the arrays are reused by the next call
 }
 
-// Children laid out on the device (one CTA): size i + (e_d - j) + (n_m - e_m)
-// from the two extents, 16-byte aligned starts by an exclusive scan, the
-// copy record and the first copy tile of every child.  A child that would
-// end past the arena's capacity (not possible when the capacity was sized
-// from the bound n_m + n_d - j - 1) is not copied and sets kErrExtent.
-__global__ void __launch_bounds__(1024) xo_layout_kernel(const ExtentQuery *__restrict__ q,
-                                                         const uint64_t *__restrict__ ends, uint32_t n,
-                                                         uint32_t tile_bytes, uint64_t arena_cap,
-                                                         XoChild *__restrict__ kids, uint64_t *__restrict__ cstart,
-                                                         uint64_t *__restrict__ csize, uint32_t *__restrict__ tile_base,
-                                                         uint32_t *n_tiles, uint32_t *err)
+// Children laid out on the device in three grid-wide steps: (1) every
+// child's size i + (e_d - j) + (n_m - e_m) from its two extents, and per CTA
+// the sums of the children's 16-byte aligned lengths and copy tiles; (2) one
+// CTA scans those sums; (3) every CTA scans its children again from its
+// offset: start, copy record, first copy tile.  A child that would end past
+// the arena's capacity (not possible when the capacity was sized from the
+// bound n_m + n_d - j - 1) is not copied and sets kErrExtent.
+constexpr int kLayoutT = 256;
+
+__device__ __forceinline__ uint64_t child_size(const ExtentQuery *__restrict__ q, const uint64_t *__restrict__ ends,
+                                               uint32_t k)
 {
-    __shared__ uint64_t carry_pos;
+    return q[2 * k].point + (ends[2 * k + 1] - q[2 * k + 1].point) + (q[2 * k].tree_size - ends[2 * k]);
+}
+
+__global__ void __launch_bounds__(kLayoutT) xo_size_kernel(const ExtentQuery *__restrict__ q,
+                                                           const uint64_t *__restrict__ ends, uint32_t n,
+                                                           uint32_t tile_bytes, uint64_t *__restrict__ csize,
+                                                           uint64_t *__restrict__ part_len, uint32_t *__restrict__ part_tiles)
+{
+    const uint32_t k = blockIdx.x * kLayoutT + threadIdx.x;
+    uint64_t z = 0;
+    if (k < n) {
+        z = child_size(q, ends, k);
+        csize[k] = z;
+    }
+    uint64_t ea, ta;
+    uint32_t eb, tb;
+    block_scan_pair((z + 15) & ~15ull, (uint32_t)((z + tile_bytes - 1) / tile_bytes), ea, eb, ta, tb);
+    if (threadIdx.x == 0) {
+        part_len[blockIdx.x] = ta;
+        part_tiles[blockIdx.x] = tb;
+    }
+}
+
+__global__ void __launch_bounds__(1024) xo_part_scan_kernel(uint64_t *__restrict__ part_len,
+                                                            uint32_t *__restrict__ part_tiles, uint32_t n_parts,
+                                                            uint32_t *__restrict__ tile_base, uint32_t n,
+                                                            uint32_t *n_tiles)
+{
+    __shared__ uint64_t carry_len;
     __shared__ uint32_t carry_t;
     if (threadIdx.x == 0) {
-        carry_pos = 0;
+        carry_len = 0;
         carry_t = 0;
     }
     __syncthreads();
-    for (uint32_t base = 0; base < n; base += blockDim.x) {
-        const uint32_t k = base + threadIdx.x;
-        uint64_t size = 0;
-        ExtentQuery qm{}, qd{};
-        uint64_t em = 0, ed = 0;
-        if (k < n) {
-            qm = q[2 * k];
-            qd = q[2 * k + 1];
-            em = ends[2 * k];
-            ed = ends[2 * k + 1];
-            size = qm.point + (ed - qd.point) + (qm.tree_size - em);
-        }
-        const uint64_t alen = (size + 15) & ~15ull;
-        const uint32_t tl = (uint32_t)((size + tile_bytes - 1) / tile_bytes);
+    for (uint32_t base = 0; base < n_parts; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t a = i < n_parts ? part_len[i] : 0;
+        const uint32_t b = i < n_parts ? part_tiles[i] : 0;
         uint64_t ea, ta;
         uint32_t eb, tb;
-        block_scan_pair(alen, tl, ea, eb, ta, tb);
-        if (k < n) {
-            const uint64_t start = carry_pos + ea;
-            XoChild c{};
-            c.dst = start;
-            c.n = size;
-            c.head_src = qm.tree_start;
-            c.i = qm.point;
-            c.mid_src = qd.tree_start + qd.point;
-            c.ld = ed - qd.point;
-            c.tail_src = qm.tree_start + em;
-            if (start + alen + 64 > arena_cap) {
-                atomicOr(err, kErrExtent);
-                c.n = 0;
-            }
-            kids[k] = c;
-            cstart[k] = start;
-            csize[k] = size;
-            tile_base[k] = carry_t + eb;
+        block_scan_pair(a, b, ea, eb, ta, tb);
+        if (i < n_parts) {
+            part_len[i] = carry_len + ea;
+            part_tiles[i] = carry_t + eb;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            carry_pos += ta;
+            carry_len += ta;
             carry_t += tb;
         }
         __syncthreads();
@@ -330,12 +333,54 @@ __global__ void __launch_bounds__(1024) xo_layout_kernel(const ExtentQuery *__re
     }
 }
 
+__global__ void __launch_bounds__(kLayoutT) xo_place_kernel(const ExtentQuery *__restrict__ q,
+                                                            const uint64_t *__restrict__ ends, uint32_t n,
+                                                            uint32_t tile_bytes, uint64_t arena_cap,
+                                                            const uint64_t *__restrict__ part_len,
+                                                            const uint32_t *__restrict__ part_tiles,
+                                                            XoChild *__restrict__ kids, uint64_t *__restrict__ cstart,
+                                                            const uint64_t *__restrict__ csize,
+                                                            uint32_t *__restrict__ tile_base, uint32_t *err)
+{
+    const uint32_t k = blockIdx.x * kLayoutT + threadIdx.x;
+    const uint64_t z = k < n ? csize[k] : 0;
+    const uint64_t alen = (z + 15) & ~15ull;
+    uint64_t ea, ta;
+    uint32_t eb, tb;
+    block_scan_pair(alen, (uint32_t)((z + tile_bytes - 1) / tile_bytes), ea, eb, ta, tb);
+    if (k >= n) return;
+    const uint64_t start = part_len[blockIdx.x] + ea;
+    const ExtentQuery qm = q[2 * k], qd = q[2 * k + 1];
+    XoChild c{};
+    c.dst = start;
+    c.n = z;
+    c.head_src = qm.tree_start;
+    c.i = qm.point;
+    c.mid_src = qd.tree_start + qd.point;
+    c.ld = ends[2 * k + 1] - qd.point;
+    c.tail_src = qm.tree_start + ends[2 * k];
+    if (start + alen + 64 > arena_cap) {
+        atomicOr(err, kErrExtent);
+        c.n = 0;
+    }
+    kids[k] = c;
+    cstart[k] = start;
+    tile_base[k] = part_tiles[blockIdx.x] + eb;
+}
+
+uint32_t xo_layout_parts(uint32_t n) { return (n + kLayoutT - 1) / kLayoutT; }
+
 cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_t n, uint32_t tile_bytes,
                              uint64_t arena_cap, XoChild *kids, uint64_t *cstart, uint64_t *csize,
-                             uint32_t *tile_base, uint32_t *n_tiles, uint32_t *err, cudaStream_t s)
+                             uint32_t *tile_base, uint32_t *n_tiles, uint64_t *part_len, uint32_t *part_tiles,
+                             uint32_t *err, cudaStream_t s)
 {
-    xo_layout_kernel<<<1, 1024, 0, s>>>(q, ends, n, tile_bytes, arena_cap, kids, cstart, csize, tile_base,
-                                        n_tiles, err);
+    if (n == 0) return cudaSuccess;
+    const uint32_t parts = xo_layout_parts(n);
+    xo_size_kernel<<<parts, kLayoutT, 0, s>>>(q, ends, n, tile_bytes, csize, part_len, part_tiles);
+    xo_part_scan_kernel<<<1, 1024, 0, s>>>(part_len, part_tiles, parts, tile_base, n, n_tiles);
+    xo_place_kernel<<<parts, kLayoutT, 0, s>>>(q, ends, n, tile_bytes, arena_cap, part_len, part_tiles, kids, cstart,
+                                               csize, tile_base, err);
     return cudaGetLastError();
 }
 
