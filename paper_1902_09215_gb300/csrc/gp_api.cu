@@ -1188,10 +1188,15 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
         const uint64_t o_kids = round_up(o_q + sizeof(ExtentQuery) * q.size(), 256);
         const uint64_t o_tb = round_up(o_kids + sizeof(XoChild) * n_ops, 256);
         const uint32_t parts = xo_layout_parts(n_ops);
+        const uint32_t tile = 16384;
+        uint64_t max_tiles = 0;                // children are no larger than their bounds
+        for (uint64_t b : C->h_bound) max_tiles += (b + tile - 1) / tile;
+        if (max_tiles > 0x7fffffffull) return GP_ENOMEM;
         const uint64_t o_pl = round_up(o_tb + sizeof(uint32_t) * (n_ops + 1), 256);
         const uint64_t o_pt = round_up(o_pl + sizeof(uint64_t) * parts, 256);
+        const uint64_t o_tc = round_up(o_pt + sizeof(uint32_t) * parts, 256);
         uint8_t *blk;
-        CK(tmp.alloc((void **)&blk, o_pt + sizeof(uint32_t) * parts, s));
+        CK(tmp.alloc((void **)&blk, o_tc + sizeof(uint32_t) * max_tiles, s));
         uint32_t *d_ntiles = reinterpret_cast<uint32_t *>(blk);
         uint64_t *d_end = reinterpret_cast<uint64_t *>(blk + o_end);
         ExtentQuery *d_q = reinterpret_cast<ExtentQuery *>(blk + o_q);
@@ -1203,14 +1208,13 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
             ProfScope ps(GP_KERNEL_EXTENT, s);
             CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_lerr, s));
         }
-        const uint32_t tile = 16384;
-        CK(launch_xo_layout(d_q, d_end, n_ops, tile, C->arena_bytes, d_kids, C->d_start, C->d_size, d_tb,
+        uint32_t *d_tc = reinterpret_cast<uint32_t *>(blk + o_tc);
+        CK(launch_xo_layout(d_q, d_end, n_ops, tile, C->arena_bytes, d_kids, C->d_start, C->d_size, d_tb, d_tc,
                             d_ntiles, reinterpret_cast<uint64_t *>(blk + o_pl),
                             reinterpret_cast<uint32_t *>(blk + o_pt), d_lerr, s));
         {
             ProfScope ps(GP_KERNEL_COPY, s);
-            CK(launch_xo_copy_dev(M->d_arena, C->d_arena, d_kids, d_tb, n_ops, d_ntiles, tile,
-                                  sm_count(C->device), s));
+            CK(launch_xo_copy_map(M->d_arena, C->d_arena, d_kids, d_tb, d_tc, d_ntiles, (uint32_t)max_tiles, tile, s));
         }
         note_launches(3);                      // the layout kernels (the others are counted by scope)
         return GP_OK;

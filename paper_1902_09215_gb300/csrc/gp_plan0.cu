@@ -39,26 +39,32 @@ __global__ void plan0_count_kernel(const uint64_t *__restrict__ size, uint32_t n
 
 __global__ void plan0_bases_kernel(uint32_t *cls, uint32_t *counts)
 {
-    if (threadIdx.x != 0) return;
-    uint32_t pos = 0, r = 0;
-    for (int c = kCls - 1; c >= 0; --c) {
-        const uint32_t x = cls[c];
-        cls[c] = pos;
-        pos += x;
+    __shared__ uint32_t v[3 * kCls];
+    for (int i = threadIdx.x; i < 3 * kCls; i += blockDim.x) v[i] = cls[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t pos = 0, r = 0;
+        for (int c = kCls - 1; c >= 0; --c) {
+            const uint32_t x = v[c];
+            v[c] = pos;
+            pos += x;
+        }
+        counts[2] = pos;                 // one slot per chunk
+        for (int c = kCls - 1; c >= 0; --c) {
+            const uint32_t x = v[kCls + c];
+            v[kCls + c] = pos;
+            pos += x;
+        }
+        for (int c = kCls - 1; c >= 0; --c) {
+            const uint32_t x = v[2 * kCls + c];
+            v[2 * kCls + c] = r;
+            r += x;
+        }
+        counts[0] = pos;
+        counts[1] = r;
     }
-    counts[2] = pos;                     // one slot per chunk
-    for (int c = kCls - 1; c >= 0; --c) {
-        const uint32_t x = cls[kCls + c];
-        cls[kCls + c] = pos;
-        pos += x;
-    }
-    for (int c = kCls - 1; c >= 0; --c) {
-        const uint32_t x = cls[2 * kCls + c];
-        cls[2 * kCls + c] = r;
-        r += x;
-    }
-    counts[0] = pos;
-    counts[1] = r;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * kCls; i += blockDim.x) cls[i] = v[i];
 }
 
 __global__ void plan0_place_kernel(const uint64_t *__restrict__ start, const uint64_t *__restrict__ size, uint32_t n,
@@ -112,7 +118,7 @@ cudaError_t launch_plan_level0(const uint64_t *start, const uint64_t *size, uint
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)umin64((n + 255) / 256, (uint64_t)sms * 4);
     plan0_count_kernel<<<blocks, 256, 0, s>>>(size, n, C, cls);
-    plan0_bases_kernel<<<1, 32, 0, s>>>(cls, counts);
+    plan0_bases_kernel<<<1, 3 * kCls, 0, s>>>(cls, counts);
     plan0_place_kernel<<<blocks, 256, 0, s>>>(start, size, n, C, items, ropes, cls);
     return cudaGetLastError();
 }

@@ -11,29 +11,49 @@ namespace gpk {
 // One warp per query: the end (exclusive) of the subtree rooted at `point`.
 // Reading left to right, `need` counts subtrees still to be read: an
 // operator adds one, a leaf removes one; the subtree ends where it reaches
-// zero.  Each step covers 32 lanes x 16 bytes.
+// zero.  Each step covers 32 lanes x 64 bytes from a 16-byte aligned base,
+// every lane with four 16-byte loads issued together (bytes before `point`
+// or past the tree do not count; a lane loads only if its first byte is
+// inside the tree, and trees are followed by at least 64 padding bytes).
+constexpr uint32_t kExtLane = 64;
+
 __device__ __forceinline__ void extent_one(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
                                            uint32_t w, int lane, uint64_t *__restrict__ end_out,
                                            uint32_t *err)
 {
     const ExtentQuery Q = q[w];
     const uint64_t tend = Q.tree_start + Q.tree_size;
-    uint64_t pos = Q.tree_start + Q.point;
+    const uint64_t p0 = Q.tree_start + Q.point;
+    uint64_t base = p0 & ~15ull;
     int64_t need = 1;
     for (;;) {
-        if (pos >= tend) {
+        if (base >= tend) {
             if (lane == 0) {
                 atomicOr(err, kErrExtent);
                 end_out[w] = Q.tree_size;
             }
             return;
         }
-        const uint64_t lo = pos + 16ull * lane;
+        const uint64_t lo = base + (uint64_t)kExtLane * lane;
+        uint4 v[kExtLane / 16];
+#pragma unroll
+        for (int k = 0; k < (int)(kExtLane / 16); ++k)
+            v[k] = lo < tend ? __ldg(reinterpret_cast<const uint4 *>(arena + lo) + k) : make_uint4(0, 0, 0, 0);
+        // bytes [ia, ib) of this lane's 64 count
+        const int ia = p0 > lo ? (int)umin64(p0 - lo, kExtLane) : 0;
+        const int ib = tend > lo ? (int)umin64(tend - lo, kExtLane) : 0;
+        // this lane's net change and lowest running value over its bytes
         int s = 0, mn = 1 << 30;
-        for (int k = 0; k < 16; ++k) {
-            if (lo + k < tend) {
-                s += (arena[lo + k] < 4) ? 1 : -1;
-                mn = min(mn, s);
+#pragma unroll
+        for (int k = 0; k < (int)(kExtLane / 16); ++k) {
+            const uint32_t wd[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = 16 * k + i;
+                if (j >= ia && j < ib) {
+                    s += ((wd[i >> 2] >> (8 * (i & 3))) & 0xFFu) < 4 ? 1 : -1;
+                    mn = min(mn, s);
+                }
             }
         }
         // exclusive prefix of s over lanes
@@ -43,23 +63,31 @@ __device__ __forceinline__ void extent_one(const uint8_t *__restrict__ arena, co
             if (lane >= off) incl += o;
         }
         const int excl = incl - s;
-        const bool closes = (lo < tend) && (need + excl + mn <= 0);
+        const bool closes = need + excl + mn <= 0;
         const unsigned ball = __ballot_sync(0xffffffffu, closes);
         if (ball) {
             const int f = __ffs(ball) - 1;
             if (lane == f) {
                 int64_t r = need + excl;
-                uint64_t k = 0;
-                for (; k < 16; ++k) {
-                    r += (arena[lo + k] < 4) ? 1 : -1;
-                    if (r == 0) break;
+                int e = -1;
+#pragma unroll
+                for (int k = 0; k < (int)(kExtLane / 16); ++k) {
+                    const uint32_t wd[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int j = 16 * k + i;
+                        if (e < 0 && j >= ia && j < ib) {
+                            r += ((wd[i >> 2] >> (8 * (i & 3))) & 0xFFu) < 4 ? 1 : -1;
+                            if (r == 0) e = j;
+                        }
+                    }
                 }
-                end_out[w] = lo + k + 1 - Q.tree_start;
+                end_out[w] = lo + (uint64_t)e + 1 - Q.tree_start;
             }
             return;
         }
         need += __shfl_sync(0xffffffffu, incl, 31);
-        pos += 512;
+        base += 32ull * kExtLane;
     }
 }
 
@@ -340,7 +368,8 @@ __global__ void __launch_bounds__(kLayoutT) xo_place_kernel(const ExtentQuery *_
                                                             const uint32_t *__restrict__ part_tiles,
                                                             XoChild *__restrict__ kids, uint64_t *__restrict__ cstart,
                                                             const uint64_t *__restrict__ csize,
-                                                            uint32_t *__restrict__ tile_base, uint32_t *err)
+                                                            uint32_t *__restrict__ tile_base,
+                                                            uint32_t *__restrict__ tile_child, uint32_t *err)
 {
     const uint32_t k = blockIdx.x * kLayoutT + threadIdx.x;
     const uint64_t z = k < n ? csize[k] : 0;
@@ -365,22 +394,49 @@ __global__ void __launch_bounds__(kLayoutT) xo_place_kernel(const ExtentQuery *_
     }
     kids[k] = c;
     cstart[k] = start;
-    tile_base[k] = part_tiles[blockIdx.x] + eb;
+    const uint32_t tb0 = part_tiles[blockIdx.x] + eb;
+    tile_base[k] = tb0;
+    const uint32_t nt = (uint32_t)((z + tile_bytes - 1) / tile_bytes);
+    for (uint32_t i = 0; i < nt; ++i) tile_child[tb0 + i] = k;     // the copy's tile -> child map
 }
 
 uint32_t xo_layout_parts(uint32_t n) { return (n + kLayoutT - 1) / kLayoutT; }
 
 cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_t n, uint32_t tile_bytes,
                              uint64_t arena_cap, XoChild *kids, uint64_t *cstart, uint64_t *csize,
-                             uint32_t *tile_base, uint32_t *n_tiles, uint64_t *part_len, uint32_t *part_tiles,
-                             uint32_t *err, cudaStream_t s)
+                             uint32_t *tile_base, uint32_t *tile_child, uint32_t *n_tiles, uint64_t *part_len,
+                             uint32_t *part_tiles, uint32_t *err, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const uint32_t parts = xo_layout_parts(n);
     xo_size_kernel<<<parts, kLayoutT, 0, s>>>(q, ends, n, tile_bytes, csize, part_len, part_tiles);
     xo_part_scan_kernel<<<1, 1024, 0, s>>>(part_len, part_tiles, parts, tile_base, n, n_tiles);
     xo_place_kernel<<<parts, kLayoutT, 0, s>>>(q, ends, n, tile_bytes, arena_cap, part_len, part_tiles, kids, cstart,
-                                               csize, tile_base, err);
+                                               csize, tile_base, tile_child, err);
+    return cudaGetLastError();
+}
+
+// Copy tiles numbered on the device, each tile's child read from the map the
+// layout wrote: a CTA takes tiles t = blockIdx.x, +gridDim.x, ...
+__global__ void xo_copy_map_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                                   const XoChild *__restrict__ children, const uint32_t *__restrict__ tile_base,
+                                   const uint32_t *__restrict__ tile_child, const uint32_t *n_tiles_dev,
+                                   uint32_t tile_bytes)
+{
+    const uint32_t n_tiles = *n_tiles_dev;
+    for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const uint32_t k = tile_child[t];
+        copy_tile(src, dst, children[k], (uint64_t)(t - tile_base[k]) * tile_bytes, tile_bytes);
+    }
+}
+
+cudaError_t launch_xo_copy_map(const uint8_t *src, uint8_t *dst, const XoChild *children, const uint32_t *tile_base,
+                               const uint32_t *tile_child, const uint32_t *n_tiles_dev, uint32_t max_tiles,
+                               uint32_t tile_bytes, cudaStream_t s)
+{
+    if (max_tiles == 0) return cudaSuccess;
+    xo_copy_map_kernel<<<(uint32_t)umin64(max_tiles, 8192), 256, 0, s>>>(src, dst, children, tile_base, tile_child,
+                                                                         n_tiles_dev, tile_bytes);
     return cudaGetLastError();
 }
 
