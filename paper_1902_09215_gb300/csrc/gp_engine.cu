@@ -928,6 +928,7 @@ gp_status Engine::write_head(uint32_t mode, const std::vector<uint32_t> &runs, c
 gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
 {
     uint32_t nl = 0;
+    uint32_t prev_chunks = 0;            // sizing: chunks the previous level cut
     for (uint32_t level = 0; level < levels_max; ++level) {
         const bool wide = level > 0;
         const int k = level & 1;
@@ -951,11 +952,17 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
                 w.spill = (float2 *)p;
                 w.cap_dedicated = nd;
                 A.cap_dedicated = nd;
+                // the failed build zeroed the chunk count the level starts
+                // from: put back the previous level's before building again
                 GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
+                GK(cudaMemcpyAsync(&ctl->n_chunks, &prev_chunks, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
                 items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
                                                   t_first_, t_state_, w.items);
                 GK(cudaGetLastError());
+                GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+                GK(cudaStreamSynchronize(s));
             }
+            prev_chunks = c.n_chunks;
         }
         fill_chunks_kernel<<<sms * 4, 256, 0, s>>>(ctl, w.C, t_first_, t_lo_, t_hi_, w.items);
         GK(cudaGetLastError());

@@ -181,7 +181,24 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
         float ms = -1.f;
         for (int rep = 0; rep < 2; ++rep) ms = time_eval(G, cs);             // timed, device only
         if ((st = E.read_run(G->run, &R, cs))) return fail(st);
-        if (ms < 0.f || R.err) return fail(R.err ? map_err(R.err, 0) : GP_ECUDA);
+        if (ms < 0.f || R.err) {
+            if (verbose && verbose[0] == '1' && R.err == 0) {
+                std::fprintf(stderr, "gp_generation_create: chunk %u: timing launch failed\n", C);
+            } else if (verbose && verbose[0] == '1') {
+                BatchCtl c2{};
+                E.read_ctl(&c2, cs);
+                std::fprintf(stderr, "gp_generation_create: chunk %u timed: run error bits 0x%x, batch error 0x%x, "
+                             "eval error 0x%x, caps codes %llu/%llu values %llu/%llu items %llu ded %llu, "
+                             "needs codes %llu/%llu values %llu/%llu items %llu ded %llu\n", C, R.err, c2.err,
+                             c2.eval_err[0], (unsigned long long)E.w.cap_codes[0], (unsigned long long)E.w.cap_codes[1],
+                             (unsigned long long)E.w.cap_values[0], (unsigned long long)E.w.cap_values[1],
+                             (unsigned long long)E.w.cap_items, (unsigned long long)E.w.cap_dedicated,
+                             (unsigned long long)c2.need_codes[0], (unsigned long long)c2.need_codes[1],
+                             (unsigned long long)c2.need_values[0], (unsigned long long)c2.need_values[1],
+                             (unsigned long long)c2.need_items, (unsigned long long)c2.need_dedicated);
+            }
+            return fail(R.err ? map_err(R.err, 0) : GP_ECUDA);
+        }
         if (k < 8) {
             G->info.autotune_chunk[k] = C;
             G->info.autotune_ms[k] = ms;

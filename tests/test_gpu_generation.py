@@ -95,6 +95,29 @@ def test_many_levels_large_trees(gpu, oracle):
         nodes, offs, ref = kids, koffs, ref_next
 
 
+def test_creation_grows_dedicated_spill_of_upper_levels(gpu, oracle):
+    """Comb-shaped trees (every operator's first argument an x leaf, its
+    second the rest of the tree) cut into 1024-node chunks have upper trees
+    that do not shrink, so the first upper level makes them final items with
+    dedicated spill areas far above the creation's first guess: its sizing
+    pass must grow the pool, build that level again from the same chunk
+    counts, and go on to every later level."""
+    rng = np.random.default_rng(21)
+    trees = []
+    for k in (60000, 90000, 150000):
+        t = np.full(2 * k + 1, 4, np.uint8)
+        t[0:2 * k:2] = rng.integers(0, 4, k).astype(np.uint8)
+        trees.append(t)
+    trees += [synth.random_tree(rng, n) for n in (101, 2001, 30001)]
+    nodes, offs = synth.pack(trees)
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=3, chunk_nodes=1024, use_graph=True)
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+    assert_same_eval(gpu, G, ref)
+    gpu.gp_generation_destroy(G)
+
+
 def test_level_budget_follows_growth(gpu, oracle):
     """Generation 0 fits one chunk per tree (one level), so the level budget
     starts at three; children of a few hundred nodes with 256-node chunks
