@@ -149,14 +149,39 @@ __device__ void block_scan2(uint64_t *sa, uint64_t *sb, uint64_t a, uint64_t b)
     }
 }
 
-// One CTA per batch slot.  Generate: child sizes (child = mum[0,i) ++
-// dad[j,e_d) ++ mum[e_m,n_m)), node limit, 16-byte aligned starts in the
-// run's other buffer, copy tiles; the batch's tree table gets the children.
-// Evaluate: the batch's tree table gets the run's current population.
-// A run that has stopped contributes no trees (size 0).
-__global__ void __launch_bounds__(kScanT) children_kernel(
+// Children of a batch in three steps.  children_size_kernel (a thread per
+// child): the child's size i + (e_d - j) + (n_m - e_m) from the extent
+// queries and ends, into bsize; runs stopped by an error and evaluate-mode
+// batches take their current trees instead.  children_scan_kernel (one CTA
+// per run): 16-byte aligned offsets and copy tiles by a block scan over the
+// run's children (coalesced, no gathers), node limit and buffer capacity;
+// a run that does not fit gets its error and no children.  children_place_
+// kernel (a thread per child): copy records and the new buffer's starts and
+// sizes.
+__global__ void children_size_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run,
+                                     const uint32_t *__restrict__ tree_base, const ExtentQuery *__restrict__ q,
+                                     const uint64_t *__restrict__ ends, uint64_t *__restrict__ bstart,
+                                     uint64_t *__restrict__ bsize)
+{
+    const BatchHead h = ctl->head;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < h.n_trees; g += gridDim.x * blockDim.x) {
+        const uint32_t slot = slot_of(tree_base, h.n_runs, g);
+        const RunDev *R = runs + slot_run[slot];
+        const uint32_t c = g - tree_base[slot];
+        const bool stopped = R->err != 0 || (h.mode == kModeGenerate && ctl->eval_err[1] != 0);
+        if (stopped || h.mode == kModeEvaluate) {
+            const RunBuf &B = R->buf[R->cur];
+            bstart[g] = stopped ? 0 : B.start[c];
+            bsize[g] = stopped ? 0 : B.size[c];
+            continue;
+        }
+        const ExtentQuery qm = q[2 * g], qd = q[2 * g + 1];
+        bsize[g] = qm.point + (ends[2 * g + 1] - qd.point) + (qm.tree_size - ends[2 * g]);
+    }
+}
+
+__global__ void __launch_bounds__(kScanT) children_scan_kernel(
     BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run, const uint32_t *__restrict__ tree_base,
-    const gp_xo *__restrict__ recs, const uint64_t *__restrict__ ends, XoChild *__restrict__ kids,
     uint32_t *__restrict__ tile_local, uint32_t *__restrict__ run_tiles, uint64_t *__restrict__ bstart,
     uint64_t *__restrict__ bsize)
 {
@@ -168,66 +193,35 @@ __global__ void __launch_bounds__(kScanT) children_kernel(
     if (slot >= h.n_runs) return;
     RunDev *R = runs + slot_run[slot];
     const uint32_t base = tree_base[slot], n = R->n;
+    const bool stopped = R->err != 0 || (h.mode == kModeGenerate && ctl->eval_err[1] != 0);
+    if (stopped || h.mode == kModeEvaluate) {
+        if (t == 0) run_tiles[slot] = 0;
+        return;
+    }
     if (t == 0) {
         s_bad = 0;
         s_nodes = 0;
     }
     __syncthreads();
-    const bool stopped = R->err != 0 || (h.mode == kModeGenerate && ctl->eval_err[1] != 0);
-    if (stopped || h.mode == kModeEvaluate) {
-        const RunBuf B = R->buf[R->cur];         // by value (see below)
-        for (uint32_t c = t; c < n; c += kScanT) {
-            bstart[base + c] = stopped ? 0 : B.start[c];
-            bsize[base + c] = stopped ? 0 : B.size[c];
-        }
-        if (t == 0) run_tiles[slot] = 0;
-        return;
-    }
-    // the run's fields once, by value: the stores below could otherwise
-    // alias them and force a reload after every store
-    const uint32_t cur = R->cur;
-    const RunBuf P = R->buf[cur];
-    const RunBuf Cb = R->buf[cur ^ 1];
+    const RunBuf Cb = R->buf[R->cur ^ 1];
     const uint64_t max_nodes = R->max_nodes;
-    const uint64_t *__restrict__ psize = P.size;
-    const uint64_t *__restrict__ pstart = P.start;
-    // rounds of kScanT children, one per thread (independent, coalesced
-    // loads), a block scan per round and a running carry; the outputs of a
-    // run that turns out not to fit are cleared at the end
+    // rounds of kScanT children (coalesced), a block scan per round and a
+    // running carry; this run's children offsets go to bstart for now
     uint64_t carry_a = 0, carry_b = 0, nodes = 0;
     uint32_t bad = 0;
     for (uint32_t r0 = 0; r0 < n; r0 += kScanT) {
-        const uint32_t c = r0 + t, g = base + c;
-        uint64_t m = 0, a = 0, b = 0, em = 0, ed = 0;
-        gp_xo r{};
+        const uint32_t c = r0 + t;
+        uint64_t m = 0;
         if (c < n) {
-            r = recs[g];
-            em = ends[2 * g];
-            ed = ends[2 * g + 1];
-            m = r.mum_point + (ed - r.dad_point) + (psize[r.mum] - em);
+            m = bsize[base + c];
             if (max_nodes && m > max_nodes) bad |= kGErrLimit;
-            a = (m + 15) & ~15ull;
-            b = (m + kTile - 1) / kTile;
             nodes += m;
         }
+        const uint64_t a = (m + 15) & ~15ull, b = (m + kTile - 1) / kTile;
         block_scan2(sa, sb, a, b);
-        const uint64_t ra = carry_a + sa[t] - a, rb = carry_b + sb[t] - b;
         if (c < n) {
-            XoChild k;
-            k.dst = Cb.lo + ra;
-            k.n = m;
-            k.head_src = pstart[r.mum];
-            k.i = r.mum_point;
-            k.mid_src = pstart[r.dad] + r.dad_point;
-            k.ld = ed - r.dad_point;
-            k.tail_src = pstart[r.mum] + em;     // tail byte p comes from mum[em + p - i - ld]
-            k.pad = 0;
-            kids[g] = k;
-            Cb.start[c] = Cb.lo + ra;
-            Cb.size[c] = m;
-            bstart[g] = Cb.lo + ra;
-            bsize[g] = m;
-            tile_local[g] = (uint32_t)rb;
+            bstart[base + c] = carry_a + sa[t] - a;
+            tile_local[base + c] = (uint32_t)(carry_b + sb[t] - b);
         }
         carry_a += sa[kScanT - 1];
         carry_b += sb[kScanT - 1];
@@ -250,6 +244,38 @@ __global__ void __launch_bounds__(kScanT) children_kernel(
         run_tiles[slot] = (uint32_t)carry_b;
         R->next_nodes = s_nodes;
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->child_nodes), s_nodes);
+    }
+}
+
+__global__ void children_place_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run,
+                                      const uint32_t *__restrict__ tree_base, const ExtentQuery *__restrict__ q,
+                                      const uint64_t *__restrict__ ends, XoChild *__restrict__ kids,
+                                      uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize)
+{
+    const BatchHead h = ctl->head;
+    if (h.mode != kModeGenerate || ctl->eval_err[1] != 0) return;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < h.n_trees; g += gridDim.x * blockDim.x) {
+        const uint32_t slot = slot_of(tree_base, h.n_runs, g);
+        RunDev *R = runs + slot_run[slot];
+        if (R->err != 0) continue;           // stopped before, or its children did not fit
+        const uint32_t c = g - tree_base[slot];
+        const RunBuf &Cb = R->buf[R->cur ^ 1];
+        const ExtentQuery qm = q[2 * g], qd = q[2 * g + 1];
+        const uint64_t em = ends[2 * g], ed = ends[2 * g + 1];
+        const uint64_t dst = Cb.lo + bstart[g], m = bsize[g];
+        XoChild k;
+        k.dst = dst;
+        k.n = m;
+        k.head_src = qm.tree_start;
+        k.i = qm.point;
+        k.mid_src = qd.tree_start + qd.point;
+        k.ld = ed - qd.point;
+        k.tail_src = qm.tree_start + em;         // tail byte p comes from mum[em + p - i - ld]
+        k.pad = 0;
+        kids[g] = k;
+        Cb.start[c] = dst;
+        Cb.size[c] = m;
+        bstart[g] = dst;
     }
 }
 
@@ -1043,14 +1069,19 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     select_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, recs_, q_);
     GK(cudaGetLastError());
     GK(launch_extent_dev(heap, q_, 2 * max_trees, &ctl->n_queries, ends_, &ctl->eval_err[1], sms, s));
-    children_kernel<<<max_runs, kScanT, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, recs_, ends_, kids_,
-                                                 tile_local_, run_tiles_, bstart_, bsize_);
+    children_size_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, q_, ends_, bstart_, bsize_);
+    GK(cudaGetLastError());
+    children_scan_kernel<<<max_runs, kScanT, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, tile_local_, run_tiles_,
+                                                      bstart_, bsize_);
+    GK(cudaGetLastError());
+    children_place_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, q_, ends_, kids_, bstart_,
+                                                  bsize_);
     GK(cudaGetLastError());
     run_tiles_scan_kernel<<<1, 32, 0, s>>>(ctl, run_tiles_);
     GK(cudaGetLastError());
     GK(launch_xo_copy_runs(heap, kids_, tile_local_, tree_base_, run_tiles_, &ctl->head.n_runs, &ctl->n_tiles,
                            kTile, sms, s));
-    nl += 5;
+    nl += 7;
     gp_status st = enqueue_eval(s, sizing, &nl);
     if (st) return st;
     const uint32_t sblocks =
