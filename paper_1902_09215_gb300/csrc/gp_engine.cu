@@ -303,6 +303,7 @@ struct LevelArgs {
     uint32_t last;                // the last level: every open tree becomes a final item
     uint64_t spill_base;          // first dedicated spill entry (after the per-warp areas)
     uint64_t cap_dedicated;       // dedicated spill entries available
+    uint64_t cap_slots;           // fused chunk slots (0: no fused chunks)
 };
 
 __device__ __forceinline__ uint32_t size_bucket(uint64_t len)
@@ -312,14 +313,20 @@ __device__ __forceinline__ uint32_t size_bucket(uint64_t len)
 }
 
 // One CTA.  Level 0: every tree of the batch (size 0: none); a tree of at
-// most C nodes is one final item, a larger one is cut into chunks of C.
-// Level k > 0: every tree that had chunks at level k-1 now has an upper
-// tree of codes [frag_off[first chunk], frag_off[one past its last chunk]);
-// it becomes a final item when it fits one chunk, did not at least halve, or
-// this is the last level (a final above C gets a dedicated spill area);
-// otherwise it is cut again.
-// Chunk items come first in tree order (their fragments must be contiguous
-// per tree), then finals from the largest size bucket down.
+// most C nodes is one final item; a tree of 2..kFuseMaxChunks chunks (when
+// the workspace has fused slots) becomes fused chunks, each writing its
+// fragment into its own slot (the tree's slots consecutive), and its rope
+// (a final item over those slots) goes to level 1; a larger tree is cut into
+// planned chunks of C.  Level k > 0: every tree that had planned chunks at
+// level k-1 now has an upper tree of codes [frag_off[first chunk],
+// frag_off[one past its last chunk]); it becomes a final item when it fits
+// one chunk, did not at least halve, or this is the last level (a final
+// above C gets a dedicated spill area); otherwise it is cut again.
+// Items: planned chunks first in tree order (their fragments must be
+// contiguous per tree), then fused chunks, then finals (ropes included)
+// from the largest size bucket down.
+// Tree states: 0 done or empty, 1 open (planned), 2 rope pending (t_lo: its
+// first slot, t_hi: its chunk count).
 __global__ void __launch_bounds__(kScanT) items_kernel(
     BatchCtl *ctl, LevelArgs A, const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
     const uint64_t *__restrict__ frag_off, uint64_t *__restrict__ t_lo, uint64_t *__restrict__ t_hi,
@@ -333,9 +340,9 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     const uint32_t t = threadIdx.x;
     const uint32_t n = ctl->head.n_trees, C = A.C;
     // nothing to do: an earlier error, or no tree was cut at the level before
-    if (ctl->err != 0 || (A.level > 0 && ctl->n_chunks == 0)) {
-        __syncthreads();                      // every thread has read n_chunks
-        if (t == 0) ctl->n_items = ctl->n_chunks = 0;
+    if (ctl->err != 0 || (A.level > 0 && ctl->n_chunks == 0 && ctl->n_ropes == 0)) {
+        __syncthreads();                      // every thread has read n_chunks / n_ropes
+        if (t == 0) ctl->n_items = ctl->n_chunks = ctl->n_ropes = 0;
         return;
     }
     if (t < kBuckets) {
@@ -344,6 +351,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     }
     const uint32_t per = (n + kScanT - 1) / kScanT;
     const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
+    const uint64_t fuse_hi = (A.level == 0 && A.cap_slots) ? (uint64_t)kFuseMaxChunks * C : 0;
 
     // phase 1: this level's range of every open tree (all reads of the old
     // t_first happen before the barrier; phase 3 rewrites it)
@@ -353,20 +361,27 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             t_hi[i] = bstart[i] + bsize[i];
             t_prev[i] = ~0ull;
             t_state[i] = bsize[i] != 0;
-        } else if (t_state[i]) {
+        } else if (t_state[i] == 1) {
             t_lo[i] = frag_off[t_first[i]];
             t_hi[i] = frag_off[t_first[i + 1]];
         }
     }
     __syncthreads();
-    // phase 2: chunks, dedicated spill and finals per size bucket
-    uint64_t nch = 0, ded = 0;
+    // phase 2: planned chunks, dedicated spill, fused chunks and finals per
+    // size bucket
+    uint64_t nch = 0, ded = 0, nfz = 0;
     for (uint32_t i = lo; i < hi; ++i) {
         if (!t_state[i]) continue;
+        if (t_state[i] == 2) {                // a rope: final
+            atomicAdd(&s_cnt[size_bucket(t_hi[i] * C)], 1u);
+            continue;
+        }
         const uint64_t len = t_hi[i] - t_lo[i];
         if (A.last || len <= C || 2 * len > t_prev[i]) {
             atomicAdd(&s_cnt[size_bucket(len)], 1u);
             if (len > C) ded += len;
+        } else if (len <= fuse_hi) {
+            nfz += (len + C - 1) / C;
         } else {
             nch += (len + C - 1) / C;
         }
@@ -374,8 +389,12 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     block_scan2(sa, sb, nch, ded);
     uint64_t ex_ch = sa[t] - nch, ex_ded = sb[t] - ded;
     const uint64_t tot_ch = sa[kScanT - 1], tot_ded = sb[kScanT - 1];
+    __syncthreads();                          // the arrays are scanned again
+    block_scan2(sa, sb, nfz, 0);
+    uint64_t ex_fz = sa[t] - nfz;
+    const uint64_t tot_fz = sa[kScanT - 1];
     if (t == 0) {
-        uint64_t pos = tot_ch;                // finals after the chunks, largest bucket first
+        uint64_t pos = tot_ch + tot_fz;       // finals after the chunks, largest bucket first
         for (int b = (int)kBuckets - 1; b >= 0; --b) {
             s_base[b] = pos;
             pos += s_cnt[b];
@@ -383,25 +402,40 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         uint32_t err = 0;
         ctl->need_dedicated = max(ctl->need_dedicated, tot_ded);
         ctl->need_items = max(ctl->need_items, pos);
+        ctl->need_slots = max(ctl->need_slots, tot_fz);
         if (pos > A.cap_items) err |= kGErrItems;
         if (tot_ded > A.cap_dedicated) err |= kGErrSpill;
+        if (tot_fz > A.cap_slots) err |= kGErrSlots;
         if (err) {
             atomicOr(&ctl->err, err);
-            ctl->n_items = ctl->n_chunks = 0;
+            ctl->n_items = ctl->n_chunks = ctl->n_ropes = 0;
         } else {
             ctl->n_items = (uint32_t)pos;
             ctl->n_chunks = (uint32_t)tot_ch;
+            ctl->n_ropes = (uint32_t)tot_fz;
             if (pos) ctl->levels = A.level + 1;
         }
         s_err = err;
     }
     __syncthreads();
     if (s_err) return;
-    // phase 3: chunk offsets per tree, final items (any order within a
-    // bucket), states
+    // phase 3: chunk offsets per tree, fused chunks, final items (any order
+    // within a bucket), states
     for (uint32_t i = lo; i < hi; ++i) {
         t_first[i] = (uint32_t)ex_ch;
         if (!t_state[i]) continue;
+        if (t_state[i] == 2) {
+            const uint32_t b = size_bucket(t_hi[i] * C);
+            EvalItem it{};
+            it.tree = i;
+            it.flags = kItemFinal | gpk::kItemRope;
+            it.pt_base = t_lo[i];
+            it.frag_len = (uint32_t)t_hi[i];
+            it.spill_off = kNoSpill;
+            items[s_base[b] + atomicAdd(&s_fill[b], 1u)] = it;
+            t_state[i] = 0;
+            continue;
+        }
         const uint64_t len = t_hi[i] - t_lo[i];
         if (A.last || len <= C || 2 * len > t_prev[i]) {
             const uint32_t b = size_bucket(len);
@@ -418,6 +452,24 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             }
             items[s_base[b] + atomicAdd(&s_fill[b], 1u)] = it;
             t_state[i] = 0;
+        } else if (len <= fuse_hi) {
+            const uint32_t m = (uint32_t)((len + C - 1) / C);
+            for (uint32_t j = 0; j < m; ++j) {
+                EvalItem it{};
+                it.begin = t_lo[i] + (uint64_t)j * C;
+                it.end = umin64(t_hi[i], it.begin + C);
+                it.tree = i;
+                it.flags = gpk::kItemFused;
+                it.frag_off = ex_fz + j;
+                it.pt_base = ex_fz;
+                it.frag_len = m;
+                it.spill_off = kNoSpill;
+                items[tot_ch + ex_fz + j] = it;
+            }
+            t_state[i] = 2;
+            t_lo[i] = ex_fz;
+            t_hi[i] = m;
+            ex_fz += m;
         } else {
             t_prev[i] = len;
             ex_ch += (len + C - 1) / C;
@@ -514,10 +566,13 @@ __global__ void scatter_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t
 
 // End of a batch: a batch error stops every run in it (no run advances);
 // otherwise each run still going advances one generation (Generate mode).
-__global__ void finish_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run)
+__global__ void finish_kernel(const BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run,
+                              const uint32_t *__restrict__ fz_redo)
 {
     const BatchHead h = ctl->head;
-    const uint32_t berr = batch_errors(ctl);
+    // a rope that found one of its slots overflowed left its tree without
+    // results: the batch made nothing (the caller enlarges the slots)
+    const uint32_t berr = batch_errors(ctl) | ((fz_redo && fz_redo[0]) ? kGErrSlots : 0u);
     for (uint32_t s = threadIdx.x; s < h.n_runs; s += blockDim.x) {
         RunDev *R = runs + slot_run[s];
         if (R->err) continue;
@@ -892,8 +947,39 @@ gp_status Engine::load_run(uint32_t r, const uint8_t *nodes, const uint64_t *off
     return e == cudaSuccess ? GP_OK : gfail(e);
 }
 
+gp_status Engine::set_slots(uint64_t cap_slots, uint32_t fz_cap_pt)
+{
+    cudaDeviceSynchronize();
+    for (void *p : {(void *)w.fz_codes, (void *)w.fz_pt, (void *)w.fz_len, (void *)w.fz_over, (void *)w.fz_redo})
+        if (p) {
+            cudaFree(p);
+            work_allocs_.erase(std::remove(work_allocs_.begin(), work_allocs_.end(), p), work_allocs_.end());
+        }
+    w.fz_codes = w.fz_len = w.fz_over = w.fz_redo = nullptr;
+    w.fz_pt = nullptr;
+    w.cap_slots = cap_slots;
+    w.fz_cap_pt = fz_cap_pt ? fz_cap_pt : std::max<uint32_t>(128, w.C / 8);
+    for (auto &e : exec)                 // the graphs captured the old slots
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    if (!cap_slots) return GP_OK;
+    auto &v = work_allocs_;
+    gp_status st;
+    if ((st = galloc(v, (void **)&w.fz_codes, sizeof(uint32_t) * (cap_slots * w.C + 32)))) return st;
+    if ((st = galloc(v, (void **)&w.fz_pt, sizeof(float2) * (cap_slots * w.fz_cap_pt * lanes + 1)))) return st;
+    if ((st = galloc(v, (void **)&w.fz_len, sizeof(uint32_t) * cap_slots))) return st;
+    if ((st = galloc(v, (void **)&w.fz_over, sizeof(uint32_t) * max_trees))) return st;
+    if ((st = galloc(v, (void **)&w.fz_redo, sizeof(uint32_t) * (1 + (uint64_t)max_trees)))) return st;
+    if (cudaMemset(w.fz_over, 0, sizeof(uint32_t) * max_trees) != cudaSuccess ||
+        cudaMemset(w.fz_redo, 0, sizeof(uint32_t)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return GP_ECUDA;                 // done before any stream uses the slots
+    return GP_OK;
+}
+
 gp_status Engine::set_workspace(uint32_t C, const uint64_t cap_codes[2], const uint64_t cap_values[2],
-                                uint64_t cap_dedicated, uint64_t cap_items)
+                                uint64_t cap_dedicated, uint64_t cap_items, uint64_t cap_slots, uint32_t fz_cap_pt)
 {
     cudaDeviceSynchronize();
     gfree(work_allocs_);
@@ -919,6 +1005,7 @@ gp_status Engine::set_workspace(uint32_t C, const uint64_t cap_codes[2], const u
         if ((st = galloc(v, (void **)&w.vals[k], sizeof(float2) * (cap_values[k] * lanes + 1)))) return st;
     }
     if ((st = galloc(v, (void **)&w.spill, sizeof(float2) * lanes * (w.spill_base + w.cap_dedicated)))) return st;
+    if ((st = set_slots(cap_slots, fz_cap_pt))) return st;
     // the graphs captured the old workspace
     for (auto &e : exec)
         if (e) {
@@ -959,7 +1046,7 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
         const bool wide = level > 0;
         const int k = level & 1;
         LevelArgs A{level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu),
-                    level + 1 == levels_max ? 1u : 0u, w.spill_base, w.cap_dedicated};
+                    level + 1 == levels_max ? 1u : 0u, w.spill_base, w.cap_dedicated, w.cap_slots};
         items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
                                           t_state_, w.items);
         GK(cudaGetLastError());
@@ -970,6 +1057,20 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
             BatchCtl c{};
             GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             GK(cudaStreamSynchronize(s));
+            if (c.err == kGErrSlots && w.cap_slots) {
+                // more fused chunks than slots: more slots, the level again
+                gp_status st = set_slots(std::max<uint64_t>(2 * c.need_slots, w.cap_slots), w.fz_cap_pt);
+                if (st) return st;
+                A.cap_slots = w.cap_slots;
+                GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
+                GK(cudaMemsetAsync(w.fz_over, 0, sizeof(uint32_t) * max_trees, s));
+                GK(cudaMemsetAsync(w.fz_redo, 0, sizeof(uint32_t), s));
+                items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
+                                                  t_first_, t_state_, w.items);
+                GK(cudaGetLastError());
+                GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+                GK(cudaStreamSynchronize(s));
+            }
             if (c.err == kGErrSpill) {
                 const uint64_t nd = std::max<uint64_t>(2 * c.need_dedicated, w.cap_dedicated);
                 void *p = nullptr;
@@ -1050,6 +1151,15 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
         p.spill = w.spill;
         p.spill_per_warp = w.spill_per_warp;
         p.err = &ctl->eval_err[0];
+        if (w.cap_slots) {
+            p.fz_codes = w.fz_codes;
+            p.fz_pt = w.fz_pt;
+            p.fz_len = w.fz_len;
+            p.fz_over = w.fz_over;
+            p.fz_redo = w.fz_redo;
+            p.fz_cap_codes = w.C;
+            p.fz_cap_pt = w.fz_cap_pt;
+        }
         GK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s));
         nl += 2;
     }
@@ -1062,8 +1172,12 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     (void)mode;
     uint32_t nl = 0;
     GK(cudaMemsetAsync(ctl->counter, 0, sizeof(ctl->counter), s));
-    // err, n_queries, n_tiles, n_items, n_chunks, levels, eval_err[4]
-    GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t) * 10, s));
+    // err, n_queries, n_tiles, n_items, n_chunks, levels, eval_err[4], n_ropes, pad2
+    GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t) * 12, s));
+    if (w.cap_slots) {                   // fused slots: overflow flags and the redo list
+        GK(cudaMemsetAsync(w.fz_over, 0, sizeof(uint32_t) * max_trees, s));
+        GK(cudaMemsetAsync(w.fz_redo, 0, sizeof(uint32_t), s));
+    }
     GK(cudaMemsetAsync(&ctl->child_nodes, 0, sizeof(uint64_t), s));
     const uint32_t blocks = std::max<uint32_t>(1, std::min<uint32_t>((max_trees + 127) / 128, sms * 8));
     select_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, recs_, q_);
@@ -1088,7 +1202,7 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
         (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)max_trees * n_cases + 255) / 256, sms * 8));
     scatter_kernel<<<sblocks, 256, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, bfit_, bvals_, bhits_, n_cases);
     GK(cudaGetLastError());
-    finish_kernel<<<1, 256, 0, s>>>(ctl, runs_dev, slot_run_);
+    finish_kernel<<<1, 256, 0, s>>>(ctl, runs_dev, slot_run_, w.cap_slots ? w.fz_redo : nullptr);
     GK(cudaGetLastError());
     nl += 2;
     if (launches) *launches = nl;

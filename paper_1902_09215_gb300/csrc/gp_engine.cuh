@@ -34,7 +34,10 @@ constexpr uint32_t kGErrEval = 32u;      // the evaluator reported an error
 constexpr uint32_t kGErrExtent = 64u;    // a subtree extent ran off its tree
 constexpr uint32_t kGErrSpill = 128u;    // oversized finals above the dedicated spill pool
 constexpr uint32_t kGErrGen = 256u;      // generation counter past 2^24
-constexpr uint32_t kGErrBatch = kGErrWork | kGErrLevels | kGErrItems | kGErrSpill | kGErrEval | kGErrExtent;
+constexpr uint32_t kGErrSlots = 512u;    // fused chunks: more than the slots, or a slot's value entries overflowed
+constexpr uint32_t kGErrBatch =
+    kGErrWork | kGErrLevels | kGErrItems | kGErrSpill | kGErrEval | kGErrExtent | kGErrSlots;
+constexpr uint32_t kFuseMaxChunks = 32;  // trees of 2..32 chunks: fused chunks and a rope
 
 constexpr uint32_t kModeGenerate = 0u;   // make one generation of every run in the batch
 constexpr uint32_t kModeEvaluate = 1u;   // evaluate every run's current population
@@ -66,8 +69,9 @@ struct BatchCtl {
     uint32_t err;                        // batch-level error bits of this batch
     uint32_t n_queries, n_tiles, n_items, n_chunks, levels;
     uint32_t eval_err[4];                // [0] evaluator error word, [1] extent error word
+    uint32_t n_ropes, pad2;              // fused chunks cut at level 0 (their ropes are level 1's)
     uint64_t totals[4];                  // plan scan totals of the current level
-    uint64_t need_codes[2], need_values[2], need_dedicated, need_items;   // sizing records (largest seen)
+    uint64_t need_codes[2], need_values[2], need_dedicated, need_items, need_slots;   // sizing records
     uint64_t child_nodes;                // nodes of all children made by this batch
     uint32_t counter[64];                // evaluator work counters, one per level
 };
@@ -92,6 +96,12 @@ struct Work {
     float2 *vals[2] = {nullptr, nullptr};
     float2 *spill = nullptr;
     uint64_t spill_per_warp = 0, spill_base = 0;
+    // fused chunks (trees of 2..32 chunks at level 0): one slot per chunk
+    // for its fragment (C codes, fz_cap_pt value entries); cap_slots 0 = off
+    uint64_t cap_slots = 0;
+    uint32_t fz_cap_pt = 0;
+    uint32_t *fz_codes = nullptr, *fz_len = nullptr, *fz_over = nullptr, *fz_redo = nullptr;
+    float2 *fz_pt = nullptr;
 };
 
 class Engine {
@@ -115,8 +125,13 @@ class Engine {
     // Upload, validate and lay out a run's initial population (generation 0,
     // not evaluated).
     gp_status load_run(uint32_t run, const uint8_t *nodes, const uint64_t *offsets, cudaStream_t s);
+    // cap_slots: fused chunk slots (0: every multi-chunk tree is planned);
+    // fz_cap_pt: value entries per slot (0: max(128, C / 8)).
     gp_status set_workspace(uint32_t C, const uint64_t cap_codes[2], const uint64_t cap_values[2],
-                            uint64_t cap_dedicated, uint64_t cap_items);
+                            uint64_t cap_dedicated, uint64_t cap_items, uint64_t cap_slots = 0,
+                            uint32_t fz_cap_pt = 0);
+    // Replace the fused slots by cap_slots slots of fz_cap_pt entries each.
+    gp_status set_slots(uint64_t cap_slots, uint32_t fz_cap_pt);
     // Enqueue one batch; `sizing` reads each level's totals back and grows
     // the workspace (never inside a capture).
     gp_status enqueue(uint32_t mode, const std::vector<uint32_t> &runs, cudaStream_t s, bool sizing,

@@ -30,7 +30,7 @@ gp_status map_err(uint32_t err, uint32_t eval_err)
 {
     if (!err) return GP_OK;
     if (err & (kGErrLimit | kGErrGen)) return GP_ELIMIT;
-    if (err & (kGErrArena | kGErrWork | kGErrItems | kGErrSpill | kGErrLevels)) return GP_ENOMEM;
+    if (err & (kGErrArena | kGErrWork | kGErrItems | kGErrSpill | kGErrLevels | kGErrSlots)) return GP_ENOMEM;
     if (err & kGErrExtent) return GP_EMALFORMED;
     if (err & kGErrEval) return (eval_err & gpk::kErrMalformed) ? GP_EMALFORMED : GP_ECUDA;
     return GP_ECUDA;
@@ -156,19 +156,36 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
     cudaStream_t cs = E.cap_stream;
     uint32_t best_C = 0;
     float best_ms = 0.f;
-    uint64_t best_codes[2] = {0, 0}, best_vals[2] = {0, 0}, best_ded = 0;
+    uint64_t best_codes[2] = {0, 0}, best_vals[2] = {0, 0}, best_ded = 0, best_slots = 0;
+    uint32_t best_pt = 0;
     for (size_t k = 0; k < tries.size(); ++k) {
         const uint32_t C = tries[k];
         const uint64_t c0[2] = {1u << 20, 1u << 20}, v0[2] = {1u << 18, 1u << 18};
-        step = "autotune workspace";
-        if ((st = E.set_workspace(C, c0, v0, 1u << 16, cap_arena / C + 2ull * n_trees + 1024))) return fail(st);
-        step = "autotune sizing pass";
-        if (cudaMemset(E.ctl, 0, sizeof(BatchCtl)) != cudaSuccess) return fail(GP_ECUDA);
-        E.forget_head();
-        if ((st = E.enqueue(kModeEvaluate, {G->run}, cs, true, nullptr))) return fail(st);   // sizing pass
+        // fused chunk slots: grown by the sizing pass; a slot whose value
+        // entries overflowed doubles the entries per slot (up to C, after
+        // which multi-chunk trees are planned instead)
+        uint64_t slots = 1024;
+        uint32_t pt = std::max<uint32_t>(128, C / 8);
         BatchCtl c{};
         RunDev R{};
-        if ((st = E.read_ctl(&c, cs)) || (st = E.read_run(G->run, &R, cs))) return fail(st);
+        for (;;) {
+            step = "autotune workspace";
+            if ((st = E.set_workspace(C, c0, v0, 1u << 16, cap_arena / C + 2ull * n_trees + 1024, slots, pt)))
+                return fail(st);
+            step = "autotune sizing pass";
+            // on the sizing stream: a legacy-stream memset is not ordered
+            // with the non-blocking stream and could land after the pass
+            // has recorded its needs
+            if (cudaMemsetAsync(E.ctl, 0, sizeof(BatchCtl), cs) != cudaSuccess) return fail(GP_ECUDA);
+            E.forget_head();
+            if ((st = E.enqueue(kModeEvaluate, {G->run}, cs, true, nullptr))) return fail(st);   // sizing pass
+            if ((st = E.read_ctl(&c, cs)) || (st = E.read_run(G->run, &R, cs))) return fail(st);
+            if (R.err != kGErrSlots || !slots) break;
+            slots = std::max<uint64_t>(slots, c.need_slots + c.need_slots / 2 + 64);
+            if (pt < C) pt *= 2;
+            else slots = 0;
+            if ((st = E.clear_error(G->run, cs))) return fail(st);
+        }
         if (R.err) {
             if (verbose && verbose[0] == '1')
                 std::fprintf(stderr, "gp_generation_create: chunk %u: run error bits 0x%x, batch error 0x%x, "
@@ -203,6 +220,9 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
             G->info.autotune_chunk[k] = C;
             G->info.autotune_ms[k] = ms;
         }
+        if (verbose && verbose[0] == '1')
+            std::fprintf(stderr, "gp_generation_create: chunk %u: %.3f ms, fused slots %llu needed (%llu x %u held)\n",
+                         C, ms, (unsigned long long)c.need_slots, (unsigned long long)E.w.cap_slots, E.w.fz_cap_pt);
         if (!best_C || ms < best_ms) {
             best_C = C;
             best_ms = ms;
@@ -211,6 +231,8 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
                 best_vals[i] = c.need_values[i];
             }
             best_ded = c.need_dedicated;
+            best_slots = slots ? std::max<uint64_t>(c.need_slots + c.need_slots / 2 + 64, 256) : 0;
+            best_pt = pt;
         }
     }
     // capacities: the measured need of generation 0 with a margin for the
@@ -224,13 +246,23 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
     }
     const uint64_t cap_ded = std::max<uint64_t>(2 * best_ded, 1u << 20);
     step = "final workspace";
-    if ((st = E.set_workspace(best_C, cap_codes, cap_vals, cap_ded, cap_arena / best_C + 2ull * n_trees + 1024)))
+    if ((st = E.set_workspace(best_C, cap_codes, cap_vals, cap_ded, cap_arena / best_C + 2ull * n_trees + 1024,
+                              best_slots, best_pt)))
         return fail(st);
     step = "generation 0 evaluation";
     if ((st = E.enqueue(kModeEvaluate, {G->run}, cs, false, nullptr))) return fail(st);
     {
         RunDev R{};
         if ((st = E.read_run(G->run, &R, cs))) return fail(st);
+        if (R.err && verbose && verbose[0] == '1') {
+            BatchCtl c2{};
+            E.read_ctl(&c2, cs);
+            std::fprintf(stderr, "gp_generation_create: generation 0: run error bits 0x%x, batch error 0x%x, "
+                         "eval error 0x%x, slots %llu (need %llu) x %u entries, items %llu (need %llu)\n", R.err,
+                         c2.err, c2.eval_err[0], (unsigned long long)E.w.cap_slots,
+                         (unsigned long long)c2.need_slots, E.w.fz_cap_pt, (unsigned long long)E.w.cap_items,
+                         (unsigned long long)c2.need_items);
+        }
         if (R.err) return fail(map_err(R.err, 0));
         G->info.levels = R.levels;
     }
@@ -296,7 +328,7 @@ gp_status gp_generation_recover(gp_generation *G, void *cuda_stream)
     RunDev R{};
     gp_status st = E.read_run(G->run, &R, G->last);
     if (st) return st;
-    const uint32_t room = kGErrArena | kGErrWork | kGErrItems | kGErrSpill;
+    const uint32_t room = kGErrArena | kGErrWork | kGErrItems | kGErrSpill | kGErrSlots;
     if (!R.err || (R.err & ~room)) return GP_EINVAL;
     if (R.err & kGErrArena) {
         const uint64_t cap = 2 * G->info.arena_bytes;
@@ -304,6 +336,20 @@ gp_status gp_generation_recover(gp_generation *G, void *cuda_stream)
         if (E.heap_largest_free() < need && (st = E.grow_heap(E.heap_bytes + need))) return st;
         if ((st = E.grow_run(G->run, cap, s))) return st;
         G->info.arena_bytes = cap;
+    }
+    if (R.err & kGErrSlots) {
+        // more fused chunks than slots: more slots; else a slot's value
+        // entries overflowed: twice the entries per slot, or (at C entries
+        // already) no fused chunks at all
+        BatchCtl c{};
+        if ((st = E.read_ctl(&c, s))) return st;
+        if (c.need_slots > E.w.cap_slots)
+            st = E.set_slots(std::max<uint64_t>(2 * E.w.cap_slots, c.need_slots + c.need_slots / 2), E.w.fz_cap_pt);
+        else if (E.w.fz_cap_pt < E.w.C)
+            st = E.set_slots(E.w.cap_slots, 2 * E.w.fz_cap_pt);
+        else
+            st = E.set_slots(0, 0);
+        if (st) return st;
     }
     if (R.err & (kGErrWork | kGErrItems | kGErrSpill)) {
         BatchCtl c{};
@@ -323,7 +369,7 @@ gp_status gp_generation_recover(gp_generation *G, void *cuda_stream)
         bool same = ded == E.w.cap_dedicated && items == E.w.cap_items;
         for (int k = 0; k < 2; ++k) same = same && codes[k] == E.w.cap_codes[k] && vals[k] == E.w.cap_values[k];
         if (same) return GP_EINVAL;              // nothing recorded as short: not a sizing failure
-        if ((st = E.set_workspace(E.w.C, codes, vals, ded, items))) return st;
+        if ((st = E.set_workspace(E.w.C, codes, vals, ded, items, E.w.cap_slots, E.w.fz_cap_pt))) return st;
         G->info.workspace_codes = E.w.cap_codes[0] + E.w.cap_codes[1];
         G->info.workspace_values = E.w.cap_values[0] + E.w.cap_values[1];
     }

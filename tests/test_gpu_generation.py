@@ -118,6 +118,34 @@ def test_creation_grows_dedicated_spill_of_upper_levels(gpu, oracle):
     gpu.gp_generation_destroy(G)
 
 
+def test_fused_slots_overflow_falls_back(gpu, oracle):
+    """Left combs (all operators first, then all leaves) of 10..20 chunks of
+    1024 nodes: their leaf-only chunks leave 1024 values each, far above a
+    slot's first 128 value entries, and their ropes would hold 10^4 values:
+    the creation doubles the entries per slot up to the chunk size and then
+    plans such trees instead; generations stay exact."""
+    rng = np.random.default_rng(31)
+    trees = []
+    for k in (5000, 8000, 10000):
+        trees.append(np.concatenate([rng.integers(0, 4, k).astype(np.uint8), np.full(k + 1, 4, np.uint8)]))
+    trees += [synth.random_tree(rng, n) for n in (101, 2001, 15001, 25001)]
+    nodes, offs = synth.pack(trees)
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    seed = 8
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=1024, use_graph=True)
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+    assert_same_eval(gpu, G, ref)
+    for g in range(2):
+        recs, kids, koffs, ref_next = oracle_step(oracle, nodes, offs, ref["fitness"], seed, g, (x, y, c))
+        gpu.gp_generation_step(G)
+        gn, go = gpu.gp_generation_trees(G)
+        assert np.array_equal(go, koffs) and np.array_equal(gn, kids), g
+        assert_same_eval(gpu, G, ref_next)
+        nodes, offs, ref = kids, koffs, ref_next
+    gpu.gp_generation_destroy(G)
+
+
 def test_level_budget_follows_growth(gpu, oracle):
     """Generation 0 fits one chunk per tree (one level), so the level budget
     starts at three; children of a few hundred nodes with 256-node chunks
