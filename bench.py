@@ -766,7 +766,9 @@ def run_ltee(args):
     prob = gp.Problem(x, y, c)
     nodes, offs = synth.ramped_half_and_half(seed=1, count=4000)
     stream = torch.cuda.Stream(torch.device("cuda", 0))
-    G = gp.gp_generation_create(prob, nodes, offs, seed=SEED_GEN, use_graph=True, stream=stream)
+    G = gp.gp_generation_create(prob, nodes, offs, seed=SEED_GEN, chunk_nodes=args.chunk, use_graph=True,
+                                stream=stream)
+    info0 = gp.gp_generation_get_info(G)
     sizes, best_fit = [int(offs[-1])], []
     recoveries, done, evaluated = 0, 0, 0
     t0 = time.perf_counter()
@@ -809,6 +811,8 @@ def run_ltee(args):
                              "samples": sizes[::every]},
         "best_fitness": {"every": every, "samples": best_fit[::every]},
         "recoveries": recoveries,
+        "chunk_nodes": int(info0["chunk_nodes"]), "levels_last": int(info["levels"]),
+        "autotune": {str(k): v for k, v in zip(info0["autotune_chunk"], info0["autotune_ms"]) if k},
         "arena_bytes": int(info["arena_bytes"]),
         "workspace": {"codes": int(info["workspace_codes"]), "values": int(info["workspace_values"])},
         "best": {"tree": best, "fitness": float(fit[best]), "hits": int(hits[best])},

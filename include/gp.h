@@ -278,11 +278,11 @@ gp_status gp_generation_step(gp_generation *g, uint32_t n, void *cuda_stream);
 gp_status gp_generation_rewind(gp_generation *g, void *cuda_stream);
 
 /* After a synchronising call reported GP_ENOMEM (the children outgrew the
- * population buffers, a level outgrew the evaluator workspace, or trees of
- * 2..32 chunks outgrew their fused chunk slots): enlarge what ran out (a
- * slot whose value entries overflowed doubles the entries per slot, up to
- * the chunk size, after which such trees go through planned levels), clear
- * the error and capture the generation again.  The next step makes the
+ * population buffers, a level outgrew the evaluator workspace, or a fused
+ * chunk's slot ran out of value entries): enlarge what ran out (the entries
+ * per slot double up to the chunk size, after which trees of 2..8 chunks go
+ * through planned levels too), clear the error and capture the generation
+ * again.  The next step makes the
  * failed generation again (its draws are the same).  Synchronises.
  * GP_EINVAL if the run has no such error; GP_ENOMEM if the device cannot
  * hold the larger buffers. */

@@ -367,6 +367,29 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         }
     }
     __syncthreads();
+    // level 0: trees of 2..kFuseMaxChunks chunks take fused slots in tree
+    // order while slots remain (the ones after are planned: a batch that
+    // outgrew the slots still runs); state 3 marks them until phase 3
+    uint64_t ncand = 0;
+    if (fuse_hi) {
+        for (uint32_t i = lo; i < hi; ++i) {
+            const uint64_t len = t_hi[i] - t_lo[i];
+            if (t_state[i] == 1 && len > C && len <= fuse_hi) ncand += (len + C - 1) / C;
+        }
+    }
+    block_scan2(sa, sb, ncand, 0);
+    uint64_t run_c = sa[t] - ncand;
+    if (t == 0) ctl->need_slots = max(ctl->need_slots, sa[kScanT - 1]);
+    __syncthreads();                          // the arrays are scanned again
+    if (fuse_hi) {
+        for (uint32_t i = lo; i < hi; ++i) {
+            const uint64_t len = t_hi[i] - t_lo[i];
+            if (t_state[i] != 1 || len <= C || len > fuse_hi) continue;
+            const uint64_t m = (len + C - 1) / C;
+            if (run_c + m <= A.cap_slots) t_state[i] = 3;
+            run_c += m;
+        }
+    }
     // phase 2: planned chunks, dedicated spill, fused chunks and finals per
     // size bucket
     uint64_t nch = 0, ded = 0, nfz = 0;
@@ -377,11 +400,11 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             continue;
         }
         const uint64_t len = t_hi[i] - t_lo[i];
-        if (A.last || len <= C || 2 * len > t_prev[i]) {
+        if (t_state[i] == 3) {
+            nfz += (len + C - 1) / C;
+        } else if (A.last || len <= C || 2 * len > t_prev[i]) {
             atomicAdd(&s_cnt[size_bucket(len)], 1u);
             if (len > C) ded += len;
-        } else if (len <= fuse_hi) {
-            nfz += (len + C - 1) / C;
         } else {
             nch += (len + C - 1) / C;
         }
@@ -402,10 +425,8 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         uint32_t err = 0;
         ctl->need_dedicated = max(ctl->need_dedicated, tot_ded);
         ctl->need_items = max(ctl->need_items, pos);
-        ctl->need_slots = max(ctl->need_slots, tot_fz);
         if (pos > A.cap_items) err |= kGErrItems;
         if (tot_ded > A.cap_dedicated) err |= kGErrSpill;
-        if (tot_fz > A.cap_slots) err |= kGErrSlots;
         if (err) {
             atomicOr(&ctl->err, err);
             ctl->n_items = ctl->n_chunks = ctl->n_ropes = 0;
@@ -437,7 +458,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             continue;
         }
         const uint64_t len = t_hi[i] - t_lo[i];
-        if (A.last || len <= C || 2 * len > t_prev[i]) {
+        if (t_state[i] != 3 && (A.last || len <= C || 2 * len > t_prev[i])) {
             const uint32_t b = size_bucket(len);
             EvalItem it{};
             it.begin = t_lo[i];
@@ -452,7 +473,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             }
             items[s_base[b] + atomicAdd(&s_fill[b], 1u)] = it;
             t_state[i] = 0;
-        } else if (len <= fuse_hi) {
+        } else if (t_state[i] == 3) {
             const uint32_t m = (uint32_t)((len + C - 1) / C);
             for (uint32_t j = 0; j < m; ++j) {
                 EvalItem it{};
@@ -1057,8 +1078,9 @@ gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
             BatchCtl c{};
             GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             GK(cudaStreamSynchronize(s));
-            if (c.err == kGErrSlots && w.cap_slots) {
-                // more fused chunks than slots: more slots, the level again
+            if (level == 0 && c.err == 0 && w.cap_slots && c.need_slots > w.cap_slots) {
+                // more fused-chunk candidates than slots (some went planned):
+                // more slots, the level again
                 gp_status st = set_slots(std::max<uint64_t>(2 * c.need_slots, w.cap_slots), w.fz_cap_pt);
                 if (st) return st;
                 A.cap_slots = w.cap_slots;

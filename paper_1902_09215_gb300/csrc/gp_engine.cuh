@@ -34,10 +34,14 @@ constexpr uint32_t kGErrEval = 32u;      // the evaluator reported an error
 constexpr uint32_t kGErrExtent = 64u;    // a subtree extent ran off its tree
 constexpr uint32_t kGErrSpill = 128u;    // oversized finals above the dedicated spill pool
 constexpr uint32_t kGErrGen = 256u;      // generation counter past 2^24
-constexpr uint32_t kGErrSlots = 512u;    // fused chunks: more than the slots, or a slot's value entries overflowed
+constexpr uint32_t kGErrSlots = 512u;    // a fused chunk's slot ran out of value entries
 constexpr uint32_t kGErrBatch =
     kGErrWork | kGErrLevels | kGErrItems | kGErrSpill | kGErrEval | kGErrExtent | kGErrSlots;
-constexpr uint32_t kFuseMaxChunks = 32;  // trees of 2..32 chunks: fused chunks and a rope
+// Trees of 2..kFuseMaxChunks chunks: fused chunks and a rope.  A rope walks
+// its tree's fragments one after the other and restarts its copy pipeline
+// at each, so the longest ropes (bloated populations) are kept short; larger
+// trees go through planned levels.
+constexpr uint32_t kFuseMaxChunks = 8;
 
 constexpr uint32_t kModeGenerate = 0u;   // make one generation of every run in the batch
 constexpr uint32_t kModeEvaluate = 1u;   // evaluate every run's current population
@@ -96,7 +100,7 @@ struct Work {
     float2 *vals[2] = {nullptr, nullptr};
     float2 *spill = nullptr;
     uint64_t spill_per_warp = 0, spill_base = 0;
-    // fused chunks (trees of 2..32 chunks at level 0): one slot per chunk
+    // fused chunks (trees of 2..kFuseMaxChunks chunks at level 0): one slot per chunk
     // for its fragment (C codes, fz_cap_pt value entries); cap_slots 0 = off
     uint64_t cap_slots = 0;
     uint32_t fz_cap_pt = 0;

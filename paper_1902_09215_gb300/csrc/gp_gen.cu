@@ -145,17 +145,23 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
     step = "load_run";
     if ((st = E.load_run(G->run, nodes, offsets, s))) return fail(st);
 
-    // chunk size: the given one, or the fastest candidate on generation 0
-    // (larger populations favour larger chunks: fewer fragment boundaries,
-    // fewer value entries; the per-warp spill area grows with the chunk)
+    // chunk size: the given one, or the fastest candidate on generation 0,
+    // a larger chunk preferred within 3% of the fastest (larger populations
+    // favour larger chunks: fewer fragment boundaries, fewer value entries;
+    // the per-warp spill area grows with the chunk).  A population whose
+    // trees all fit the smallest candidate says nothing about chunks (every
+    // candidate evaluates whole trees), and runs grow: 4096 then.
     const uint32_t small_c[4] = {1024, 2048, 4096, 8192}, large_c[3] = {4096, 8192, 16384};
+    uint64_t maxn = 0;
+    for (uint32_t t = 0; t < n_trees; ++t) maxn = std::max<uint64_t>(maxn, offsets[t + 1] - offsets[t]);
     std::vector<uint32_t> tries;
     if (params->chunk_nodes) tries.push_back(params->chunk_nodes);
+    else if (maxn <= small_c[0]) tries.push_back(4096);
     else if (used <= 100000000ull) tries.assign(small_c, small_c + 4);
     else tries.assign(large_c, large_c + 3);
     cudaStream_t cs = E.cap_stream;
     uint32_t best_C = 0;
-    float best_ms = 0.f;
+    float min_ms = 0.f;
     uint64_t best_codes[2] = {0, 0}, best_vals[2] = {0, 0}, best_ded = 0, best_slots = 0;
     uint32_t best_pt = 0;
     for (size_t k = 0; k < tries.size(); ++k) {
@@ -180,9 +186,9 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
             E.forget_head();
             if ((st = E.enqueue(kModeEvaluate, {G->run}, cs, true, nullptr))) return fail(st);   // sizing pass
             if ((st = E.read_ctl(&c, cs)) || (st = E.read_run(G->run, &R, cs))) return fail(st);
-            if (R.err != kGErrSlots || !slots) break;
+            if (R.err != kGErrSlots || !slots) break;      // a slot's value entries overflowed:
             slots = std::max<uint64_t>(slots, c.need_slots + c.need_slots / 2 + 64);
-            if (pt < C) pt *= 2;
+            if (pt < C) pt *= 2;                           // more entries, or no fused chunks
             else slots = 0;
             if ((st = E.clear_error(G->run, cs))) return fail(st);
         }
@@ -223,9 +229,9 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
         if (verbose && verbose[0] == '1')
             std::fprintf(stderr, "gp_generation_create: chunk %u: %.3f ms, fused slots %llu needed (%llu x %u held)\n",
                          C, ms, (unsigned long long)c.need_slots, (unsigned long long)E.w.cap_slots, E.w.fz_cap_pt);
-        if (!best_C || ms < best_ms) {
+        min_ms = best_C ? std::min(min_ms, ms) : ms;
+        if (!best_C || ms <= 1.03f * min_ms) {          // candidates come in increasing chunk size
             best_C = C;
-            best_ms = ms;
             for (int i = 0; i < 2; ++i) {
                 best_codes[i] = c.need_codes[i];
                 best_vals[i] = c.need_values[i];
@@ -338,17 +344,14 @@ gp_status gp_generation_recover(gp_generation *G, void *cuda_stream)
         G->info.arena_bytes = cap;
     }
     if (R.err & kGErrSlots) {
-        // more fused chunks than slots: more slots; else a slot's value
-        // entries overflowed: twice the entries per slot, or (at C entries
-        // already) no fused chunks at all
+        // a slot's value entries overflowed: twice the entries per slot (and
+        // room for every candidate), or (at C entries already) no fused
+        // chunks at all
         BatchCtl c{};
         if ((st = E.read_ctl(&c, s))) return st;
-        if (c.need_slots > E.w.cap_slots)
-            st = E.set_slots(std::max<uint64_t>(2 * E.w.cap_slots, c.need_slots + c.need_slots / 2), E.w.fz_cap_pt);
-        else if (E.w.fz_cap_pt < E.w.C)
-            st = E.set_slots(E.w.cap_slots, 2 * E.w.fz_cap_pt);
-        else
-            st = E.set_slots(0, 0);
+        const uint64_t slots = std::max<uint64_t>(E.w.cap_slots, c.need_slots + c.need_slots / 2);
+        if (E.w.fz_cap_pt < E.w.C) st = E.set_slots(slots, 2 * E.w.fz_cap_pt);
+        else st = E.set_slots(0, 0);
         if (st) return st;
     }
     if (R.err & (kGErrWork | kGErrItems | kGErrSpill)) {
