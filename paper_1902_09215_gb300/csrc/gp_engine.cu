@@ -127,26 +127,48 @@ __global__ void select_kernel(BatchCtl *ctl, RunDev *runs, const uint32_t *__res
     }
 }
 
-// Block-wide inclusive scan of two 64-bit values per thread (kScanT threads).
+// Block-wide inclusive scan of two 64-bit values per thread (kScanT
+// threads): warp scans by shuffles, a scan of the 32 warp totals by warp 0,
+// then each thread's warp offset; the results land in sa[t], sb[t] (the
+// block totals in sa[kScanT-1], sb[kScanT-1]) once it returns.
 __device__ void block_scan2(uint64_t *sa, uint64_t *sb, uint64_t a, uint64_t b)
 {
-    const uint32_t t = threadIdx.x;
+    __shared__ uint64_t wa[kScanT / 32], wb[kScanT / 32];
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (uint32_t off = 1; off < 32; off <<= 1) {
+        const uint64_t oa = __shfl_up_sync(0xffffffffu, a, off);
+        const uint64_t ob = __shfl_up_sync(0xffffffffu, b, off);
+        if (lane >= off) {
+            a += oa;
+            b += ob;
+        }
+    }
+    if (lane == 31) {
+        wa[warp] = a;
+        wb[warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t xa = wa[lane], xb = wb[lane];
+        for (uint32_t off = 1; off < 32; off <<= 1) {
+            const uint64_t oa = __shfl_up_sync(0xffffffffu, xa, off);
+            const uint64_t ob = __shfl_up_sync(0xffffffffu, xb, off);
+            if (lane >= off) {
+                xa += oa;
+                xb += ob;
+            }
+        }
+        wa[lane] = xa;                       // inclusive warp totals
+        wb[lane] = xb;
+    }
+    __syncthreads();
+    if (warp > 0) {
+        a += wa[warp - 1];
+        b += wb[warp - 1];
+    }
     sa[t] = a;
     sb[t] = b;
     __syncthreads();
-    for (uint32_t off = 1; off < kScanT; off <<= 1) {
-        uint64_t va = 0, vb = 0;
-        if (t >= off) {
-            va = sa[t - off];
-            vb = sb[t - off];
-        }
-        __syncthreads();
-        if (t >= off) {
-            sa[t] += va;
-            sb[t] += vb;
-        }
-        __syncthreads();
-    }
 }
 
 // Children of a batch in three steps.  children_size_kernel (a thread per
