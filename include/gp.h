@@ -230,15 +230,19 @@ typedef struct gp_generation_params {
     uint64_t seed;               /* seed of the draws                                   */
     uint32_t tournament_size;    /* 1..32 (7 in the paper)                               */
     uint32_t chunk_nodes;        /* evaluator chunk (multiple of 16, 256..65536);
-                                    0 = autotuned on the initial population: the fastest
-                                    of 1024..8192 (up to 1e8 nodes) or 4096..16384       */
+                                    0 = autotuned on the initial population: of
+                                    1024..8192 (up to 1e8 nodes) or 4096..16384, the
+                                    largest within 3% of the fastest; 4096 when every
+                                    initial tree fits 1024 nodes                        */
     uint64_t arena_bytes;        /* capacity of each population buffer; 0 = twice the
                                     initial population plus slack                        */
     uint64_t workspace_codes;    /* upper-tree codes per level; 0 = twice what the
                                     initial population needs, at least 2^20             */
     uint64_t workspace_values;   /* value-buffer entries per level; 0 = as above        */
     uint32_t use_graph;          /* nonzero: replay one CUDA graph per generation        */
-    uint32_t max_levels;         /* evaluation levels per generation (2..16; 0 = 8)      */
+    uint32_t max_levels;         /* evaluation levels per generation (2..16); 0 = those
+                                    of generation 0 plus two (3..8), widened by two
+                                    when a generation uses them all                     */
 } gp_generation_params;
 
 typedef struct gp_generation_info {

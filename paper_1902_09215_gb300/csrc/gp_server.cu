@@ -229,7 +229,7 @@ void worker_main(gp_server *S)
         ++S->st.batches;
         S->st.device_ms += ms;
         S->runs_in_batches += batch.size();
-        bool overflow = false;
+        bool overflow = false, slots_short = false;
         for (Run *R : batch) {
             R->in_batch = false;
             if (st) {
@@ -238,6 +238,14 @@ void worker_main(gp_server *S)
             }
             const RunDev &D = S->table[R->slot];
             const uint32_t batch_bits = kGErrWork | kGErrItems | kGErrSpill | kGErrLevels;
+            if (D.err == kGErrSlots) {
+                // a fused chunk's slot ran out of value entries: the batch
+                // goes again once the slots are larger (or off)
+                S->eng.clear_error(R->slot, S->stream);
+                slots_short = true;
+                ++S->st.retries;
+                continue;
+            }
             if (D.err) {
                 if (D.err == kGErrArena && 2 * R->arena + 512 <= S->prm.hbm_budget_bytes / 2) {
                     // outgrew its buffers: larger ones when there is room
@@ -275,6 +283,17 @@ void worker_main(gp_server *S)
             S->st.child_nodes += c.child_nodes;
             S->st.most_level_codes = std::max<uint64_t>(c.need_codes[0], c.need_codes[1]);
             S->st.most_level_values = std::max<uint64_t>(c.need_values[0], c.need_values[1]);
+        }
+        if (slots_short) {
+            // twice the value entries per slot, up to the chunk size; then
+            // every multi-chunk tree is planned
+            cudaStreamSynchronize(S->stream);
+            Engine &E = S->eng;
+            gp_status g = E.w.fz_cap_pt < E.w.C ? E.set_slots(E.w.cap_slots, 2 * E.w.fz_cap_pt) : E.set_slots(0, 0);
+            if (!g && S->prm.use_graph) g = E.capture(kModeGenerate);
+            if (g) {
+                for (Run *R : batch) fail_run(S, *R, g);
+            }
         }
         if (overflow) {
             cudaStreamSynchronize(S->stream);
@@ -324,8 +343,12 @@ gp_status gp_server_create(const gp_problem *problem, const gp_server_params *pa
     vals[0] = p.workspace_values ? p.workspace_values : std::max<uint64_t>(N / 33, 1u << 18);
     codes[1] = std::max<uint64_t>(codes[0] / 8, 1u << 20);
     vals[1] = std::max<uint64_t>(vals[0] / 8, 1u << 18);
+    // fused chunk slots for trees of 2..8 chunks (taken in tree order while
+    // they last, the rest planned): one per chunk of about an eighth of a
+    // full batch, at most 8192
+    const uint64_t fz_slots = std::max<uint64_t>(256, std::min<uint64_t>(N / p.chunk_nodes / 8, 8192));
     if (!st) st = S->eng.set_workspace(p.chunk_nodes, codes, vals, std::max<uint64_t>(codes[0] / 4, 1u << 20),
-                                       N / p.chunk_nodes + p.max_batch_trees + 1024);
+                                       N / p.chunk_nodes + p.max_batch_trees + 1024, fz_slots);
     if (!st && p.use_graph) st = S->eng.capture(kModeGenerate);
     if (!st && (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreate(&S->ev0) != cudaSuccess || cudaEventCreate(&S->ev1) != cudaSuccess))
