@@ -148,3 +148,30 @@ def test_generation_rejects_bad_arguments(oracle):
         oracle.generation_records(f, s, 10, seed=1, g=0, tsize=33)
     with pytest.raises(oracle.OracleError):
         oracle.generation_records(f, s, 10, seed=1, g=1 << 24)
+
+
+def test_child_size_bound(oracle):
+    """The arena a crossover sizes without reading the children back rests on
+    child size <= n_mum + n_dad - dad_point - 1 (the child keeps at most
+    mum's nodes other than the one at the crossover point, and gains at most
+    dad's nodes from dad_point on).  Checked on the oracle's children for
+    random points, and exact when mum's subtree is a leaf and dad's subtree
+    runs to the end of dad."""
+    rng = np.random.default_rng(77)
+    trees = [synth.random_tree(rng, int(n)) for n in rng.choice(np.arange(1, 400, 2), 60)]
+    nodes, offs = synth.pack(trees)
+    sizes = np.diff(offs.astype(np.int64))
+    mum, dad, mp, dp = synth.crossover_points(9, sizes, 500)
+    kn, ko = oracle.crossover_population(nodes, offs, mum, dad, mp, dp)
+    child = np.diff(ko.astype(np.int64))
+    bound = sizes[mum] + sizes[dad] - dp.astype(np.int64) - 1
+    assert np.all(child <= bound)
+    # equality: mum's point a leaf, dad's point the root (its subtree is all of dad)
+    m_leaf = [(t, int(np.nonzero(tr >= 4)[0][0])) for t, tr in enumerate(trees)]
+    mum2 = np.array([t for t, _ in m_leaf], np.uint32)
+    mp2 = np.array([i for _, i in m_leaf], np.uint64)
+    dad2 = np.roll(mum2, 1)
+    dp2 = np.zeros_like(mp2)
+    kn2, ko2 = oracle.crossover_population(nodes, offs, mum2, dad2, mp2, dp2)
+    child2 = np.diff(ko2.astype(np.int64))
+    assert np.array_equal(child2, sizes[mum2] + sizes[dad2] - 1)
