@@ -216,9 +216,10 @@ cudaError_t prepare_eval_once(int lanes, bool wide, size_t smem)
 
 struct EvalCfg {
     uint32_t C = 0, W = 0, K = 0, Wu = 0, Ku = 0;  // chunk, warps and windows (level 0 / upper)
+    uint32_t Wr = 0, Kr = 0;                       // a launch of ropes only
     int rows = (int)kLeafRows;                     // leaf table rows: 'x' + the constants
     int lanes = 0, sms = 0;
-    size_t smem = 0, smem_u = 0;
+    size_t smem = 0, smem_u = 0, smem_r = 0;
 };
 
 struct gp_population {
@@ -635,6 +636,18 @@ gp_status eval_config(const gp_population *P, const gp_eval_options *opt, EvalCf
     while (c.Wu > 1 && eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true, c.rows) > (size_t)maxsm) --c.Wu;
     c.smem = eval_smem_bytes(c.lanes, (int)c.W, (int)c.K, false, c.rows);
     c.smem_u = eval_smem_bytes(c.lanes, (int)c.Wu, (int)c.Ku, true, c.rows);
+    // A launch of ropes only: few long serial walks, latency-bound; a deeper
+    // window (fewer spills) beats more warps there (0.173 against 0.188 ms
+    // for the bench population's ropes at 192 and 128 entries).
+    c.Kr = opt && opt->upper_window_entries ? c.Ku : std::max<uint32_t>(c.K, 192);
+    c.Wr = std::min<uint32_t>(c.W, 16);
+    while (c.Wr > 1 && eval_smem_bytes(c.lanes, (int)c.Wr, (int)c.Kr, true, c.rows) > (size_t)maxsm) --c.Wr;
+    c.smem_r = eval_smem_bytes(c.lanes, (int)c.Wr, (int)c.Kr, true, c.rows);
+    if (c.smem_r > (size_t)maxsm) {
+        c.Kr = c.Ku;
+        c.Wr = c.Wu;
+        c.smem_r = c.smem_u;
+    }
     if (c.smem > (size_t)maxsm || c.smem_u > (size_t)maxsm) return GP_EINVAL;
     *cfg = c;
     return GP_OK;
@@ -932,7 +945,7 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
     const uint32_t C = cfg.C;
     const int lanes = cfg.lanes, sms = cfg.sms;
     CK(prepare_eval_once(lanes, false, cfg.smem));
-    CK(prepare_eval_once(lanes, true, cfg.smem_u));
+    CK(prepare_eval_once(lanes, true, std::max(cfg.smem_u, cfg.smem_r)));
     uint64_t max_items = 0, max_slots = 0, max_ropes = 0;
     for (uint64_t b : P->h_bound) {
         const uint64_t m = (b + C - 1) / C;
@@ -1011,9 +1024,9 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
             p.n_items = (uint32_t)max_ropes;
             p.n_items_dev = d_counts + 1;
             p.counter = d_counter + 1;
-            p.window = cfg.Ku;
+            p.window = cfg.Kr;
             ProfScope ps(GP_KERNEL_EVAL_UPPER, s);
-            CK(launch_eval(lanes, true, p, sms, (int)cfg.Wu, cfg.smem_u, s));
+            CK(launch_eval(lanes, true, p, sms, (int)cfg.Wr, cfg.smem_r, s));
             P->redo_pending = true;
         }
         CK(cudaMemcpyAsync(P->d_stat, d_counts, sizeof(uint32_t) * 3, cudaMemcpyDeviceToDevice, s));
