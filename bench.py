@@ -434,9 +434,24 @@ def cpu_baseline(nodes, offs, ops, x, y, c, child_nodes):
         if time.perf_counter() - t0 > 10.0:
             break
     el = time.perf_counter() - t0
+    # the same oracle on one thread, on a smaller sample (about 3 s)
+    one = 100
+    rn, ro = oracle.crossover_population(nodes, offs, *(a[:one] for a in ops))
+    t1 = time.perf_counter()
+    one_nodes, one_reps = 0, 0
+    while True:
+        oracle.eval_population(rn, ro, x, y, c, n_threads=1)
+        one_nodes += int(ro[-1])
+        one_reps += 1
+        if time.perf_counter() - t1 > 3.0:
+            break
+    el1 = time.perf_counter() - t1
     return {"value": done_nodes * len(x) / el, "unit": "GPops/s", "cores": cores, "kind": "oracle",
             "sample": f"{reps} x (crossover of the first {sample} of the 4000 records + oracle "
-                      f"evaluation of those children on {cores} threads), {el:.1f} s"}
+                      f"evaluation of those children on {cores} threads), {el:.1f} s",
+            "single_core": {"value": one_nodes * len(x) / el1, "unit": "GPops/s", "cores": 1,
+                            "sample": f"{one_reps} x oracle evaluation of the children of the first "
+                                      f"{one} records on 1 thread, {el1:.1f} s"}}
 
 
 # ---------------------------------------------------------------------------
