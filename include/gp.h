@@ -154,8 +154,9 @@ gp_status gp_tree_read(const gp_population *pop, uint32_t tree, uint8_t *dst, ui
 /* Device pointers and sizes of a population (valid until it is destroyed). */
 gp_status gp_population_get_info(const gp_population *pop, gp_population_info *info);
 
-/* Free a population's device memory (stream-ordered on the stream it was
- * last used with).  NULL is ignored. */
+/* Free a population's device memory, stream-ordered on the stream of the
+ * last call that enqueued work on it (its creation, an evaluation, or a
+ * crossover that read it as parents).  NULL is ignored. */
 void gp_destroy_population(gp_population *pop);
 
 /* Static, human-readable name of a status. */

@@ -1158,6 +1158,8 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
     }
     DeviceGuard dg(M->device);
     cudaStream_t s = Stream(cuda_stream).s;
+    // the parents are read on `s` from here on: their memory is freed there
+    const_cast<gp_population *>(M)->stream = s;
     gp_population *C = new (std::nothrow) gp_population();
     if (!C) return GP_ENOMEM;
     copy_problem_from(C, M);
