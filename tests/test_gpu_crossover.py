@@ -127,3 +127,29 @@ def test_children_device_planning_and_host_fallback(gpu, oracle, chunk):
     assert same_f32(vals, ref["out"]) and same_f32(fit, ref["fitness"])
     kn, ko = gpu.read_all_trees(kids)
     assert np.array_equal(kn, rn) and np.array_equal(ko, ro)
+
+
+def test_crossover_on_another_stream_then_parents_freed(gpu, oracle):
+    """Parents made on one stream, crossed on a second (after the first
+    finished) and destroyed at once: the parents' memory is freed on the
+    stream that read them, so the children are intact; they are evaluated
+    on that stream and match the oracle."""
+    import torch
+    x, y, c = synth.problem()
+    nodes, offs = synth.population_loguniform(seed=14, count=500, hi=60001)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    pop = gpu.gp_create_population(gpu.Problem(x, y, c), nodes, offs, sa)
+    sa.synchronize()
+    ops = synth.crossover_points(6, np.diff(offs.astype(np.int64)), 500)
+    kids = gpu.gp_crossover(pop, ops, sb)
+    gpu.gp_destroy_population(pop)
+    # new allocations on the first stream while the copies may still run
+    other = gpu.gp_create_population(gpu.Problem(x, y, c), nodes, offs, sa)
+    gpu.gp_evaluate(kids, sb)
+    fit, vals, _ = gpu.gp_fitness(kids, case_values=True)
+    rn, ro = oracle.crossover_population(nodes, offs, *ops)
+    ref = oracle.eval_population(rn, ro, x, y, c, n_threads=8)
+    assert same_f32(vals, ref["out"]) and same_f32(fit, ref["fitness"])
+    kn, ko = gpu.read_all_trees(kids)
+    assert np.array_equal(kn, rn) and np.array_equal(ko, ro)
+    gpu.gp_destroy_population(other)

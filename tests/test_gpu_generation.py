@@ -296,3 +296,28 @@ def test_paper_run_start_ramped_half_and_half(gpu, oracle):
         assert np.array_equal(go, koffs) and np.array_equal(gn, kids), g
         assert_same_eval(gpu, G, ref_next)
         nodes, offs, ref = kids, koffs, ref_next
+
+
+@pytest.mark.parametrize("trees", [[31], [1, 1], [1, 3, 1]])
+def test_degenerate_populations(gpu, oracle, trees):
+    """A one-tree population (every tournament picks it; it crosses with
+    itself) and populations of single leaves (every child is a leaf of a
+    parent): three generations identical to the oracle's."""
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    rng = np.random.default_rng(len(trees))
+    nodes, offs = synth.pack([synth.random_tree(rng, n) for n in trees])
+    seed = 77
+    G = gpu.gp_generation_create(prob, nodes, offs, seed=seed)
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=1)
+    assert_same_eval(gpu, G, ref)
+    for g in range(3):
+        recs, kids, koffs, ref_next = oracle_step(oracle, nodes, offs, ref["fitness"], seed, g, (x, y, c))
+        gpu.gp_generation_step(G)
+        got = gpu.gp_generation_records(G)
+        assert all(np.array_equal(a.astype(np.uint64), b.astype(np.uint64)) for a, b in zip(got, recs)), g
+        gn, go = gpu.gp_generation_trees(G)
+        assert np.array_equal(go, koffs) and np.array_equal(gn, kids), g
+        assert_same_eval(gpu, G, ref_next)
+        nodes, offs, ref = kids, koffs, ref_next
+    gpu.gp_generation_destroy(G)
