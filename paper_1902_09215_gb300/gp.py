@@ -244,10 +244,34 @@ def gp_create_population(problem: Problem, nodes, offsets, stream=None) -> Popul
     return Population(out, n, problem.n_cases)
 
 
+# gp_xo records as a numpy structured type with the C struct's field offsets
+_XO_DTYPE = np.dtype({"names": ["mum", "dad", "mum_point", "dad_point"],
+                      "formats": [np.uint32, np.uint32, np.uint64, np.uint64],
+                      "offsets": [gp_xo.mum.offset, gp_xo.dad.offset, gp_xo.mum_point.offset,
+                                  gp_xo.dad_point.offset],
+                      "itemsize": C.sizeof(gp_xo)})
+
+
 def make_xo(mum, dad, mum_point, dad_point):
-    ops = (gp_xo * len(mum))()
-    for k, (a, b, i, j) in enumerate(zip(mum, dad, mum_point, dad_point)):
-        ops[k] = gp_xo(int(a), int(b), int(i), int(j))
+    """A ctypes array of gp_xo from four equal-length integer sequences
+    (values wrap to the fields' widths, as ctypes assignment does)."""
+    def column(v, dt):
+        a = np.asarray(v)
+        if a.dtype.kind in "iu":
+            return a.reshape(-1).astype(dt, casting="unsafe")
+        mask = (1 << (8 * dt.itemsize)) - 1              # other values: wrap one by one
+        return np.array([int(x) & mask for x in np.asarray(v, dtype=object).reshape(-1)], dtype=dt)
+
+    cols = [column(v, _XO_DTYPE[name]) for v, name in zip((mum, dad, mum_point, dad_point), _XO_DTYPE.names)]
+    n = len(cols[0])
+    if any(len(v) != n for v in cols):
+        raise ValueError("mum, dad, mum_point and dad_point need the same length")
+    rec = np.zeros(n, _XO_DTYPE)
+    for name, v in zip(_XO_DTYPE.names, cols):
+        rec[name] = v
+    ops = (gp_xo * n)()
+    if n:
+        C.memmove(ops, rec.ctypes.data, rec.nbytes)
     return ops
 
 
