@@ -425,11 +425,13 @@ def gp_generation_fitness(g: Generation, case_values=False, hits=False):
 def gp_generation_records(g: Generation):
     recs = (gp_xo * g.n_trees)()
     _check(lib().gp_generation_records(g._h, recs), "gp_generation_records")
-    mum = np.array([r.mum for r in recs], np.uint32)
-    dad = np.array([r.dad for r in recs], np.uint32)
-    mp = np.array([r.mum_point for r in recs], np.uint64)
-    dp = np.array([r.dad_point for r in recs], np.uint64)
-    return mum, dad, mp, dp
+    return split_xo(recs)
+
+
+def split_xo(recs):
+    """(mum, dad, mum_point, dad_point) arrays of a ctypes array of gp_xo."""
+    rec = np.frombuffer(bytes(recs), dtype=_XO_DTYPE, count=len(recs))
+    return tuple(rec[name].copy() for name in _XO_DTYPE.names)
 
 
 def gp_generation_trees(g: Generation):

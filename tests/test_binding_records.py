@@ -35,3 +35,15 @@ def test_records_wrap_like_ctypes():
 def test_records_need_equal_lengths():
     with pytest.raises(ValueError):
         gp.make_xo([0, 1], [0], [0, 0], [0, 0])
+
+
+@pytest.mark.parametrize("n", [0, 1, 300])
+def test_records_split_back_to_arrays(n):
+    rng = np.random.default_rng(10 + n)
+    cols = (rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32),
+            rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32),
+            rng.integers(0, 2 ** 63, n, dtype=np.int64).astype(np.uint64) * 2 + 1,
+            rng.integers(0, 2 ** 63, n, dtype=np.int64).astype(np.uint64))
+    out = gp.split_xo(one_by_one(*cols))
+    for got, want, dt in zip(out, cols, (np.uint32, np.uint32, np.uint64, np.uint64)):
+        assert got.dtype == dt and np.array_equal(got, want)
