@@ -299,14 +299,23 @@ gp_status gp_generation_recover(gp_generation *g, void *cuda_stream);
  * GP_ECUDA. */
 gp_status gp_generation_fitness(gp_generation *g, float *fitness, float *case_values, uint32_t *hits);
 
-/* Synchronise and copy the crossover records of the last step (n_trees). */
+/* Synchronise and copy the crossover records that made the current
+ * population: records[n_trees], child t = record t (mum and dad index the
+ * previous population).  GP_EINVAL while the current population is
+ * generation 0 (before the first step, or after rewinding it); a failed
+ * step's error otherwise, as gp_generation_fitness. */
 gp_status gp_generation_records(gp_generation *g, gp_xo *records);
 
 /* Synchronise and copy the current population: offsets [n_trees + 1] and,
- * if nodes is not null, the packed trees (cap bytes at least the total). */
+ * if nodes is not null, the packed trees (cap bytes at least the total,
+ * else GP_EINVAL).  A failed step's error as gp_generation_fitness. */
 gp_status gp_generation_trees(gp_generation *g, uint64_t *offsets, uint8_t *nodes, uint64_t cap);
 
+/* Synchronise and describe the run (also after a failed step, whose
+ * generation is then error_generation; total_nodes is 0 in that case). */
 gp_status gp_generation_get_info(gp_generation *g, gp_generation_info *info);
+/* Free the run's device memory and graphs (waits for its work).  NULL is
+ * ignored. */
 void gp_generation_destroy(gp_generation *g);
 
 /* ---- Serving: many independent runs on one GPU (continuous batching).
@@ -373,6 +382,9 @@ gp_status gp_server_create(const gp_problem *problem, const gp_server_params *pa
  * the other fields are ignored.  GP_ENOMEM if the run can never fit. */
 gp_status gp_server_open_run(gp_server *s, const gp_generation_params *params, uint32_t n_trees,
                              const uint8_t *nodes, const uint64_t *offsets, uint64_t *run_id);
+/* Ask for `n_generations` (>= 1) more generations of a run; returns at
+ * once with the request's id.  GP_EINVAL for an unknown run or zero
+ * generations; the run's failure status if it has failed. */
 gp_status gp_server_submit(gp_server *s, uint64_t run_id, uint32_t n_generations, uint64_t *request_id);
 /* Wait for a request (timeout_ms < 0: no limit).  GP_ETIMEOUT if it has not
  * completed; otherwise GP_OK with the result (result->status is the
@@ -386,6 +398,8 @@ gp_status gp_server_run_trees(gp_server *s, uint64_t run_id, uint64_t *offsets, 
  * then be admitted).  A run not admitted yet is closed at once and its
  * requests complete with GP_EINVAL. */
 gp_status gp_server_close_run(gp_server *s, uint64_t run_id);
+/* Counters since the server was created (latency percentiles over every
+ * completed request); does not wait for the scheduler's current batch. */
 gp_status gp_server_get_stats(gp_server *s, gp_server_stats *stats);
 /* Stops the scheduler and frees everything; no other call on the server may
  * be in progress or follow (clients must have stopped waiting). */

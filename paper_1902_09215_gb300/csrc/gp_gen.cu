@@ -404,6 +404,7 @@ gp_status gp_generation_records(gp_generation *G, gp_xo *records)
     RunDev R{};
     gp_status st = sync_run(G, &R);
     if (st) return st;
+    if (R.gen == 0) return GP_EINVAL;      // no step has made the current population
     return G->eng.copy_records(records, 0, G->n);
 }
 

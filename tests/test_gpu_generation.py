@@ -274,6 +274,9 @@ def test_generation_rejects_bad_parameters(gpu):
     G = gpu.gp_generation_create(prob, nodes, offs, seed=1, chunk_nodes=256)
     with pytest.raises(gpu.GpError):
         gpu.gp_generation_rewind(G)                  # nothing to undo
+    with pytest.raises(gpu.GpError) as e:
+        gpu.gp_generation_records(G)                 # no step has made generation 0
+    assert e.value.status == gpu.GP_EINVAL
 
 
 def test_paper_run_start_ramped_half_and_half(gpu, oracle):
