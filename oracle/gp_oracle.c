@@ -2,8 +2,8 @@
  * CPU oracle for GP fitness evaluation and subtree crossover.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
- * calls this file: only tests/, __graft_entry__.smoke() and the CPU-baseline
- * leg of bench.py may use it.  It shares no code, header or table with the
+ * calls this file: only tests/, __graft_entry__.smoke() and bench.py's
+ * CPU-baseline leg and reference arm (--impl reference) may use it.  It shares no code, header or table with the
  * CUDA library.
  *
  * What it follows (Langdon & Banzhaf, "Faster Genetic Programming GPquick via

@@ -1,7 +1,8 @@
 """Python access to the CPU oracle (oracle/gp_oracle.c).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and
-bench.py's CPU-baseline leg, never by the product package.  It shares no
+bench.py's CPU-baseline leg and reference arm (--impl reference), never by
+the product package.  It shares no
 code with the CUDA library; both sides only share the seeded input
 generators of paper_1902_09215_gb300.synth.
 
