@@ -40,10 +40,14 @@ struct ProfScope {
     ProfScope(int k, cudaStream_t st) : kind(k), s(st) {
         g_launches.fetch_add(1, std::memory_order_relaxed);
         std::lock_guard<std::mutex> lk(g_prof_mu);
-        if (g_prof_on && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
-            cudaEventRecord(a, s);
-        else
-            a = b = nullptr;
+        if (g_prof_on && cudaEventCreate(&a) == cudaSuccess) {
+            if (cudaEventCreate(&b) == cudaSuccess) {
+                cudaEventRecord(a, s);
+                return;
+            }
+            cudaEventDestroy(a);
+        }
+        a = b = nullptr;
     }
     ~ProfScope() {
         if (a) {
