@@ -202,26 +202,30 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up (also sizes the child population); as many populations alive
-    # at once as in the timed loop, so the memory pool is at its working
-    # size before timing starts
-    keep = []
-    for _ in range(args.warmup):
-        keep.append(step())
-        gp.gp_fitness(keep[-1])
-        if len(keep) > 1:
-            keep.pop(0)
-    child_nodes = int(gp.gp_population_get_info(keep[-1]).total_nodes)
-    stats = gp.gp_eval_stats_get(keep[-1])
-    keep.clear()
+    # Clocks are sampled from before the warm-up to the end of the timed
+    # steps, so the sampler's start-up pause does not leave the GPU idle
+    # (its clocks falling) right before the first timed step.
+    clk = ClockSampler(local).__enter__()
+    try:
+        # warm-up (also sizes the child population); as many populations
+        # alive at once as in the timed loop, so the memory pool is at its
+        # working size before timing starts
+        keep = []
+        for _ in range(args.warmup):
+            keep.append(step())
+            gp.gp_fitness(keep[-1])
+            if len(keep) > 1:
+                keep.pop(0)
+        child_nodes = int(gp.gp_population_get_info(keep[-1]).total_nodes)
+        stats = gp.gp_eval_stats_get(keep[-1])
+        keep.clear()
 
-    # ---- timed: K steps, L2 flushed before each, device time per step
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    keep = []
-    barrier()
-    launches0 = gp.gp_kernel_launch_count()
-    with ClockSampler(local) as clk:
+        # ---- timed: K steps, L2 flushed before each, device time per step
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        keep = []
+        barrier()
+        launches0 = gp.gp_kernel_launch_count()
         t0 = time.perf_counter()
         for k in range(args.steps):
             with torch.cuda.stream(stream):
@@ -233,6 +237,8 @@ def run_ours(args):
                 keep.pop(0)
         barrier()
         wall = time.perf_counter() - t0
+    finally:
+        clk.__exit__(None, None, None)
     launches = gp.gp_kernel_launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     keep.clear()
