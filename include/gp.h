@@ -311,6 +311,13 @@ gp_status gp_generation_records(gp_generation *g, gp_xo *records);
  * else GP_EINVAL).  A failed step's error as gp_generation_fitness. */
 gp_status gp_generation_trees(gp_generation *g, uint64_t *offsets, uint8_t *nodes, uint64_t cap);
 
+/* Synchronise and copy one tree of the current population: its node count
+ * to *n_nodes and, if nodes is not null, its bytes (cap at least the count,
+ * else GP_EINVAL).  GP_EINVAL for tree >= n_trees; a failed step's error as
+ * gp_generation_fitness. */
+gp_status gp_generation_tree_read(gp_generation *g, uint32_t tree, uint8_t *nodes, uint64_t cap,
+                                  uint64_t *n_nodes);
+
 /* Synchronise and describe the run (also after a failed step, whose
  * generation is then error_generation; total_nodes is 0 in that case). */
 gp_status gp_generation_get_info(gp_generation *g, gp_generation_info *info);

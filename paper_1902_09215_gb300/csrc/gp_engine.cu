@@ -1353,6 +1353,21 @@ gp_status Engine::copy_trees(const RunBuf &B, uint32_t n, uint64_t *offsets, uin
     return GP_OK;
 }
 
+// One tree of a buffer: its size, and its bytes when `nodes` is given.
+gp_status Engine::copy_tree(const RunBuf &B, uint32_t t, uint8_t *nodes, uint64_t cap, uint64_t *n_nodes)
+{
+    uint64_t start = 0, size = 0;
+    GK(cudaDeviceSynchronize());
+    GK(cudaMemcpy(&start, B.start + t, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    GK(cudaMemcpy(&size, B.size + t, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (nodes) {
+        if (cap < size) return GP_EINVAL;
+        if (size) GK(cudaMemcpy(nodes, heap + start, size, cudaMemcpyDeviceToHost));
+    }
+    *n_nodes = size;
+    return GP_OK;
+}
+
 gp_status Engine::clear_error(uint32_t r, cudaStream_t s)
 {
     if (r >= max_runs) return GP_EINVAL;

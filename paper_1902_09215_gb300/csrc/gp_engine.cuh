@@ -152,6 +152,7 @@ class Engine {
     // a run buffer's trees packed (offsets [n+1], nodes if not null).
     gp_status copy_records(gp_xo *out, uint32_t first, uint32_t n);
     gp_status copy_trees(const RunBuf &B, uint32_t n, uint64_t *offsets, uint8_t *nodes, uint64_t cap);
+    gp_status copy_tree(const RunBuf &B, uint32_t t, uint8_t *nodes, uint64_t cap, uint64_t *n_nodes);
     // The device head was overwritten (e.g. the control block was cleared).
     void forget_head() { last_mode_ = ~0u; last_runs_.clear(); }
     uint64_t heap_free() const;

@@ -417,6 +417,16 @@ gp_status gp_generation_trees(gp_generation *G, uint64_t *offsets, uint8_t *node
     return G->eng.copy_trees(R.buf[R.cur], G->n, offsets, nodes, cap);
 }
 
+gp_status gp_generation_tree_read(gp_generation *G, uint32_t tree, uint8_t *nodes, uint64_t cap,
+                                  uint64_t *n_nodes)
+{
+    if (!G || !n_nodes || tree >= G->n) return GP_EINVAL;
+    RunDev R{};
+    gp_status st = sync_run(G, &R);
+    if (st) return st;
+    return G->eng.copy_tree(R.buf[R.cur], tree, nodes, cap, n_nodes);
+}
+
 gp_status gp_generation_get_info(gp_generation *G, gp_generation_info *info)
 {
     if (!G || !info) return GP_EINVAL;

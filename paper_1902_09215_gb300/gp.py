@@ -25,7 +25,8 @@ EXPORTED = [
     "gp_status_string", "gp_eval_stats_get", "gp_kernel_launch_count", "gp_profile_enable",
     "gp_profile_read", "gp_evaluate_noalloc",
     "gp_generation_create", "gp_generation_step", "gp_generation_rewind", "gp_generation_fitness",
-    "gp_generation_records", "gp_generation_trees", "gp_generation_get_info", "gp_generation_destroy",
+    "gp_generation_records", "gp_generation_trees", "gp_generation_tree_read", "gp_generation_get_info",
+    "gp_generation_destroy",
     "gp_generation_recover",
     "gp_server_create", "gp_server_open_run", "gp_server_submit", "gp_server_wait", "gp_server_run_fitness",
     "gp_server_run_trees", "gp_server_close_run", "gp_server_get_stats", "gp_server_destroy",
@@ -150,6 +151,7 @@ def lib():
             L.gp_generation_fitness.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_uint32)]
             L.gp_generation_records.argtypes = [vp, P(gp_xo)]
             L.gp_generation_trees.argtypes = [vp, P(C.c_uint64), P(C.c_uint8), C.c_uint64]
+            L.gp_generation_tree_read.argtypes = [vp, C.c_uint32, P(C.c_uint8), C.c_uint64, P(C.c_uint64)]
             L.gp_generation_get_info.argtypes = [vp, P(gp_generation_info)]
             L.gp_generation_destroy.argtypes = [vp]
             L.gp_generation_destroy.restype = None
@@ -441,6 +443,16 @@ def gp_generation_trees(g: Generation):
     _check(lib().gp_generation_trees(g._h, _ptr(offs, C.c_uint64), _ptr(nodes, C.c_uint8), nodes.shape[0]),
            "gp_generation_trees")
     return nodes[:int(offs[-1])], offs
+
+
+def gp_generation_tree_read(g: Generation, tree: int) -> np.ndarray:
+    """Bytes of one tree of the current population."""
+    n = C.c_uint64()
+    _check(lib().gp_generation_tree_read(g._h, int(tree), None, 0, C.byref(n)), "gp_generation_tree_read")
+    out = np.empty(max(int(n.value), 1), np.uint8)
+    _check(lib().gp_generation_tree_read(g._h, int(tree), _ptr(out, C.c_uint8), out.shape[0], C.byref(n)),
+           "gp_generation_tree_read")
+    return out[:int(n.value)]
 
 
 def gp_generation_get_info(g: Generation) -> dict:
