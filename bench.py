@@ -312,7 +312,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         a = time.perf_counter()
         p2 = gp.gp_create_population(prob, nodes_h, offs_h, stream)
-        k3 = gp.gp_crossover(p2, xo, stream)
+        k3 = gp.gp_crossover(p2, ops, stream)        # records marshalled as a caller's arrays
         gp.gp_evaluate(k3, stream)
         fit, _, _ = gp.gp_fitness(k3)
         te.append(time.perf_counter() - a)
