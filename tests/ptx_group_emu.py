@@ -1,9 +1,10 @@
-"""CPU model of the evaluator's byte-code group interpreter, for testing
-without a GPU.
+"""CPU model of the evaluator's group interpreters, for testing without a
+GPU.
 
-`group_asm(path)` expands the hand-written inline-PTX string of `group_u8`
-in gp_eval.cu (its macros included) into plain text by compiling a small C
-program that prints the same string literal.  `run` interprets that text
+`group_asm(path, fn)` expands the hand-written inline-PTX string of
+`group_u8` (byte codes) or `group_u32` (upper trees) in gp_eval.cu, its
+macros included, into plain text by compiling a small C program that
+prints the same string literal.  `run` interprets that text
 for one lane (each 64-bit stack entry is a pair of float32) over the dozen
 PTX forms the interpreter uses.  `push_pop` is the interpreter's intended
 meaning written plainly: codes read right to left (Sec. 2.2's single-pass
@@ -23,11 +24,14 @@ F = np.float32
 M32 = 0xFFFFFFFF
 
 
-def group_asm(src_path):
+def group_asm(src_path, fn="group_u8"):
+    """The inline-PTX text of `fn` (group_u8: byte codes; group_u32: upper
+    trees, whose value-buffer leaves read staged entries)."""
     s = open(src_path).read()
-    g = s.index("__device__ __forceinline__ int group_u8(")
+    g = s.index(f"__device__ __forceinline__ int {fn}(")
     tmpl = s.rindex("template <uint32_t S>", 0, g)
-    first = min(i for i in (s.find("#define GP_GOPS"), s.find("#define GP_GNODE(")) if i >= 0)
+    marks = ("#define GP_UNODE",) if fn == "group_u32" else ("#define GP_GOPS", "#define GP_GNODE(")
+    first = min(i for i in (s.find(m) for m in marks) if 0 <= i < tmpl)
     a = s.index("asm volatile(", g) + len("asm volatile(")
     b = s.index(': "+l"(tos)', a)
     c_src = ("#include <stdio.h>\n" + s[first:tmpl] + "\nint main(void) { fputs(\n" + s[a:b]
@@ -56,6 +60,17 @@ def parse(text):
             continue
         prog.append(ln.rstrip(";"))
     return prog, labels, tables
+
+
+def _addr(r, expr):
+    """A shared address [a+b*c+...] of registers and immediates."""
+    total = 0
+    for term in expr.strip("[]").split("+"):
+        prod = 1
+        for f in term.split("*"):
+            prod *= _val(r, f)
+        total += prod
+    return total & M32
 
 
 def _val(r, tok):
@@ -105,9 +120,9 @@ def run(parsed, regs, shared, max_steps=100000):
         elif op == "mad.lo.u32":
             r[args[0]] = (v(1) * v(2) + v(3)) & M32
         elif op == "ld.shared.b64":
-            r[args[0]] = shared[_val(r, args[1].strip("[]"))]
+            r[args[0]] = shared[_addr(r, args[1])]
         elif op == "st.shared.b64":
-            shared[_val(r, args[0].strip("[]"))] = v(1)
+            shared[_addr(r, args[0])] = v(1)
         elif op in ("mov.b32", "mov.u32", "mov.s32", "mov.b64"):
             d, s = args
             if d.startswith("{"):
