@@ -396,7 +396,8 @@ gp_status gp_server_submit(gp_server *s, uint64_t run_id, uint32_t n_generations
 /* Wait for a request (timeout_ms < 0: no limit).  GP_ETIMEOUT if it has not
  * completed; otherwise GP_OK with the result (result->status is the
  * request's own outcome), and the request is forgotten: a second wait on it
- * returns GP_EINVAL. */
+ * returns GP_EINVAL, and so does a wait that was already waiting on it when
+ * another thread collected it. */
 gp_status gp_server_wait(gp_server *s, uint64_t request_id, double timeout_ms, gp_server_result *result);
 /* After the run's requests completed: its current population's results / trees. */
 gp_status gp_server_run_fitness(gp_server *s, uint64_t run_id, float *fitness, float *case_values, uint32_t *hits);

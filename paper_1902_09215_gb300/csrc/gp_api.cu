@@ -203,17 +203,6 @@ int sm_count(int dev)
     return v;
 }
 
-cudaError_t prepare_eval_once(int lanes, bool wide, size_t smem)
-{
-    static std::mutex mu;
-    static size_t done[2][33] = {};
-    std::lock_guard<std::mutex> lk(mu);
-    if (done[wide][lanes] >= smem) return cudaSuccess;
-    cudaError_t e = eval_prepare(lanes, wide, smem);
-    if (e == cudaSuccess) done[wide][lanes] = smem;
-    return e;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- population
@@ -666,8 +655,8 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
 {
     const uint32_t C = cfg.C;
     const int lanes = cfg.lanes, sms = cfg.sms;
-    CK(prepare_eval_once(lanes, false, cfg.smem));
-    CK(prepare_eval_once(lanes, true, cfg.smem_u));
+    CK(eval_prepare_at_least(lanes, false, cfg.smem));
+    CK(eval_prepare_at_least(lanes, true, cfg.smem_u));
     DevBufs ws;
     auto body = [&]() -> gp_status {
         // Small and medium trees, largest first (ties in the given order):
@@ -948,8 +937,8 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
 {
     const uint32_t C = cfg.C;
     const int lanes = cfg.lanes, sms = cfg.sms;
-    CK(prepare_eval_once(lanes, false, cfg.smem));
-    CK(prepare_eval_once(lanes, true, std::max(cfg.smem_u, cfg.smem_r)));
+    CK(eval_prepare_at_least(lanes, false, cfg.smem));
+    CK(eval_prepare_at_least(lanes, true, std::max(cfg.smem_u, cfg.smem_r)));
     uint64_t max_items = 0, max_slots = 0, max_ropes = 0;
     for (uint64_t b : P->h_bound) {
         const uint64_t m = (b + C - 1) / C;

@@ -20,6 +20,10 @@
 //     and the operators whose arguments reach past the chunk stay operators.
 //     The upper tree is evaluated by the next launch (recursively if large).
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "gp_internal.cuh"
@@ -202,80 +206,112 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
 
-// The group interpreter below keeps the top of stack `tos` in a register and
-// the rest of the operand stack in this lane's column of the shared window;
-// `t` is the shared address of the next free entry (entries S bytes apart).
+// The byte-code group loop below keeps the top of stack `tos` in a register
+// and the rest of the operand stack in this lane's column of the shared
+// window; `t` is the shared address of the next free entry (entries S bytes
+// apart) and `wb` the window's bottom.
 //   leaf c >= 4 : push tos; tos = table[c] (shared address tb + c*S)
 //   op   c < 4  : tos = tos (op) pop -- tos holds the operator's first
 //                 argument, the popped entry its second
 //   '/' is protected: a zero divisor gives d0.
-// One node of the group interpreter below (code = byte BIT of register w,
-// node index IDX for unique labels).  Operands: %0 tos, %1 t, %7 tb, %11 S.
-//   leaf  : push tos; tos = table[c]
-//   op    : v = pop; tos = tos (op) v; '/' jumps to the shared DIV routine
-#define GP_GNODE(BIT, IDX)                                                       \
-    "bfe.u32 c, w, " #BIT ", 8;\n\t"                                           \
-    "setp.gt.u32 pl, c, 3;\n\t"                                                \
-    "@pl bra.uni LF" #IDX ";\n\t"                                              \
-    "sub.u32 %1, %1, %11;\n\t"                                                 \
-    "ld.shared.b64 v, [%1];\n\t"                                               \
-    "setp.lt.u32 p, c, 2;\n\t"                                                 \
-    "@p bra.uni LO" #IDX ";\n\t"                                               \
-    "setp.eq.u32 p, c, 2;\n\t"                                                 \
-    "@p bra.uni MU" #IDX ";\n\t"                                               \
-    "mov.u32 ret, " #IDX ";\n\t"                                               \
-    "bra.uni DIVR;\n"                                                          \
-    "MU" #IDX ":\n\tmul.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
-    "LO" #IDX ":\n\tsetp.eq.u32 p, c, 0;\n\t@p bra.uni AD" #IDX ";\n\t"          \
-    "sub.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"                          \
-    "AD" #IDX ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #IDX ";\n"              \
-    "LF" #IDX ":\n\tst.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %11;\n\t"          \
-    "mad.lo.u32 a, c, %11, %7;\n\tld.shared.b64 %0, [a];\n"                      \
-    "E" #IDX ":\n\t"
+// A leaf whose next code in the same word is an operator is that
+// operator's first argument: the pair runs as `v = tos; tos = table[c]`
+// followed by the operator without its pop (no stack traffic for the pair).
+//
+// One node at group position K (0..15, read from 15 down), its code in byte
+// K&3 of word register W (prmt selector SEL); NSEL selects the next code of
+// the same word (empty for a word's last node, which does not fuse); KN is
+// the next node's position.  Operands: %0 tos, %1 t, %5 tb, %7 wb, %9 S.
+// An operator that finds the window empty (its second argument lies to the
+// right of what the window holds: spilled entries, or a spine operator of a
+// chunk) leaves with %2 = 16 + K before popping.
+#define GP_BN_HEAD(K, W, SEL)                                                    \
+    "N" #K ":\n\tprmt.b32 c, " W ", z, " SEL ";\n\t"                           \
+    "setp.gt.u32 pl, c, 3;\n\t@pl bra.uni L" #K ";\n\t"                        \
+    "setp.eq.u32 p, %1, %7;\n\t@p bra.uni U" #K ";\n\t"                        \
+    "sub.u32 %1, %1, %9;\n\tld.shared.b64 v, [%1];\n"                          \
+    "P" #K ":\n\tsetp.lt.u32 p, c, 2;\n\t@p bra.uni LO" #K ";\n\t"             \
+    "setp.eq.u32 p, c, 2;\n\t@p bra.uni MU" #K ";\n\t"                         \
+    "mov.u32 ret, " #K ";\n\tbra.uni DIVR;\n"                                  \
+    "MU" #K ":\n\tmul.rn.f32x2 %0, %0, v;\n\tbra.uni E" #K ";\n"                 \
+    "LO" #K ":\n\tsetp.eq.u32 p, c, 0;\n\t@p bra.uni AD" #K ";\n\t"            \
+    "sub.rn.f32x2 %0, %0, v;\n\tbra.uni E" #K ";\n"                            \
+    "AD" #K ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #K ";\n"
+#define GP_BN_FUSE(K, W, SEL, NSEL, KN)                                          \
+    GP_BN_HEAD(K, W, SEL)                                                        \
+    "F" #K ":\n\tmov.b64 v, %0;\n\tld.shared.b64 %0, [a];\n\tbra.uni P" #KN ";\n" \
+    "L" #K ":\n\tmad.lo.u32 a, c, %9, %5;\n\t"                                 \
+    "prmt.b32 c, " W ", z, " NSEL ";\n\tsetp.lt.u32 p, c, 4;\n\t@p bra.uni F" #K ";\n\t" \
+    "st.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %9;\n\tld.shared.b64 %0, [a];\n" \
+    "E" #K ":\n\t"
+#define GP_BN_LAST(K, W, SEL)                                                    \
+    GP_BN_HEAD(K, W, SEL)                                                        \
+    "L" #K ":\n\tmad.lo.u32 a, c, %9, %5;\n\t"                                 \
+    "st.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %9;\n\tld.shared.b64 %0, [a];\n" \
+    "E" #K ":\n\t"
+// Word Q (positions 4Q+3 .. 4Q): it runs only with room for four pushes
+// (t - wb <= %8), else the loop leaves with %2 = 4Q+3.
+#define GP_BW(Q, W, K3, K2, K1, K0)                                              \
+    "W" #Q ":\n\tsub.u32 dd, %1, %7;\n\tsetp.gt.u32 p, dd, %8;\n\t@p bra.uni X" #Q ";\n\t" \
+    GP_BN_FUSE(K3, W, "0x4443", "0x4442", K2)                                    \
+    GP_BN_FUSE(K2, W, "0x4442", "0x4441", K1)                                    \
+    GP_BN_FUSE(K1, W, "0x4441", "0x4440", K0)                                    \
+    GP_BN_LAST(K0, W, "0x4440")
+#define GP_BU(K) "U" #K ":\n\tmov.s32 %2, 16+" #K ";\n\tbra.uni DONE;\n"
 
-// Word entry: leave with %2 = Q unless the window holds >= 4 entries and has
-// room for 4 more (t - lo <= span), then interpret its four codes.
-#define GP_GWORD(Q, REG, I0, I1, I2, I3)                                         \
-    "W" #Q ":\n\tsub.u32 dd, %1, %9;\n\tsetp.gt.u32 p, dd, %10;\n\t"               \
-    "@p bra.uni X" #Q ";\n\tmov.b32 w, " REG ";\n\t"                              \
-    GP_GNODE(24, I0) GP_GNODE(16, I1) GP_GNODE(8, I2) GP_GNODE(0, I3)
-
-// Interprets the codes of one 16-code group (words w3..w0, each read from
-// its high byte down, i.e. right to left in the tree) starting at word q,
-// for as long as each next word can run without checks.  Returns the index
-// of the first word it did not interpret, or -1.  Codes are warp-uniform,
-// so every branch is marked .uni; protected division (a zero divisor gives
-// d0) is one shared routine reached with a return index.
+// Interprets 16-code groups of byte codes from the group at address %3
+// down to the group at %4 (both 16-byte aligned, %3 >= %4), entering the
+// first group at position %2 (a word start enters through its room check).
+// Groups are loaded with 16-byte loads, the next one a group ahead; codes
+// are warp-uniform, so every branch is .uni.  Leaves with %3 = the current
+// group and %2 = -1 (every group done), 4Q+3 (word Q needs room: spill) or
+// 16 + K (the operator at position K found the window empty).
 template <uint32_t S>
-__device__ __forceinline__ int group_u8(uint64_t &tos, uint32_t &t, int q, uint4 w4, uint32_t tb,
-                                        float d0, uint32_t lo, uint32_t span)
+__device__ __forceinline__ int groups_u8(uint64_t &tos, uint32_t &t, const uint8_t *&p, int pos,
+                                         const uint8_t *plo, uint32_t tb, float d0, uint32_t wb,
+                                         uint32_t room)
 {
+    uint64_t pa = reinterpret_cast<uint64_t>(p);
     asm volatile(
-        "{\n\t.reg .pred p, pl;\n\t.reg .b32 c, a, w, ret, dd;\n\t.reg .b64 v;\n\t"
-        ".reg .f32 tx, ty, bx, by, qx, qy;\n\t"
-        "ENT: .branchtargets W0, W1, W2, W3;\n\t"
+        "{\n\t.reg .pred p, pl;\n\t.reg .b32 c, a, ret, dd, z, w0, w1, w2, w3, n0, n1, n2, n3;\n\t"
+        ".reg .b64 v, pn;\n\t.reg .f32 tx, ty, bx, by, qx, qy;\n\t"
+        "mov.b32 z, 0;\n\t"
+        "ld.global.nc.v4.u32 {w0, w1, w2, w3}, [%3];\n\t"
+        "setp.gt.u64 p, %3, %4;\n\tsub.u64 pn, %3, 16;\n\t"
+        "@p ld.global.nc.v4.u32 {n0, n1, n2, n3}, [pn];\n\t"
+        "ENT: .branchtargets N0, N1, N2, W0, N4, N5, N6, W1, N8, N9, N10, W2, N12, N13, N14, W3;\n\t"
         "brx.idx.uni %2, ENT;\n"
-        GP_GWORD(3, "%6", 0, 1, 2, 3)
-        GP_GWORD(2, "%5", 4, 5, 6, 7)
-        GP_GWORD(1, "%4", 8, 9, 10, 11)
-        GP_GWORD(0, "%3", 12, 13, 14, 15)
-        "mov.s32 %2, -1;\n\tbra.uni DONE;\n"
-        "X3:\n\tmov.s32 %2, 3;\n\tbra.uni DONE;\n"
-        "X2:\n\tmov.s32 %2, 2;\n\tbra.uni DONE;\n"
-        "X1:\n\tmov.s32 %2, 1;\n\tbra.uni DONE;\n"
-        "X0:\n\tmov.s32 %2, 0;\n\tbra.uni DONE;\n"
+        GP_BW(3, "w3", 15, 14, 13, 12)
+        GP_BW(2, "w2", 11, 10, 9, 8)
+        GP_BW(1, "w1", 7, 6, 5, 4)
+        GP_BW(0, "w0", 3, 2, 1, 0)
+        "setp.le.u64 p, %3, %4;\n\t@p bra.uni FIN;\n\t"
+        "sub.u64 %3, %3, 16;\n\t"
+        "mov.b32 w0, n0;\n\tmov.b32 w1, n1;\n\tmov.b32 w2, n2;\n\tmov.b32 w3, n3;\n\t"
+        "setp.gt.u64 p, %3, %4;\n\tsub.u64 pn, %3, 16;\n\t"
+        "@p ld.global.nc.v4.u32 {n0, n1, n2, n3}, [pn];\n\t"
+        "bra.uni W3;\n"
+        "FIN:\n\tmov.s32 %2, -1;\n\tbra.uni DONE;\n"
+        "X3:\n\tmov.s32 %2, 15;\n\tbra.uni DONE;\n"
+        "X2:\n\tmov.s32 %2, 11;\n\tbra.uni DONE;\n"
+        "X1:\n\tmov.s32 %2, 7;\n\tbra.uni DONE;\n"
+        "X0:\n\tmov.s32 %2, 3;\n\tbra.uni DONE;\n"
+        GP_BU(0) GP_BU(1) GP_BU(2) GP_BU(3) GP_BU(4) GP_BU(5) GP_BU(6) GP_BU(7)
+        GP_BU(8) GP_BU(9) GP_BU(10) GP_BU(11) GP_BU(12) GP_BU(13) GP_BU(14) GP_BU(15)
         "DIVR:\n\tmov.b64 {tx, ty}, %0;\n\tmov.b64 {bx, by}, v;\n\t"
-        "div.rn.f32 qx, tx, bx;\n\tsetp.neu.f32 p, bx, 0f00000000;\n\tselp.f32 tx, qx, %8, p;\n\t"
-        "div.rn.f32 qy, ty, by;\n\tsetp.neu.f32 p, by, 0f00000000;\n\tselp.f32 ty, qy, %8, p;\n\t"
+        "div.rn.f32 qx, tx, bx;\n\tsetp.neu.f32 p, bx, 0f00000000;\n\tselp.f32 tx, qx, %6, p;\n\t"
+        "div.rn.f32 qy, ty, by;\n\tsetp.neu.f32 p, by, 0f00000000;\n\tselp.f32 ty, qy, %6, p;\n\t"
         "mov.b64 %0, {tx, ty};\n\t"
         "RET: .branchtargets E0, E1, E2, E3, E4, E5, E6, E7, E8, E9, E10, E11, E12, E13, E14, E15;\n\t"
         "brx.idx.uni ret, RET;\n"
         "DONE:\n\t}"
-        : "+l"(tos), "+r"(t), "+r"(q)
-        : "r"(w4.x), "r"(w4.y), "r"(w4.z), "r"(w4.w), "r"(tb), "f"(d0), "r"(lo), "r"(span), "n"(S));
-    return q;
+        : "+l"(tos), "+r"(t), "+r"(pos), "+l"(pa)
+        : "l"(reinterpret_cast<uint64_t>(plo)), "r"(tb), "f"(d0), "r"(wb), "r"(room),
+          "n"(S)
+        : "memory");
+    p = reinterpret_cast<const uint8_t *>(pa);
+    return pos;
 }
-
 
 template <int LANES, typename Code, bool WIDE>
 __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *itp, uint32_t win_sa,
@@ -431,45 +467,57 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
     const uint64_t b = rb, e = re;
     if (e <= b) continue;
     if constexpr (!WIDE) {
-        int64_t gs = (int64_t)((e - 1) & ~15ull);
+        // Byte codes: the group loop runs whole 16-byte groups, from the
+        // item's last group down to its first whole one, and leaves only
+        // where the stack needs the C++ side: before a word without room
+        // for four pushes (spill), at an operator that finds the window
+        // empty (refill, or a spine operator of a chunk), and after the
+        // last group.  A stack without a value (the item's start, after a
+        // spine operator) takes checked steps up to its first leaf.
+        const uint8_t *cb = reinterpret_cast<const uint8_t *>(codes);
         const int64_t glo = (int64_t)(b & ~15ull);
-        Group<Code> cur;
-        cur.load(codes + gs);
-        for (; gs >= glo; gs -= 16) {
-            Group<Code> nxt;                  // the next group's load overlaps this one
-            if (gs - 16 >= glo) nxt.load(codes + gs - 16);
-            const bool full = (uint64_t)gs >= b && (uint64_t)gs + 16 <= e;
-            if (full) {
-                int q = 3;
-                for (;;) {
-                    q = group_u8<S>(tos, t, q, cur.w, tb, d0, fast_lo, fast_span);
-                    if (q < 0) break;
-                    rebalance();
-                    if (fault) break;
-                    if ((t - fast_lo) <= fast_span) continue;     // runnable after all
-                    // Shallow stack (nothing spilled): this word with checks.
-                    if (q < 3) prev = Group<Code>::code(cur.sub(q + 1), 0);
-                    const uint32_t v = cur.sub(q);
-#pragma unroll
-                    for (int k = 3; k >= 0; --k) step_checked(Group<Code>::code(v, k));
-                    if (fault || --q < 0) break;
-                }
-                prev = cur.first();
-            } else {
-#pragma unroll 1
-                for (int q = 3; q >= 0 && !fault; --q) {
-                    const uint32_t v = cur.sub(q);
-                    rebalance();
-                    if (fault) break;
-#pragma unroll
-                    for (int k = 3; k >= 0; --k) {
-                        const uint64_t pos = (uint64_t)gs + 4 * q + k;
-                        if (pos >= b && pos < e) step_checked(Group<Code>::code(v, k));
-                    }
-                }
+        const int64_t gfast = (b & 15) ? glo + 16 : glo;   // lowest group the loop runs
+        int64_t gs = (int64_t)((e - 1) & ~15ull);
+        int pos = (int)((int64_t)(e - 1) - gs);
+        auto code_at = [&](int64_t i) -> uint32_t { return __ldg(cb + i); };
+        const uint32_t room = (uint32_t)(K - 4) * S;
+        while (!fault && gs >= gfast) {
+            if (!have) {
+                step_checked(code_at(gs + pos));
+                if (--pos < 0) { pos = 15; gs -= 16; }
+                continue;
             }
+            if (t - wb > room) {
+                rebalance();
+                if (fault) break;
+            }
+            const uint8_t *pg = cb + gs;
+            const int r = groups_u8<S>(tos, t, pg, pos, cb + gfast, tb, d0, wb, room);
+            gs = (int64_t)(pg - cb);
+            if (r < 0) {                      // every group down to gfast done
+                gs -= 16;
+                pos = 15;
+                break;
+            }
+            if (r < 16) {                     // word at r needs room: spill half the window
+                pos = r;
+                rebalance();
+                continue;
+            }
+            pos = r - 16;                     // operator at pos with an empty window
+            if (g > 0) {                      // its argument was spilled: refill
+                rebalance();
+                continue;
+            }
+            prev = (gs + pos + 1 < (int64_t)e) ? code_at(gs + pos + 1) : 0xFFFFFFFFu;
+            step_checked(code_at(gs + pos));  // spine operator (or a malformed tree)
+            if (--pos < 0) { pos = 15; gs -= 16; }
+        }
+        // codes of an item that starts inside a group
+        for (int64_t i = gs + pos; !fault && i >= (int64_t)b; --i) {
+            rebalance();
             if (fault) break;
-            cur = nxt;
+            step_checked(code_at(i));
         }
     } else {
         // Upper-tree codes: the value entries a group names are copied
@@ -684,23 +732,33 @@ static void *eval_fn_for(int lanes, bool wide)
     }
 }
 
-cudaError_t eval_prepare(int lanes, bool wide, size_t smem)
-{
-    void *fn = eval_fn_for(lanes, wide);
-    if (!fn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-// Raise (never lower) the kernel's dynamic shared-memory limit to `smem`.
+// Raise (never lower) the kernel's dynamic shared-memory limit on the
+// current device to `smem`.  Every launcher goes through here, so a limit
+// only grows: a launch prepared on one host thread stays valid while another
+// thread prepares a smaller one.  One lock covers the check and the set; the
+// record of what was raised is kept per device, like the attribute itself.
 cudaError_t eval_prepare_at_least(int lanes, bool wide, size_t smem)
 {
     void *fn = eval_fn_for(lanes, wide);
     if (!fn) return cudaErrorInvalidValue;
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, fn);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if ((size_t)a.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, size_t> raised;   // (device, kernel) -> limit
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = raised[std::make_pair(dev, lanes * 2 + (wide ? 1 : 0))];
+    if (cur >= smem) return cudaSuccess;
+    cudaFuncAttributes a;
+    e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= smem) {
+        cur = (size_t)a.maxDynamicSharedSizeBytes;
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
 }
 
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,

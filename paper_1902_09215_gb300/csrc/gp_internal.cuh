@@ -117,7 +117,6 @@ void note_launches(uint64_t n);
 
 // Launchers (defined in the .cu files; return the launch's error).
 size_t eval_smem_bytes(int lanes, int warps, int window, bool wide, int leaf_rows = (int)kLeafRows);
-cudaError_t eval_prepare(int lanes, bool wide, size_t smem);
 cudaError_t eval_prepare_at_least(int lanes, bool wide, size_t smem);
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
                         size_t smem, cudaStream_t s);

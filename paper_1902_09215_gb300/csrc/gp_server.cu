@@ -425,12 +425,19 @@ gp_status gp_server_wait(gp_server *S, uint64_t request_id, double timeout_ms, g
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(request_id);
     if (it == S->reqs.end()) return GP_EINVAL;
-    auto done = [&] { return S->reqs[request_id].done; };
+    // A request another waiter collected meanwhile counts as done here (and
+    // is reported as unknown below): looking it up never re-creates it.
+    auto done = [&] {
+        auto f = S->reqs.find(request_id);
+        return f == S->reqs.end() || f->second.done;
+    };
     if (timeout_ms < 0) S->cv_done.wait(lk, done);
     else if (!S->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), done))
         return GP_ETIMEOUT;
-    if (result) *result = S->reqs[request_id].res;
-    S->reqs.erase(request_id);                      // a completed request is collected once
+    it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) return GP_EINVAL;
+    if (result) *result = it->second.res;
+    S->reqs.erase(it);                              // a completed request is collected once
     return GP_OK;
 }
 

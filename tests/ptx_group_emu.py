@@ -2,9 +2,9 @@
 GPU.
 
 `group_asm(path, fn)` expands the hand-written inline-PTX string of
-`group_u8` (byte codes) or `group_u32` (upper trees) in gp_eval.cu, its
-macros included, into plain text by compiling a small C program that
-prints the same string literal.  `run` interprets that text
+`groups_u8` (the byte-code group loop) or `group_u32` (upper trees) in
+gp_eval.cu, its macros included, into plain text by compiling a small C
+program that prints the same string literal.  `run` interprets that text
 for one lane (each 64-bit stack entry is a pair of float32) over the dozen
 PTX forms the interpreter uses.  `push_pop` is the interpreter's intended
 meaning written plainly: codes read right to left (Sec. 2.2's single-pass
@@ -24,13 +24,13 @@ F = np.float32
 M32 = 0xFFFFFFFF
 
 
-def group_asm(src_path, fn="group_u8"):
-    """The inline-PTX text of `fn` (group_u8: byte codes; group_u32: upper
-    trees, whose value-buffer leaves read staged entries)."""
+def group_asm(src_path, fn="groups_u8"):
+    """The inline-PTX text of `fn` (groups_u8: the byte-code group loop;
+    group_u32: upper trees, whose value-buffer leaves read staged entries)."""
     s = open(src_path).read()
     g = s.index(f"__device__ __forceinline__ int {fn}(")
     tmpl = s.rindex("template <uint32_t S>", 0, g)
-    marks = ("#define GP_UNODE",) if fn == "group_u32" else ("#define GP_GOPS", "#define GP_GNODE(")
+    marks = ("#define GP_UNODE",) if fn == "group_u32" else ("#define GP_BN_HEAD",)
     first = min(i for i in (s.find(m) for m in marks) if 0 <= i < tmpl)
     a = s.index("asm volatile(", g) + len("asm volatile(")
     b = s.index(': "+l"(tos)', a)
@@ -79,12 +79,18 @@ def _val(r, tok):
         return r[tok]
     if tok.startswith("0f"):
         return np.frombuffer(int(tok[2:], 16).to_bytes(4, "little"), dtype=F)[0]
-    return int(tok)
+    if "+" in tok:                                  # constant expression, e.g. 16+3
+        return sum(int(x, 0) for x in tok.split("+"))
+    return int(tok, 0)
 
 
-def run(parsed, regs, shared, max_steps=100000):
-    """Interpret parsed PTX; regs maps %0..%11 (and gets the named
-    registers), shared maps byte address -> (float32, float32)."""
+M64 = (1 << 64) - 1
+
+
+def run(parsed, regs, shared, gmem=None, max_steps=100000):
+    """Interpret parsed PTX; regs maps the operands %0.. (and gets the named
+    registers), shared maps byte address -> (float32, float32), gmem maps a
+    16-byte aligned global address -> its 16 bytes."""
     prog, labels, tables = parsed
     r, pc = dict(regs), 0
     for _ in range(max_steps):
@@ -105,6 +111,25 @@ def run(parsed, regs, shared, max_steps=100000):
             pc = labels[tables[args[1]][v(0) & M32]]
         elif op == "bfe.u32":
             r[args[0]] = (v(1) >> v(2)) & ((1 << v(3)) - 1)
+        elif op == "prmt.b32":
+            src = (v(1) & M32) | ((v(2) & M32) << 32)
+            sel = v(3)
+            out = 0
+            for i in range(4):
+                k = (sel >> (4 * i)) & 7
+                out |= ((src >> (8 * k)) & 0xFF) << (8 * i)
+            r[args[0]] = out
+        elif op == "ld.global.nc.v4.u32":
+            dst = [x.strip() for x in args[0].strip("{}").split(",")]
+            blk = gmem[_val(r, args[1].strip("[]"))]
+            for i, d in enumerate(dst):
+                r[d] = int.from_bytes(bytes(blk[4 * i:4 * i + 4]), "little")
+        elif op == "sub.u64":
+            r[args[0]] = (v(1) - v(2)) & M64
+        elif op.startswith("setp.") and op.endswith(".u64"):
+            _, cmp, _ = op.split(".")
+            a, b = v(1) & M64, v(2) & M64
+            r[args[0]] = {"gt": a > b, "le": a <= b, "lt": a < b, "eq": a == b}[cmp]
         elif op.startswith("setp."):
             _, cmp, ty = op.split(".")
             a, b = v(1), v(2)

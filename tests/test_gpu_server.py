@@ -259,3 +259,31 @@ def test_closing_a_waiting_run_fails_its_requests(gpu):
     assert gpu.gp_server_wait(srv, qb)["status"] == gpu.GP_EINVAL
     gpu.gp_server_close_run(srv, a)
     gpu.gp_server_destroy(srv)
+
+
+def test_two_waiters_on_one_request(gpu):
+    """Two threads wait on the same request: one collects its result, the
+    other is told the request is unknown (GP_EINVAL); neither hangs."""
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs, seed = make_runs(1, hi=4001)[0]
+    srv = gpu.gp_server_create(prob, hbm_budget_bytes=1 << 30, max_runs=2, chunk_nodes=4096)
+    rid = gpu.gp_server_open_run(srv, nodes, offs, seed=seed)
+    q = gpu.gp_server_submit(srv, rid, 3)
+    outcome = []
+
+    def waiter():
+        try:
+            outcome.append(gpu.gp_server_wait(srv, q, timeout_ms=60000)["status"])
+        except gpu.GpError as e:
+            outcome.append(e.status)
+
+    th = [threading.Thread(target=waiter) for _ in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=120)
+    assert not any(t.is_alive() for t in th)
+    assert sorted(outcome) == sorted([gpu.GP_OK, gpu.GP_EINVAL])
+    gpu.gp_server_close_run(srv, rid)
+    gpu.gp_server_destroy(srv)

@@ -1,11 +1,11 @@
 """The evaluator's group interpreters (hand-written inline PTX in
-gp_eval.cu: byte codes, and the upper trees' 32-bit codes whose
-value-buffer leaves read staged entries), run on the CPU by a model of the
-PTX forms they use, against
-its plain push/pop meaning (Sec. 2.2 EVAL read right to left; protected
-division of Table gp.details) on random 16-code groups: operator mixes,
-stack depths that make words exit early, NaN, signed zeros, subnormals and
-zero divisors.  No GPU: this checks the interpreter's control flow (labels,
+gp_eval.cu: the byte-code group loop, and the upper trees' 32-bit codes
+whose value-buffer leaves read staged entries), run on the CPU by a model
+of the PTX forms they use, against their plain push/pop meaning (Sec. 2.2
+EVAL read right to left; protected division of Table gp.details) on random
+groups: operator mixes, leaf-operator pairs, entries at every position,
+stack depths that make words stop for room and operators that find the
+window empty, NaN, signed zeros, subnormals and zero divisors.  No GPU: this checks the interpreter's control flow (labels,
 branches, the divide routine's return index, the window checks) bit for
 bit; the GPU parity tests check the compiled kernel."""
 import os
@@ -59,9 +59,55 @@ def same(a, b):
                for x, y in zip(a, b))
 
 
-def one_group(parsed, rng):
-    """Run one random group through the PTX model and the plain meaning;
-    returns None when they agree, else a description."""
+GBASE = 0x40000                      # global address of the lowest group of the byte-code loop
+ROOM = (K - 4) * S                   # a word of the byte-code loop runs with room for 4 pushes
+
+
+def loop_meaning(groups, pos, tos, t, d0, shared):
+    """The byte-code group loop's meaning: groups[g] holds the 16 codes of
+    the group at GBASE + 16 g (code j at position j); reading starts at
+    position `pos` of the highest group and goes right to left, group after
+    group.  A word start reached on the way (and the entry itself, if it
+    is one) needs room for four pushes, else the loop stops there (exit
+    4Q+3); an operator that finds the window empty stops before popping
+    (exit 16 + position); after the lowest group the exit is -1."""
+    sh = dict(shared)
+    g = len(groups) - 1
+    j = pos
+    while True:
+        while j >= 0:
+            if j % 4 == 3 and ((t - WB) & M32) > ROOM:
+                return j, g, tos, t, sh
+            c = groups[g][j]
+            if c > 3:
+                sh[t] = tos
+                t += S
+                tos = sh[TB + c * S]
+            else:
+                if t == WB:
+                    return 16 + j, g, tos, t, sh
+                t -= S
+                v = sh[t]
+                with np.errstate(all="ignore"):
+                    if c == 0:
+                        tos = (F(tos[0] + v[0]), F(tos[1] + v[1]))
+                    elif c == 1:
+                        tos = (F(tos[0] - v[0]), F(tos[1] - v[1]))
+                    elif c == 2:
+                        tos = (F(tos[0] * v[0]), F(tos[1] * v[1]))
+                    else:
+                        tos = tuple(F(a / b) if (np.isnan(b) or b != 0) else F(d0) for a, b in zip(tos, v))
+            j -= 1
+        if g == 0:
+            return -1, 0, tos, t, sh
+        g -= 1
+        j = 15
+
+
+def one_loop(parsed, rng):
+    """Run the byte-code group loop on 1..3 random groups through the PTX
+    model and its plain meaning; returns None when they agree, else a
+    description."""
     pool = [F(0.0), F(-0.0), F(1.0), F(np.nan), F(2.5e-40), F(-3.0)]
 
     def rv():
@@ -72,25 +118,26 @@ def one_group(parsed, rng):
         shared[WB + k * S] = (rv(), rv())
     t = WB + int(rng.integers(0, K + 1)) * S
     p_op = rng.uniform(0.2, 0.8)
-    codes = [int(rng.integers(0, 4)) if rng.random() < p_op else int(rng.integers(4, 132)) for _ in range(16)]
-    words = [0, 0, 0, 0]
-    for wi in range(4):
-        for k, bit in enumerate((24, 16, 8, 0)):
-            words[3 - wi] |= codes[4 * wi + k] << bit
-    q, tos, d0 = int(rng.integers(0, 4)), (rv(), rv()), F(1.0)
-    regs = {"%0": tos, "%1": t, "%2": q, "%3": words[0], "%4": words[1], "%5": words[2], "%6": words[3],
-            "%7": TB, "%8": d0, "%9": LO, "%10": SPAN, "%11": S}
+    n = int(rng.integers(1, 4))
+    groups = [[int(rng.integers(0, 4)) if rng.random() < p_op else int(rng.integers(4, 132)) for _ in range(16)]
+              for _ in range(n)]
+    gmem = {GBASE + 16 * g: bytes(groups[g]) for g in range(n)}
+    pos, tos, d0 = int(rng.integers(0, 16)), (rv(), rv()), F(1.0)
+    if pos % 4 != 3 and t - WB > (K - 3) * S:       # mid-word entries come with room for the word
+        t = WB + (K - 3) * S
+    regs = {"%0": tos, "%1": t, "%2": pos, "%3": GBASE + 16 * (n - 1), "%4": GBASE, "%5": TB, "%6": d0,
+            "%7": WB, "%8": ROOM, "%9": S}
     got_sh = dict(shared)
-    r = run(parsed, regs, got_sh)
-    w_tos, w_t, w_q, w_sh = push_pop(
-        lambda qq: [((words[qq] >> bit) & 0xFF, None) for bit in (24, 16, 8, 0)],
-        lambda c, j, sh: sh[TB + c * S], q, tos, t, d0, shared)
-    q_out = r["%2"] - (1 << 32) if r["%2"] > 0x7FFFFFFF else r["%2"]
-    if not same(r["%0"], w_tos) or r["%1"] != w_t or q_out != w_q:
-        return f"codes {codes} from word {q}: tos {r['%0']} vs {w_tos}, t {r['%1']} vs {w_t}, q {q_out} vs {w_q}"
+    r = run(parsed, regs, got_sh, gmem)
+    w_x, w_g, w_tos, w_t, w_sh = loop_meaning(groups, pos, tos, t, d0, shared)
+    x_out = r["%2"] - (1 << 32) if r["%2"] > 0x7FFFFFFF else r["%2"]
+    g_out = (r["%3"] - GBASE) // 16
+    if not same(r["%0"], w_tos) or r["%1"] != w_t or x_out != w_x or g_out != w_g:
+        return (f"groups {groups} from {pos}: tos {r['%0']} vs {w_tos}, t {r['%1']} vs {w_t}, "
+                f"exit {x_out} vs {w_x}, group {g_out} vs {w_g}")
     for addr in range(WB, w_t, S):                   # the live stack
         if not same(got_sh[addr], w_sh[addr]):
-            return f"codes {codes}: stack entry {(addr - WB) // S} differs"
+            return f"groups {groups}: stack entry {(addr - WB) // S} differs"
     return None
 
 
@@ -99,21 +146,32 @@ def parsed():
     return parse(group_asm(SRC))
 
 
-def test_group_interpreter_matches_push_pop(parsed):
+def test_group_loop_matches_push_pop(parsed):
     rng = np.random.default_rng(2019)
-    for _ in range(1000):
-        bad = one_group(parsed, rng)
+    for _ in range(1500):
+        bad = one_loop(parsed, rng)
         assert bad is None, bad
 
 
 def test_model_catches_a_planted_operand_swap(parsed):
     """The comparison has teeth: with the operands of one subtraction
-    swapped in the PTX text, some group disagrees."""
+    swapped in the PTX text, some run disagrees."""
     text = group_asm(SRC)
     planted = text.replace("sub.rn.f32x2 %0, %0, v;", "sub.rn.f32x2 %0, v, %0;", 1)
     assert planted != text
     rng = np.random.default_rng(7)
-    assert any(one_group(parse(planted), rng) for _ in range(300))
+    assert any(one_loop(parse(planted), rng) for _ in range(300))
+
+
+def test_model_catches_a_planted_fused_operand_order(parsed):
+    """A leaf fused with the operator after it is that operator's first
+    argument: loading the leaf into the popped register instead swaps the
+    operands of the pair, and some run disagrees."""
+    text = group_asm(SRC)
+    planted = text.replace("mov.b64 v, %0;\n\tld.shared.b64 %0, [a];", "ld.shared.b64 v, [a];", 1)
+    assert planted != text
+    rng = np.random.default_rng(11)
+    assert any(one_loop(parse(planted), rng) for _ in range(300))
 
 
 STAGE = 0x200000                     # staged value entries of the group: STAGE + position * S

@@ -115,3 +115,48 @@ def test_noalloc_errors_then_recovers(gpu):
     assert same_f32(d_vals.cpu().numpy(), vals)
     assert same_f32(d_fit.cpu().numpy(), fit)
     assert np.array_equal(d_hits.cpu().numpy().astype(np.uint32), hits)
+
+
+def test_noalloc_beside_another_thread_evaluating(gpu):
+    """gp_evaluate_noalloc on one host thread while a second thread evaluates
+    through gp_evaluate with a launch that needs less shared memory: the
+    evaluator's shared-memory limit is only ever raised, so neither thread's
+    launches fail and both stay exact."""
+    import threading
+
+    import torch
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = population(43, 200, 4095)
+    fit, vals, hits = reference(gpu, prob, nodes, offs)
+    errors = []
+
+    def other():
+        try:
+            torch.cuda.set_device(0)
+            s = torch.cuda.Stream()
+            pop = gpu.gp_create_population(prob, nodes, offs, s)
+            for _ in range(40):
+                gpu.gp_evaluate(pop, s, warps_per_cta=4, window_entries=16)
+                f, _, _ = gpu.gp_fitness(pop)
+                if not same_f32(f, fit):
+                    errors.append("fitness of the allocating path")
+            gpu.gp_destroy_population(pop)
+        except Exception as e:                        # reported below
+            errors.append(repr(e))
+
+    th = threading.Thread(target=other)
+    th.start()
+    s = torch.cuda.Stream()
+    d_nodes, d_fit, d_vals, d_hits = device_buffers(nodes, offs, 48)
+    try:
+        for _ in range(40):
+            gpu.gp_evaluate_noalloc(prob, offs, d_nodes.data_ptr(), d_fit.data_ptr(), d_vals.data_ptr(),
+                                    d_hits.data_ptr(), s)
+            s.synchronize()
+            assert same_f32(d_fit.cpu().numpy(), fit)
+    finally:
+        th.join(timeout=300)
+    assert not th.is_alive() and not errors, errors
+    assert same_f32(d_vals.cpu().numpy(), vals)
+    assert np.array_equal(d_hits.cpu().numpy().astype(np.uint32), hits)
