@@ -214,38 +214,23 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 //   op   c < 4  : tos = tos (op) pop -- tos holds the operator's first
 //                 argument, the popped entry its second
 //   '/' is protected: a zero divisor gives d0.
-// A leaf whose next code in the same word is an operator is that
-// operator's first argument: the pair runs as `v = tos; tos = table[c]`
-// followed by the operator without its pop (no stack traffic for the pair).
-//
 // One node at group position K (0..15, read from 15 down), its code in byte
-// K&3 of word register W (prmt selector SEL); NSEL selects the next code of
-// the same word (empty for a word's last node, which does not fuse); KN is
-// the next node's position.  Operands: %0 tos, %1 t, %5 tb, %7 wb, %9 S.
-// An operator that finds the window empty (its second argument lies to the
-// right of what the window holds: spilled entries, or a spine operator of a
-// chunk) leaves with %2 = 16 + K before popping.
-#define GP_BN_HEAD(K, W, SEL)                                                    \
+// K&3 of word register W (prmt selector SEL).  Operands: %0 tos, %1 t,
+// %5 tb, %7 wb, %9 S.  An operator that finds the window empty (its second
+// argument lies to the right of what the window holds: spilled entries, or
+// a spine operator of a chunk) leaves with %2 = 16 + K before popping.
+#define GP_BN(K, W, SEL)                                                         \
     "N" #K ":\n\tprmt.b32 c, " W ", z, " SEL ";\n\t"                           \
     "setp.gt.u32 pl, c, 3;\n\t@pl bra.uni L" #K ";\n\t"                        \
     "setp.eq.u32 p, %1, %7;\n\t@p bra.uni U" #K ";\n\t"                        \
-    "sub.u32 %1, %1, %9;\n\tld.shared.b64 v, [%1];\n"                          \
-    "P" #K ":\n\tsetp.lt.u32 p, c, 2;\n\t@p bra.uni LO" #K ";\n\t"             \
+    "sub.u32 %1, %1, %9;\n\tld.shared.b64 v, [%1];\n\t"                        \
+    "setp.lt.u32 p, c, 2;\n\t@p bra.uni LO" #K ";\n\t"                         \
     "setp.eq.u32 p, c, 2;\n\t@p bra.uni MU" #K ";\n\t"                         \
     "mov.u32 ret, " #K ";\n\tbra.uni DIVR;\n"                                  \
     "MU" #K ":\n\tmul.rn.f32x2 %0, %0, v;\n\tbra.uni E" #K ";\n"                 \
     "LO" #K ":\n\tsetp.eq.u32 p, c, 0;\n\t@p bra.uni AD" #K ";\n\t"            \
     "sub.rn.f32x2 %0, %0, v;\n\tbra.uni E" #K ";\n"                            \
-    "AD" #K ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #K ";\n"
-#define GP_BN_FUSE(K, W, SEL, NSEL, KN)                                          \
-    GP_BN_HEAD(K, W, SEL)                                                        \
-    "F" #K ":\n\tmov.b64 v, %0;\n\tld.shared.b64 %0, [a];\n\tbra.uni P" #KN ";\n" \
-    "L" #K ":\n\tmad.lo.u32 a, c, %9, %5;\n\t"                                 \
-    "prmt.b32 c, " W ", z, " NSEL ";\n\tsetp.lt.u32 p, c, 4;\n\t@p bra.uni F" #K ";\n\t" \
-    "st.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %9;\n\tld.shared.b64 %0, [a];\n" \
-    "E" #K ":\n\t"
-#define GP_BN_LAST(K, W, SEL)                                                    \
-    GP_BN_HEAD(K, W, SEL)                                                        \
+    "AD" #K ":\n\tadd.rn.f32x2 %0, %0, v;\n\tbra.uni E" #K ";\n"                 \
     "L" #K ":\n\tmad.lo.u32 a, c, %9, %5;\n\t"                                 \
     "st.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %9;\n\tld.shared.b64 %0, [a];\n" \
     "E" #K ":\n\t"
@@ -253,10 +238,7 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 // (t - wb <= %8), else the loop leaves with %2 = 4Q+3.
 #define GP_BW(Q, W, K3, K2, K1, K0)                                              \
     "W" #Q ":\n\tsub.u32 dd, %1, %7;\n\tsetp.gt.u32 p, dd, %8;\n\t@p bra.uni X" #Q ";\n\t" \
-    GP_BN_FUSE(K3, W, "0x4443", "0x4442", K2)                                    \
-    GP_BN_FUSE(K2, W, "0x4442", "0x4441", K1)                                    \
-    GP_BN_FUSE(K1, W, "0x4441", "0x4440", K0)                                    \
-    GP_BN_LAST(K0, W, "0x4440")
+    GP_BN(K3, W, "0x4443") GP_BN(K2, W, "0x4442") GP_BN(K1, W, "0x4441") GP_BN(K0, W, "0x4440")
 #define GP_BU(K) "U" #K ":\n\tmov.s32 %2, 16+" #K ";\n\tbra.uni DONE;\n"
 
 // Interprets 16-code groups of byte codes from the group at address %3

@@ -30,7 +30,7 @@ def group_asm(src_path, fn="groups_u8"):
     s = open(src_path).read()
     g = s.index(f"__device__ __forceinline__ int {fn}(")
     tmpl = s.rindex("template <uint32_t S>", 0, g)
-    marks = ("#define GP_UNODE",) if fn == "group_u32" else ("#define GP_BN_HEAD",)
+    marks = ("#define GP_UNODE",) if fn == "group_u32" else ("#define GP_BN(",)
     first = min(i for i in (s.find(m) for m in marks) if 0 <= i < tmpl)
     a = s.index("asm volatile(", g) + len("asm volatile(")
     b = s.index(': "+l"(tos)', a)

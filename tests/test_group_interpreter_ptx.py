@@ -3,7 +3,7 @@ gp_eval.cu: the byte-code group loop, and the upper trees' 32-bit codes
 whose value-buffer leaves read staged entries), run on the CPU by a model
 of the PTX forms they use, against their plain push/pop meaning (Sec. 2.2
 EVAL read right to left; protected division of Table gp.details) on random
-groups: operator mixes, leaf-operator pairs, entries at every position,
+groups: operator mixes, entries at every position,
 stack depths that make words stop for room and operators that find the
 window empty, NaN, signed zeros, subnormals and zero divisors.  No GPU: this checks the interpreter's control flow (labels,
 branches, the divide routine's return index, the window checks) bit for
@@ -160,17 +160,6 @@ def test_model_catches_a_planted_operand_swap(parsed):
     planted = text.replace("sub.rn.f32x2 %0, %0, v;", "sub.rn.f32x2 %0, v, %0;", 1)
     assert planted != text
     rng = np.random.default_rng(7)
-    assert any(one_loop(parse(planted), rng) for _ in range(300))
-
-
-def test_model_catches_a_planted_fused_operand_order(parsed):
-    """A leaf fused with the operator after it is that operator's first
-    argument: loading the leaf into the popped register instead swaps the
-    operands of the pair, and some run disagrees."""
-    text = group_asm(SRC)
-    planted = text.replace("mov.b64 v, %0;\n\tld.shared.b64 %0, [a];", "ld.shared.b64 v, [a];", 1)
-    assert planted != text
-    rng = np.random.default_rng(11)
     assert any(one_loop(parse(planted), rng) for _ in range(300))
 
 
