@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -60,6 +61,12 @@ def max_over_ranks(x: float, world: int, device) -> float:
 def weak_scaling_value(units_per_rank: float, world: int, max_ms: float) -> float:
     """Whole-job throughput: every rank's units over the slowest rank's time."""
     return units_per_rank * world / (max_ms / 1e3)
+
+
+def nearest_rank(values, q: float) -> float:
+    """The q-quantile by the nearest-rank rule: the ceil(q n)-th smallest."""
+    srt = sorted(values)
+    return srt[max(0, min(len(srt) - 1, math.ceil(q * len(srt)) - 1))]
 
 
 def make_workload(rank: int):
@@ -191,9 +198,13 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         parents = gp.gp_create_population(prob, nodes, offs, stream)
 
+    redo_in_step = [False]
+
     def step():
         kids = gp.gp_crossover(parents, xo, stream)
         gp.gp_evaluate(kids, stream)
+        if redo_in_step[0]:              # trees deferred to gp_fitness are part of the step
+            gp.gp_fitness(kids)
         return kids
 
     def barrier():
@@ -211,19 +222,27 @@ def run_ours(args):
         # alive at once as in the timed loop, so the memory pool is at its
         # working size before timing starts
         keep = []
-        for _ in range(args.warmup):
-            keep.append(step())
-            gp.gp_fitness(keep[-1])
+        for _ in range(args.warmup):         # the timed loop's pattern: no wait between steps
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                keep.append(step())
             if len(keep) > 1:
                 keep.pop(0)
+        barrier()
+        gp.gp_fitness(keep[-1])
         child_nodes = int(gp.gp_population_get_info(keep[-1]).total_nodes)
         stats = gp.gp_eval_stats_get(keep[-1])
+        # gp_evaluate leaves trees whose chunk fragments overflowed their
+        # slots to gp_fitness; the children are the same every step, so if
+        # any were deferred the timed step waits for gp_fitness too
+        redo_in_step[0] = stats["redone"] > 0
         keep.clear()
 
         # ---- timed: K steps, L2 flushed before each, device time per step
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         keep = []
+        host_ms = []
         barrier()
         launches0 = gp.gp_kernel_launch_count()
         t0 = time.perf_counter()
@@ -231,7 +250,9 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 flush.zero_()
                 ev[k][0].record(stream)
+                h = time.perf_counter()
                 keep.append(step())
+                host_ms.append(1e3 * (time.perf_counter() - h))
                 ev[k][1].record(stream)
             if len(keep) > 1:                # freed in stream order after its step
                 keep.pop(0)
@@ -279,8 +300,13 @@ def run_ours(args):
     ev0 = prof["eval"]
     eval_launch_ms = ev0["ms"] / max(ev0["launches"], 1)
     # algorithmic work of one evaluation: (n-1)/2 binary FP32 operations per
-    # tree per case; the level-0 launch does all but the deferred spine ops
-    n_bin_ops = (child_nodes - N_TREES) // 2 * prob.n_cases
+    # tree per case; the level-0 launch does all but the spine operators it
+    # sends up to the ropes (gp_eval_stats: upper_ops), which the rope
+    # launch does
+    upper_ops = int(stats["upper_ops"])
+    n_bin_ops = ((child_nodes - N_TREES) // 2 - upper_ops) * prob.n_cases
+    up = prof.get("eval_upper", {"ms": 0.0, "launches": 0})
+    rope_launch_ms = up["ms"] / up["launches"] if up["launches"] else None
     peaks, peak_src = measured_peaks()
     clocks = clk.summary()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -331,7 +357,11 @@ def run_ours(args):
 
     cpu = cpu_baseline(nodes, offs, ops, x, y, c, child_nodes) if world == 1 and not args.no_cpu else None
     batched = batched_compare(gp, prob, nodes, offs, stream, flush, max(10, args.steps // 10)) if world == 1 else None
-    step_sorted = sorted(step_ms)
+    configs = None
+    if world == 1 and not args.no_extra:
+        # the benchmark's other configurations, each measured once here
+        configs = {"smallest_50_trees": config1_latency(gp, prob, stream, 300, not args.no_cpu),
+                   "bloated_48_trees": config3_bloated(gp, prob, stream, not args.no_cpu)}
     line = {
         "metric": METRIC,
         "value": value,
@@ -353,10 +383,13 @@ def run_ours(args):
             "parallelism": f"replicas x{world} (independent populations)",
             "eval_levels": stats["levels"], "eval_items": stats["items"],
         },
-        "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
-                       "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))],
+        "latency_ms": {"p50": nearest_rank(step_ms, 0.5), "p99": nearest_rank(step_ms, 0.99),
+                       "rule": f"nearest rank over {len(step_ms)} timed steps",
                        "max": max(step_ms), "slowest_step": int(step_ms.index(max(step_ms))),
-                       "first_step": step_ms[0]},
+                       "first_step": step_ms[0],
+                       "host_enqueue_ms": {"p50": nearest_rank(host_ms, 0.5), "max": max(host_ms),
+                                           "slowest_step": int(host_ms.index(max(host_ms)))}},
+        "redone_trees": int(stats["redone"]),
         "eval_only": {"value": child_nodes * prob.n_cases / (statistics.median(eval_ms) / 1e3),
                       "unit": "GPops/s", "ms_p50": statistics.median(eval_ms)},
         "crossover": {"ms_p50": statistics.median(xo_ms),
@@ -369,8 +402,14 @@ def run_ours(args):
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "peak_note": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_src} max clock); "
-                                  "achieved = (n-1)/2 binary ops x 48 cases per tree / mean launch time",
+                                  "achieved = the binary ops x 48 cases level 0 performs ((n-1)/2 per tree "
+                                  "less the spine operators it sends to the ropes) / mean launch time",
                      "launch_ms": eval_launch_ms, "launches_profiled": ev0["launches"], "issue": issue,
+                     "rope_launch": None if rope_launch_ms is None else {
+                         "kernel": "eval_kernel (ropes)", "ops": upper_ops * prob.n_cases,
+                         "launch_ms": rope_launch_ms,
+                         "achieved": upper_ops * prob.n_cases / (rope_launch_ms / 1e3) / 1e12,
+                         "frac": upper_ops * prob.n_cases / (rope_launch_ms / 1e3) / 1e12 / alu_peak},
                      "kernel_ms_per_launch": {k: v["ms"] / v["launches"] for k, v in prof.items() if v["launches"]},
                      "kernel_share": {k: v["ms"] / tot_ms for k, v in prof.items() if v["launches"]}},
         "wall_s": wall,
@@ -379,6 +418,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu
     if batched:
         line["batched_vs_plain"] = batched
+    if configs:
+        line["configs"] = configs
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -464,6 +505,139 @@ def cpu_baseline(nodes, offs, ops, x, y, c, child_nodes):
             "single_core": {"value": one_nodes * len(x) / el1, "unit": "GPops/s", "cores": 1,
                             "sample": f"{one_reps} x oracle evaluation of the children of the first "
                                       f"{one} records on 1 thread, {el1:.1f} s"}}
+
+
+def config1_latency(gp, prob, stream, reps, cpu):
+    """The smallest workload (50 trees of 1..63 nodes): it is launch-bound,
+    so what counts is the time of one evaluation call, on the device (CUDA
+    events around gp_evaluate) and through the API (gp_evaluate plus the
+    gp_fitness that waits for it and copies the 50 fitness values back)."""
+    import torch
+    nodes, offs = synth.population_small(seed=1)
+    x, y, c = prob.x, prob.y, prob.consts
+    pop = gp.gp_create_population(prob, nodes, offs, stream)
+    for _ in range(20):
+        gp.gp_evaluate(pop, stream)
+        gp.gp_fitness(pop)
+    dev, wall = [], []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        a.record(stream)
+        gp.gp_evaluate(pop, stream)
+        b.record(stream)
+        gp.gp_fitness(pop)
+        wall.append(1e6 * (time.perf_counter() - t))
+        dev.append(1e3 * a.elapsed_time(b))
+    gp.gp_destroy_population(pop)
+    n = int(offs[-1])
+    out = {"workload": "50 seeded random trees, odd sizes uniform on 1..63 (seed 1), 48 cases; one evaluation",
+           "nodes": n, "device_us_p50": nearest_rank(dev, 0.5), "device_us_p99": nearest_rank(dev, 0.99),
+           "call_us_p50": nearest_rank(wall, 0.5), "call_us_p99": nearest_rank(wall, 0.99),
+           "rule": f"nearest rank over {reps} calls",
+           "GPops_per_s_call": n * prob.n_cases / (nearest_rank(wall, 0.5) / 1e6)}
+    if cpu:
+        from oracle import oracle
+        t = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t < 2.0:
+            oracle.eval_population(nodes, offs, x, y, c, n_threads=1)
+            k += 1
+        el = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": 1e6 * el / k, "unit": "us per evaluation", "cores": 1, "kind": "oracle",
+                               "sample": f"{k} oracle evaluations of the 50 trees on 1 thread, {el:.1f} s"}
+    return out
+
+
+def config3_bloated(gp, prob, stream, cpu):
+    """The 48 bloated trees (odd sizes log-uniform 1e6..4e8, 4.47e9 nodes, the
+    largest grown into a stringy chain of depth above 1e5): every tree is cut
+    into chunks and its upper trees are planned level by level.  Device time
+    of gp_evaluate (the levels' host synchronisations included), the
+    level-0 launches against the FP32 lane peak, and end to end from pinned
+    host memory (upload and validation, evaluation, fitness read-back)."""
+    import torch
+    x, y, c = prob.x, prob.y, prob.consts
+    t0 = time.perf_counter()
+    nodes, offs, info = synth.graft_population(seed=4)
+    build_s = time.perf_counter() - t0
+    n_trees = offs.shape[0] - 1
+    n = int(offs[-1])
+    pop = gp.gp_create_population(prob, nodes, offs, stream)
+    gp.gp_evaluate(pop, stream)
+    gp.gp_fitness(pop)
+    gp.gp_profile_read(reset=True)
+    gp.gp_profile_enable(True)
+    ms = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        gp.gp_evaluate(pop, stream)
+        b.record(stream)
+        gp.gp_fitness(pop)
+        ms.append(a.elapsed_time(b))
+    gp.gp_profile_enable(False)
+    prof = gp.gp_profile_read(reset=True)
+    st = gp.gp_eval_stats_get(pop)
+    gp.gp_destroy_population(pop)
+    eval_ms = statistics.median(ms)
+    l0 = prof["eval"]
+    l0_ms = l0["ms"] / max(l0["launches"], 1)
+    l0_ops = ((n - n_trees) // 2 - int(st["upper_ops"])) * prob.n_cases
+    peaks, src = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = n_sm * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    # end to end: the trees from pinned host memory, through the public API
+    pin = torch.from_numpy(nodes).pin_memory()
+    pin_offs = torch.from_numpy(offs.astype(np.uint64).view(np.int64)).pin_memory()
+    del nodes
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    p2 = gp.gp_create_population(prob, pin.numpy(), pin_offs.numpy().view(np.uint64), stream)
+    gp.gp_evaluate(p2, stream)
+    gp.gp_fitness(p2)
+    e2e_s = time.perf_counter() - t
+    gp.gp_destroy_population(p2)
+    out = {"workload": "48 bloated trees (seed 4), odd sizes log-uniform 1e6..4e8 grown by subtree-crossover "
+                       "chains, the largest a stringy chain of depth above 1e5; 48 cases; one evaluation",
+           "nodes": n, "depth_of_chain_tree": int(info["chain_depth"]), "population_build_s": build_s,
+           "value": n * prob.n_cases / (eval_ms / 1e3), "unit": "GPops/s", "ms_p50": eval_ms, "runs": len(ms),
+           "levels": int(st["levels"]), "items": int(st["items"]),
+           "kernel_ms": {k: v["ms"] / len(ms) for k, v in prof.items() if v["launches"]},
+           "roofline": {"bound": "alu", "kernel": "eval_kernel (level 0)", "launches": l0["launches"] // len(ms),
+                        "achieved": l0_ops / (l0_ms / 1e3) / 1e12 if l0["launches"] else None,
+                        "peak": alu_peak, "unit": "TFLOP/s",
+                        "frac": l0_ops / (l0_ms / 1e3) / 1e12 / alu_peak if l0["launches"] else None,
+                        "peak_note": f"{n_sm} SMs x 128 FP32 lanes x max clock ({src})"},
+           "e2e": {"value": n * prob.n_cases / e2e_s, "unit": "GPops/s", "h2d_bytes_per_step": int(n + 8 * (n_trees + 1)),
+                   "d2h_bytes_per_step": 4 * n_trees, "wall_s": e2e_s}}
+    if cpu:
+        from oracle import oracle
+        sizes = np.diff(offs.astype(np.int64))
+        order = np.argsort(sizes)
+        pick, tot = [], 0
+        for t_ in order:
+            if len(pick) >= 16 and tot > 2 * 10 ** 7:
+                break
+            pick.append(int(t_))
+            tot += int(sizes[t_])
+        sub = np.concatenate([pin.numpy()[int(offs[t_]):int(offs[t_ + 1])] for t_ in pick])
+        so = np.zeros(len(pick) + 1, np.uint64)
+        np.cumsum(sizes[pick].astype(np.uint64), out=so[1:])
+        cores = os.cpu_count() or 1
+        t = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t < 10.0:
+            oracle.eval_population(sub, so, x, y, c, n_threads=cores)
+            k += 1
+        el = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": k * tot * prob.n_cases / el, "unit": "GPops/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{k} x oracle evaluation of the {len(pick)} smallest trees "
+                                         f"({tot} nodes) on {cores} threads, {el:.1f} s"}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -634,7 +808,6 @@ def run_batched(args):
 
     med = statistics.median(ms)
     units = child_nodes * len(x)
-    srt = sorted(ms)
     line = {
         "metric": "GPops/s (tree nodes x fitness cases per second), batched generation",
         "value": units / (med / 1e3), "unit": "GPops/s", "n_gpus": 1, "steps": args.steps,
@@ -647,7 +820,7 @@ def run_batched(args):
                    "kernels_per_generation": info0["kernels_per_generation"],
                    "arena_bytes": arena, "workspace": [info0["workspace_codes"], info0["workspace_values"]],
                    "population_build_s": gen_s, "create_s": create_s},
-        "latency_ms": {"p50": med, "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "latency_ms": {"p50": med, "p99": nearest_rank(ms, 0.99), "rule": f"nearest rank over {len(ms)} steps"},
         "autotune": {str(k): v for k, v in zip(info0["autotune_chunk"], info0["autotune_ms"]) if k},
         "clocks": clk.summary(),
         "e2e": {"value": units / statistics.median(te), "unit": "GPops/s", "h2d_bytes_per_step": 0,
@@ -856,6 +1029,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="time the 4000-tree step only (not the benchmark's other configurations)")
     ap.add_argument("--serve-gens", type=int, default=10, help="generations per run in the serving workload")
     ap.add_argument("--generations", type=int, default=200, help="generations of the ltee workload")
     ap.add_argument("--time-limit", type=float, default=120.0,

@@ -166,15 +166,19 @@ const char *gp_status_string(gp_status st);
 
 /* Shape of the last gp_evaluate of a population: evaluation levels (1 when
  * no tree was split into chunks), work items over all levels, upper-tree
- * codes and value-buffer entries created by planned levels, and trees that
- * gp_fitness evaluated again through planned levels because their chunk
- * fragments did not fit the fixed per-chunk slots. */
+ * codes and value-buffer entries created by all levels, the operators
+ * evaluated above level 0, and trees that gp_fitness evaluated again
+ * through planned levels because their chunk fragments did not fit the
+ * fixed per-chunk slots (known once gp_fitness has returned).  Synchronises
+ * with the evaluation's stream. */
 typedef struct gp_eval_stats {
     uint32_t levels;
     uint32_t redone;           /* trees re-evaluated through planned levels */
     uint64_t items;
     uint64_t upper_codes;
     uint64_t value_entries;
+    uint64_t upper_ops;        /* operators evaluated above level 0 (the rest
+                                * of the (n-1)/2 per tree ran in level 0)     */
 } gp_eval_stats;
 gp_status gp_eval_stats_get(const gp_population *pop, gp_eval_stats *out);
 

@@ -232,6 +232,7 @@ struct gp_population {
     // then h_bound holds an upper bound of every tree's size.
     bool host_layout = true;
     std::vector<uint64_t> h_bound;
+    bool up_read = true;                     // stats.upper_ops read back since the last evaluation
     uint32_t *d_stat = nullptr;              // [0..2] device-planned evaluation: items, ropes,
                                              // slots; [3] error of a device-side layout
     bool stat_pending = false;
@@ -273,7 +274,7 @@ gp_status alloc_population(gp_population *P, cudaStream_t s)
         return o;
     };
     const uint64_t o_pos = take(2 * sizeof(uint64_t) * n1);        // starts, then sizes
-    const uint64_t o_err = take(sizeof(uint32_t) * (8 + n1));       // error words, counts, redo list
+    const uint64_t o_err = take(sizeof(uint32_t) * (16 + n1));      // error words, counts, redo list
     const uint64_t o_tab = take(sizeof(float) * (4 * P->lanes + P->n_consts + 1));   // x, y, constants
     const uint64_t o_fit = take(sizeof(float) * n1);
     const uint64_t o_hits = take(sizeof(uint32_t) * n1);
@@ -283,15 +284,16 @@ gp_status alloc_population(gp_population *P, cudaStream_t s)
     P->d_start = reinterpret_cast<uint64_t *>(blk + o_pos);
     P->d_size = P->d_start + n1;
     P->d_err = reinterpret_cast<uint32_t *>(blk + o_err);
-    P->d_stat = P->d_err + 4;                // [0..2] planned counts, [3] layout error
-    P->d_redo = P->d_err + 8;
+    P->d_stat = P->d_err + 4;                // [0..2] planned counts, [3] layout error,
+                                             // [4..6] codes, operators, values sent upward
+    P->d_redo = P->d_err + 12;
     P->d_x = reinterpret_cast<float *>(blk + o_tab);
     P->d_y = P->d_x + 2 * P->lanes;
     P->d_c = P->d_y + 2 * P->lanes;
     P->d_fitness = reinterpret_cast<float *>(blk + o_fit);
     P->d_hits = reinterpret_cast<uint32_t *>(blk + o_hits);
     P->d_values = reinterpret_cast<float *>(blk + o_vals);
-    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 9, s));    // error words, counts, redo count
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 13, s));   // error words, counts, redo count
     std::vector<float> tab(4 * P->lanes + P->n_consts);
     std::copy(P->hx.begin(), P->hx.begin() + 2 * P->lanes, tab.begin());
     std::copy(P->hy.begin(), P->hy.begin() + 2 * P->lanes, tab.begin() + 2 * P->lanes);
@@ -839,6 +841,7 @@ gp_status eval_trees(gp_population *P, const std::vector<uint32_t> &trees, const
             p.items = d_items;
             p.n_items = (uint32_t)cur_items.size();
             p.counter = d_counter + level;
+            p.stat_up = level == 0 ? P->d_stat + 4 : nullptr;   // what level 0 sends upward
             p.x = P->d_x;
             p.y = P->d_y;
             p.consts = P->d_c;
@@ -999,6 +1002,7 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
         p.spill = reinterpret_cast<float2 *>(blk + o_spill);
         p.spill_per_warp = spill_per_warp;
         p.err = P->d_err;
+        p.stat_up = P->d_stat + 4;
         if (max_slots) {
             p.fz_codes = reinterpret_cast<uint32_t *>(blk + o_codes);
             p.fz_pt = reinterpret_cast<float2 *>(blk + o_pt);
@@ -1054,7 +1058,9 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
     if (st) return st;
     P->cfg = cfg;
     CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
+    CK(cudaMemsetAsync(P->d_stat + 4, 0, sizeof(uint32_t) * 3, s));
     CK(cudaMemsetAsync(P->d_redo, 0, sizeof(uint32_t), s));
+    P->up_read = false;
     if (!P->host_layout) {
         uint64_t bmax = 0;
         for (uint64_t b : P->h_bound) bmax = std::max(bmax, b);
@@ -1120,14 +1126,20 @@ gp_status gp_eval_stats_get(const gp_population *Pc, gp_eval_stats *out)
 {
     gp_population *P = const_cast<gp_population *>(Pc);
     if (!P || !out) return GP_EINVAL;
-    if (P->stat_pending) {                   // a device-planned evaluation: read its counts
+    if (P->stat_pending || !P->up_read) {    // counts kept on the device
         DeviceGuard dg(P->device);
-        uint32_t c[4] = {};
+        uint32_t c[7] = {};
         CK(cudaStreamSynchronize(P->stream));
         CK(cudaMemcpy(c, P->d_stat, sizeof(c), cudaMemcpyDeviceToHost));
-        P->stats.items = (uint64_t)c[0] + c[1];
-        P->stats.levels = c[1] ? 2u : 1u;
-        P->stat_pending = false;
+        if (P->stat_pending) {               // a device-planned evaluation
+            P->stats.items = (uint64_t)c[0] + c[1];
+            P->stats.levels = c[1] ? 2u : 1u;
+            P->stats.upper_codes = c[4];
+            P->stats.value_entries = c[6];
+            P->stat_pending = false;
+        }
+        P->stats.upper_ops = c[5];
+        P->up_read = true;
     }
     *out = P->stats;
     return GP_OK;

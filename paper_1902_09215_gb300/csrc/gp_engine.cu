@@ -318,11 +318,16 @@ __global__ void run_tiles_scan_kernel(BatchCtl *ctl, uint32_t *run_tiles)
 
 // ---- evaluation levels ----------------------------------------------------
 
+// A level launched inside the captured level loop: its number is the
+// control block's count of loop levels started, plus one.
+constexpr uint32_t kDynLevel = 0xffffffffu;
+
 struct LevelArgs {
-    uint32_t level;
+    uint32_t level;               // or kDynLevel
     uint32_t C;                   // chunk (codes)
     uint32_t cap_items;
     uint32_t last;                // the last level: every open tree becomes a final item
+                                  // (kDynLevel: the number of levels the loop may run)
     uint64_t spill_base;          // first dedicated spill entry (after the per-warp areas)
     uint64_t cap_dedicated;       // dedicated spill entries available
     uint64_t cap_slots;           // fused chunk slots (0: no fused chunks)
@@ -353,16 +358,22 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     BatchCtl *ctl, LevelArgs A, const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
     const uint64_t *__restrict__ frag_off, uint64_t *__restrict__ t_lo, uint64_t *__restrict__ t_hi,
     uint64_t *__restrict__ t_prev, uint32_t *__restrict__ t_first, uint32_t *__restrict__ t_state,
-    EvalItem *__restrict__ items)
+    EvalItem *__restrict__ items, EvalItem *__restrict__ rope_items)
 {
     __shared__ uint64_t sa[kScanT], sb[kScanT];
     __shared__ uint32_t s_cnt[kBuckets], s_fill[kBuckets];
+    __shared__ uint32_t s_rcnt[kBuckets], s_rfill[kBuckets], s_rbase[kBuckets];
     __shared__ uint64_t s_base[kBuckets];
     __shared__ uint32_t s_err;
     const uint32_t t = threadIdx.x;
     const uint32_t n = ctl->head.n_trees, C = A.C;
+    const bool dyn = A.level == kDynLevel;
+    const uint32_t level = dyn ? 1u + ctl->loop_level : A.level;
+    const bool last = dyn ? level + 1 >= A.last : A.last != 0;
+    __syncthreads();                          // every thread has read the loop count
+    if (dyn && t == 0) ctl->loop_level = level;
     // nothing to do: an earlier error, or no tree was cut at the level before
-    if (ctl->err != 0 || (A.level > 0 && ctl->n_chunks == 0 && ctl->n_ropes == 0)) {
+    if (ctl->err != 0 || (level > 0 && ctl->n_chunks == 0 && ctl->n_ropes == 0)) {
         __syncthreads();                      // every thread has read n_chunks / n_ropes
         if (t == 0) ctl->n_items = ctl->n_chunks = ctl->n_ropes = 0;
         return;
@@ -370,15 +381,17 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     if (t < kBuckets) {
         s_cnt[t] = 0;
         s_fill[t] = 0;
+        s_rcnt[t] = 0;
+        s_rfill[t] = 0;
     }
     const uint32_t per = (n + kScanT - 1) / kScanT;
     const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
-    const uint64_t fuse_hi = (A.level == 0 && A.cap_slots) ? (uint64_t)kFuseMaxChunks * C : 0;
+    const uint64_t fuse_hi = (level == 0 && A.cap_slots) ? (uint64_t)kFuseMaxChunks * C : 0;
 
     // phase 1: this level's range of every open tree (all reads of the old
     // t_first happen before the barrier; phase 3 rewrites it)
     for (uint32_t i = lo; i < hi; ++i) {
-        if (A.level == 0) {
+        if (level == 0) {
             t_lo[i] = bstart[i];
             t_hi[i] = bstart[i] + bsize[i];
             t_prev[i] = ~0ull;
@@ -424,7 +437,8 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         const uint64_t len = t_hi[i] - t_lo[i];
         if (t_state[i] == 3) {
             nfz += (len + C - 1) / C;
-        } else if (A.last || len <= C || 2 * len > t_prev[i]) {
+            atomicAdd(&s_rcnt[size_bucket(len)], 1u);
+        } else if (last || len <= C || 2 * len > t_prev[i]) {
             atomicAdd(&s_cnt[size_bucket(len)], 1u);
             if (len > C) ded += len;
         } else {
@@ -444,6 +458,11 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             s_base[b] = pos;
             pos += s_cnt[b];
         }
+        uint32_t rpos = 0;                    // level 0's ropes, largest trees first
+        for (int b = (int)kBuckets - 1; b >= 0; --b) {
+            s_rbase[b] = rpos;
+            rpos += s_rcnt[b];
+        }
         uint32_t err = 0;
         ctl->need_dedicated = max(ctl->need_dedicated, tot_ded);
         ctl->need_items = max(ctl->need_items, pos);
@@ -456,7 +475,11 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             ctl->n_items = (uint32_t)pos;
             ctl->n_chunks = (uint32_t)tot_ch;
             ctl->n_ropes = (uint32_t)tot_fz;
-            if (pos) ctl->levels = A.level + 1;
+            if (pos) ctl->levels = level + 1;
+            if (level == 0 && rope_items) {
+                ctl->n_rope_items = rpos;
+                if (rpos) ctl->levels = 2;    // the ropes are level 1
+            }
         }
         s_err = err;
     }
@@ -480,7 +503,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             continue;
         }
         const uint64_t len = t_hi[i] - t_lo[i];
-        if (t_state[i] != 3 && (A.last || len <= C || 2 * len > t_prev[i])) {
+        if (t_state[i] != 3 && (last || len <= C || 2 * len > t_prev[i])) {
             const uint32_t b = size_bucket(len);
             EvalItem it{};
             it.begin = t_lo[i];
@@ -508,6 +531,16 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
                 it.frag_len = m;
                 it.spill_off = kNoSpill;
                 items[tot_ch + ex_fz + j] = it;
+            }
+            if (rope_items) {
+                EvalItem r{};
+                r.tree = i;
+                r.flags = kItemFinal | gpk::kItemRope;
+                r.pt_base = ex_fz;
+                r.frag_len = m;
+                r.spill_off = kNoSpill;
+                const uint32_t b = size_bucket(len);
+                rope_items[s_rbase[b] + atomicAdd(&s_rfill[b], 1u)] = r;
             }
             t_state[i] = 2;
             t_lo[i] = ex_fz;
@@ -547,13 +580,19 @@ __global__ void fill_chunks_kernel(const BatchCtl *ctl, uint32_t C, const uint32
 // After a level's plan scan: the level's upper-tree codes and value entries
 // must fit the workspace; the code array is zero-padded past its end (the
 // evaluator reads whole 16-code groups).
+// In a captured batch it also zeroes the level's work counter (a loop level
+// reuses one per parity) and sets the level loop's conditions: `more` (bit
+// 0 of cond) to whether the next level has trees, `zero` to 0 (bit 1) or
+// to whether this level cut planned chunks (bit 2).
 __global__ void check_kernel(BatchCtl *ctl, uint64_t cap_codes, uint64_t cap_values, uint32_t *__restrict__ u_out,
-                             uint32_t idx)
+                             uint32_t idx, uint32_t *counter, uint32_t cond, cudaGraphConditionalHandle more,
+                             cudaGraphConditionalHandle zero)
 {
     __shared__ uint32_t s_ok;
     const uint64_t codes = ctl->totals[0], vals = ctl->totals[1];
     if (threadIdx.x == 0) {
         s_ok = 0;
+        if (counter) *counter = 0;
         if (ctl->err == 0) {
             // recorded whether or not they fit: a recovery sizes from them
             ctl->need_codes[idx] = max(ctl->need_codes[idx], codes);
@@ -567,6 +606,11 @@ __global__ void check_kernel(BatchCtl *ctl, uint64_t cap_codes, uint64_t cap_val
         } else {
             ctl->n_items = 0;
         }
+        // the next level has work when this one cut trees (or left ropes)
+        const uint32_t next = ctl->err == 0 && (ctl->n_chunks != 0 || ctl->n_ropes != 0);
+        if (cond & 1u) cudaGraphSetConditional(more, next);
+        if (cond & 2u) cudaGraphSetConditional(zero, 0u);
+        if (cond & 4u) cudaGraphSetConditional(zero, ctl->n_chunks != 0);
     }
     __syncthreads();
     if (!s_ok) return;
@@ -698,6 +742,8 @@ Engine::~Engine()
     gfree(work_allocs_);
     gfree(allocs_);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (cudaStream_t b : cap_body)
+        if (b) cudaStreamDestroy(b);
     cudaSetDevice(cur);
 }
 
@@ -715,6 +761,7 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     levels_max = levels_max_;
     heap_bytes = heap_bytes_;
     GK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    for (cudaStream_t &b : cap_body) GK(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
     // launch shape as in gp_evaluate
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -725,8 +772,17 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     smem = eval_smem_bytes(lanes, (int)W, (int)K, false, rows);
     smem_u = eval_smem_bytes(lanes, (int)Wu, (int)Ku, true, rows);
     if (smem > (size_t)maxsm || smem_u > (size_t)maxsm) return GP_EINVAL;
+    Kr = std::max<uint32_t>(K, 192);
+    Wr = std::min<uint32_t>(W, 16);
+    while (Wr > 1 && eval_smem_bytes(lanes, (int)Wr, (int)Kr, true, rows) > (size_t)maxsm) --Wr;
+    smem_r = eval_smem_bytes(lanes, (int)Wr, (int)Kr, true, rows);
+    if (smem_r > (size_t)maxsm) {
+        Kr = Ku;
+        Wr = Wu;
+        smem_r = smem_u;
+    }
     GK(eval_prepare_at_least(lanes, false, smem));
-    GK(eval_prepare_at_least(lanes, true, smem_u));
+    GK(eval_prepare_at_least(lanes, true, std::max(smem_u, smem_r)));
 
     auto &v = allocs_;
     gp_status st;
@@ -757,6 +813,7 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     if ((st = galloc(v, (void **)&t_prev_, sizeof(uint64_t) * T))) return st;
     if ((st = galloc(v, (void **)&t_first_, sizeof(uint32_t) * (T + 1)))) return st;
     if ((st = galloc(v, (void **)&t_state_, sizeof(uint32_t) * T))) return st;
+    if ((st = galloc(v, (void **)&rope_items_, sizeof(EvalItem) * T))) return st;
     if ((st = galloc(v, (void **)&x_, sizeof(float) * 2 * lanes))) return st;
     if ((st = galloc(v, (void **)&y_, sizeof(float) * 2 * lanes))) return st;
     if ((st = galloc(v, (void **)&c_, sizeof(float) * (n_consts + 1)))) return st;
@@ -1081,133 +1138,277 @@ gp_status Engine::write_head(uint32_t mode, const std::vector<uint32_t> &runs, c
     return GP_OK;
 }
 
+// Graph conditions and work counter of a level inside the captured level
+// loop (all zero for a level launched directly).
+struct Engine::LevelCond {
+    uint32_t flags = 0;                  // check_kernel: bit 0 sets `more`, bit 1 zeroes `zero`
+    cudaGraphConditionalHandle more = 0, zero = 0;
+    uint32_t *counter = nullptr;         // the level's work counter, zeroed by check_kernel
+};
+
+// One evaluation level: items, chunk fill, plan, plan scan, workspace
+// check, evaluator.  `dyn`: a level of the captured loop (its number comes
+// from the control block; its buffers alternate by the parity of `level`).
+gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool sizing, uint32_t &prev_chunks,
+                                const LevelCond &cond, uint32_t *nl_out, bool *stop)
+{
+    uint32_t nl = 0;
+    const bool wide = dyn || level > 0;
+    const int k = level & 1;
+    LevelArgs A{dyn ? kDynLevel : level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu),
+                dyn ? levels_cap_graph : (level + 1 == levels_max ? 1u : 0u), w.spill_base, w.cap_dedicated,
+                w.cap_slots};
+    items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
+                                      t_state_, w.items, rope_items_);
+    GK(cudaGetLastError());
+    if (sizing) {
+        // a dedicated spill pool too small for this level's oversized
+        // finals: grow it, clear the error and build the level again
+        // (the kernel changes nothing else when it raises that error)
+        BatchCtl c{};
+        GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+        GK(cudaStreamSynchronize(s));
+        if (level == 0 && c.err == 0 && w.cap_slots && c.need_slots > w.cap_slots) {
+            // more fused-chunk candidates than slots (some went planned):
+            // more slots, the level again
+            gp_status st = set_slots(std::max<uint64_t>(2 * c.need_slots, w.cap_slots), w.fz_cap_pt);
+            if (st) return st;
+            A.cap_slots = w.cap_slots;
+            GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
+            GK(cudaMemsetAsync(w.fz_over, 0, sizeof(uint32_t) * max_trees, s));
+            GK(cudaMemsetAsync(w.fz_redo, 0, sizeof(uint32_t), s));
+            items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
+                                              t_first_, t_state_, w.items, rope_items_);
+            GK(cudaGetLastError());
+            GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+            GK(cudaStreamSynchronize(s));
+        }
+        if (c.err == kGErrSpill) {
+            const uint64_t nd = std::max<uint64_t>(2 * c.need_dedicated, w.cap_dedicated);
+            void *p = nullptr;
+            GK(cudaMalloc(&p, sizeof(float2) * lanes * (w.spill_base + nd)));
+            work_allocs_.push_back(p);
+            w.spill = (float2 *)p;
+            w.cap_dedicated = nd;
+            A.cap_dedicated = nd;
+            // the failed build zeroed the chunk count the level starts
+            // from: put back the previous level's before building again
+            GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
+            GK(cudaMemcpyAsync(&ctl->n_chunks, &prev_chunks, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+            items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
+                                              t_first_, t_state_, w.items, rope_items_);
+            GK(cudaGetLastError());
+            GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
+            GK(cudaStreamSynchronize(s));
+        }
+        prev_chunks = c.n_chunks;
+    }
+    fill_chunks_kernel<<<sms * 4, 256, 0, s>>>(ctl, w.C, t_first_, t_lo_, t_hi_, w.items);
+    GK(cudaGetLastError());
+    const void *codes = wide ? (const void *)w.codes[k ^ 1] : (const void *)heap;
+    GK(launch_plan_dev(wide, codes, w.items, (uint32_t)w.cap_items, &ctl->n_chunks, w.plan, sms, s));
+    GK(launch_plan_scan_dev(w.items, w.plan, &ctl->n_chunks, w.frag_off, ctl->totals, s));
+    nl += 4;
+    if (sizing) {
+        uint64_t tot[2];
+        uint32_t err = 0, n_items = 0;
+        GK(cudaMemcpyAsync(tot, ctl->totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
+        GK(cudaMemcpyAsync(&err, &ctl->err, sizeof(err), cudaMemcpyDeviceToHost, s));
+        GK(cudaMemcpyAsync(&n_items, &ctl->n_items, sizeof(n_items), cudaMemcpyDeviceToHost, s));
+        GK(cudaStreamSynchronize(s));
+        if (err || n_items == 0) {
+            *stop = true;
+            return GP_OK;
+        }
+        if (tot[0] + 48 > w.cap_codes[k] || tot[1] > w.cap_values[k]) {
+            // grow this level's output buffers; they hold nothing still
+            // needed (the outputs of level - 2)
+            const uint64_t nc = std::max<uint64_t>(w.cap_codes[k], tot[0] + tot[0] / 8 + 1024);
+            const uint64_t nv = std::max<uint64_t>(w.cap_values[k], tot[1] + tot[1] / 8 + 1024);
+            void *pc = nullptr, *pv = nullptr;
+            const char *vb = std::getenv("GP_VERBOSE");
+            if (vb && vb[0] == '1')
+                std::fprintf(stderr, "engine sizing: level %u needs %llu codes, %llu value entries (%.1f GB)\n",
+                             level, (unsigned long long)tot[0], (unsigned long long)tot[1],
+                             (double)nv * lanes * 8 / 1e9);
+            GK(cudaMalloc(&pc, sizeof(uint32_t) * (nc + 64)));
+            work_allocs_.push_back(pc);
+            GK(cudaMalloc(&pv, sizeof(float2) * (nv * lanes + 1)));
+            work_allocs_.push_back(pv);
+            w.codes[k] = (uint32_t *)pc;
+            w.vals[k] = (float2 *)pv;
+            w.cap_codes[k] = nc;
+            w.cap_values[k] = nv;
+        }
+    }
+    check_kernel<<<1, 64, 0, s>>>(ctl, w.cap_codes[k], w.cap_values[k], w.codes[k], (uint32_t)k, cond.counter,
+                                  cond.flags, cond.more, cond.zero);
+    GK(cudaGetLastError());
+    EvalParams p{};
+    p.codes = codes;
+    p.items = w.items;
+    p.n_items = (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu);
+    p.n_items_dev = &ctl->n_items;
+    p.counter = cond.counter ? cond.counter : &ctl->counter[level];
+    p.x = x_;
+    p.y = y_;
+    p.consts = c_;
+    p.n_cases = n_cases;
+    p.n_consts = n_consts;
+    p.leaf_rows = (uint32_t)rows;
+    p.div0 = div0;
+    p.window = wide ? Ku : K;
+    p.pt_in = wide ? w.vals[k ^ 1] : nullptr;
+    p.pt_out = w.vals[k];
+    p.u_out = w.codes[k];
+    p.values = bvals_;
+    p.fitness = bfit_;
+    p.hits = bhits_;
+    p.spill = w.spill;
+    p.spill_per_warp = w.spill_per_warp;
+    p.err = &ctl->eval_err[0];
+    if (w.cap_slots) {
+        p.fz_codes = w.fz_codes;
+        p.fz_pt = w.fz_pt;
+        p.fz_len = w.fz_len;
+        p.fz_over = w.fz_over;
+        p.fz_redo = w.fz_redo;
+        p.fz_cap_codes = w.C;
+        p.fz_cap_pt = w.fz_cap_pt;
+    }
+    GK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s));
+    nl += 2;
+    *nl_out += nl;
+    return GP_OK;
+}
+
 gp_status Engine::enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches)
 {
     uint32_t nl = 0;
     uint32_t prev_chunks = 0;            // sizing: chunks the previous level cut
-    for (uint32_t level = 0; level < levels_max; ++level) {
-        const bool wide = level > 0;
-        const int k = level & 1;
-        LevelArgs A{level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu),
-                    level + 1 == levels_max ? 1u : 0u, w.spill_base, w.cap_dedicated, w.cap_slots};
-        items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
-                                          t_state_, w.items);
-        GK(cudaGetLastError());
-        if (sizing) {
-            // a dedicated spill pool too small for this level's oversized
-            // finals: grow it, clear the error and build the level again
-            // (the kernel changes nothing else when it raises that error)
-            BatchCtl c{};
-            GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
-            GK(cudaStreamSynchronize(s));
-            if (level == 0 && c.err == 0 && w.cap_slots && c.need_slots > w.cap_slots) {
-                // more fused-chunk candidates than slots (some went planned):
-                // more slots, the level again
-                gp_status st = set_slots(std::max<uint64_t>(2 * c.need_slots, w.cap_slots), w.fz_cap_pt);
-                if (st) return st;
-                A.cap_slots = w.cap_slots;
-                GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
-                GK(cudaMemsetAsync(w.fz_over, 0, sizeof(uint32_t) * max_trees, s));
-                GK(cudaMemsetAsync(w.fz_redo, 0, sizeof(uint32_t), s));
-                items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
-                                                  t_first_, t_state_, w.items);
-                GK(cudaGetLastError());
-                GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
-                GK(cudaStreamSynchronize(s));
-            }
-            if (c.err == kGErrSpill) {
-                const uint64_t nd = std::max<uint64_t>(2 * c.need_dedicated, w.cap_dedicated);
-                void *p = nullptr;
-                GK(cudaMalloc(&p, sizeof(float2) * lanes * (w.spill_base + nd)));
-                work_allocs_.push_back(p);
-                w.spill = (float2 *)p;
-                w.cap_dedicated = nd;
-                A.cap_dedicated = nd;
-                // the failed build zeroed the chunk count the level starts
-                // from: put back the previous level's before building again
-                GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
-                GK(cudaMemcpyAsync(&ctl->n_chunks, &prev_chunks, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
-                items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
-                                                  t_first_, t_state_, w.items);
-                GK(cudaGetLastError());
-                GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
-                GK(cudaStreamSynchronize(s));
-            }
-            prev_chunks = c.n_chunks;
+    bool stop = false;
+    if (!capturing_ || sizing) {
+        // a fixed sequence of levels_max levels (empty ones return at once)
+        for (uint32_t level = 0; level < levels_max && !stop; ++level) {
+            gp_status st = enqueue_level(level, false, s, sizing, prev_chunks, LevelCond{}, &nl, &stop);
+            if (st) return st;
         }
-        fill_chunks_kernel<<<sms * 4, 256, 0, s>>>(ctl, w.C, t_first_, t_lo_, t_hi_, w.items);
-        GK(cudaGetLastError());
-        const void *codes = wide ? (const void *)w.codes[(level - 1) & 1] : (const void *)heap;
-        GK(launch_plan_dev(wide, codes, w.items, (uint32_t)w.cap_items, &ctl->n_chunks, w.plan, sms, s));
-        GK(launch_plan_scan_dev(w.items, w.plan, &ctl->n_chunks, w.frag_off, ctl->totals, s));
-        nl += 4;
-        if (sizing) {
-            uint64_t tot[2];
-            uint32_t err = 0, n_items = 0;
-            GK(cudaMemcpyAsync(tot, ctl->totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
-            GK(cudaMemcpyAsync(&err, &ctl->err, sizeof(err), cudaMemcpyDeviceToHost, s));
-            GK(cudaMemcpyAsync(&n_items, &ctl->n_items, sizeof(n_items), cudaMemcpyDeviceToHost, s));
-            GK(cudaStreamSynchronize(s));
-            if (err || n_items == 0) break;
-            if (tot[0] + 48 > w.cap_codes[k] || tot[1] > w.cap_values[k]) {
-                // grow this level's output buffers; they hold nothing still
-                // needed (the outputs of level - 2)
-                const uint64_t nc = std::max<uint64_t>(w.cap_codes[k], tot[0] + tot[0] / 8 + 1024);
-                const uint64_t nv = std::max<uint64_t>(w.cap_values[k], tot[1] + tot[1] / 8 + 1024);
-                void *pc = nullptr, *pv = nullptr;
-                const char *vb = std::getenv("GP_VERBOSE");
-                if (vb && vb[0] == '1')
-                    std::fprintf(stderr, "engine sizing: level %u needs %llu codes, %llu value entries (%.1f GB)\n",
-                                 level, (unsigned long long)tot[0], (unsigned long long)tot[1],
-                                 (double)nv * lanes * 8 / 1e9);
-                GK(cudaMalloc(&pc, sizeof(uint32_t) * (nc + 64)));
-                work_allocs_.push_back(pc);
-                GK(cudaMalloc(&pv, sizeof(float2) * (nv * lanes + 1)));
-                work_allocs_.push_back(pv);
-                w.codes[k] = (uint32_t *)pc;
-                w.vals[k] = (float2 *)pv;
-                w.cap_codes[k] = nc;
-                w.cap_values[k] = nv;
-            }
-        }
-        check_kernel<<<1, 64, 0, s>>>(ctl, w.cap_codes[k], w.cap_values[k], w.codes[k], (uint32_t)k);
-        GK(cudaGetLastError());
-        EvalParams p{};
-        p.codes = codes;
-        p.items = w.items;
-        p.n_items = (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu);
-        p.n_items_dev = &ctl->n_items;
-        p.counter = &ctl->counter[level];
-        p.x = x_;
-        p.y = y_;
-        p.consts = c_;
-        p.n_cases = n_cases;
-        p.n_consts = n_consts;
-        p.leaf_rows = (uint32_t)rows;
-        p.div0 = div0;
-        p.window = wide ? Ku : K;
-        p.pt_in = wide ? w.vals[(level - 1) & 1] : nullptr;
-        p.pt_out = w.vals[k];
-        p.u_out = w.codes[k];
-        p.values = bvals_;
-        p.fitness = bfit_;
-        p.hits = bhits_;
-        p.spill = w.spill;
-        p.spill_per_warp = w.spill_per_warp;
-        p.err = &ctl->eval_err[0];
-        if (w.cap_slots) {
-            p.fz_codes = w.fz_codes;
-            p.fz_pt = w.fz_pt;
-            p.fz_len = w.fz_len;
-            p.fz_over = w.fz_over;
-            p.fz_redo = w.fz_redo;
-            p.fz_cap_codes = w.C;
-            p.fz_cap_pt = w.fz_cap_pt;
-        }
-        GK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s));
-        nl += 2;
+        if (launches) *launches += nl;
+        return GP_OK;
     }
-    if (launches) *launches += nl;
+    // Captured: level 0, then an IF/ELSE node.  When level 0 cut planned
+    // chunks, a WHILE node runs the upper levels (its body one odd level and
+    // an IF node holding the next even level); each level's check kernel
+    // says whether the next level has trees, so a replay runs exactly the
+    // levels the generation needs (at most levels_cap_graph, the last of
+    // which finishes every open tree).  Otherwise the only upper level is
+    // the ropes level 0 listed, evaluated by one launch shaped for ropes.
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr, gb = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    GK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h_up = 0, h_loop = 0, h_even = 0;
+    GK(cudaGraphConditionalHandleCreate(&h_up, g, 0, cudaGraphCondAssignDefault));
+    GK(cudaGraphConditionalHandleCreate(&h_loop, g, 0, cudaGraphCondAssignDefault));
+    GK(cudaGraphConditionalHandleCreate(&h_even, g, 0, cudaGraphCondAssignDefault));
+    LevelCond c0;
+    c0.flags = 1 | 4;                    // the loop's first pass; planned chunks choose the loop
+    c0.more = h_loop;
+    c0.zero = h_up;
+    gp_status st = enqueue_level(0, false, s, false, prev_chunks, c0, &nl, &stop);
+    if (st) return st;
+    GK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams up{};
+    up.type = cudaGraphNodeTypeConditional;
+    up.conditional.handle = h_up;
+    up.conditional.type = cudaGraphCondTypeIf;
+    up.conditional.size = 2;
+    cudaGraphNode_t un;
+    GK(cudaGraphAddNode(&un, g, deps, nullptr, nd, &up));
+    GK(cudaStreamUpdateCaptureDependencies(s, &un, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    GK(cudaGraphAddNode(&wn, up.conditional.phGraph_out[0], nullptr, nullptr, 0, &wp));
+    GK(cudaStreamBeginCaptureToGraph(cap_body[0], wp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    uint32_t nl_odd = 0, nl_even = 0;
+    auto body = [&]() -> gp_status {
+        LevelCond c1;
+        c1.flags = 1 | 2;                // the even level's IF; the loop stops unless it continues it
+        c1.more = h_even;
+        c1.zero = h_loop;
+        c1.counter = &ctl->counter[62];
+        gp_status e = enqueue_level(1, true, cap_body[0], false, prev_chunks, c1, &nl_odd, &stop);
+        if (e) return e;
+        cudaGraph_t gi = nullptr;
+        GK(cudaStreamGetCaptureInfo(cap_body[0], &cs, nullptr, &gi, &deps, nullptr, &nd));
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = h_even;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t in;
+        GK(cudaGraphAddNode(&in, gi, deps, nullptr, nd, &ip));
+        GK(cudaStreamUpdateCaptureDependencies(cap_body[0], &in, nullptr, 1, cudaStreamSetCaptureDependencies));
+        GK(cudaStreamBeginCaptureToGraph(cap_body[1], ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+        LevelCond c2;
+        c2.flags = 1;                    // the loop goes on when the next odd level has trees
+        c2.more = h_loop;
+        c2.counter = &ctl->counter[63];
+        e = enqueue_level(2, true, cap_body[1], false, prev_chunks, c2, &nl_even, &stop);
+        cudaError_t ce = cudaStreamEndCapture(cap_body[1], &gb);
+        if (e) return e;
+        GK(ce);
+        return GP_OK;
+    };
+    st = body();
+    cudaError_t ce = cudaStreamEndCapture(cap_body[0], &gb);
+    if (st) return st;
+    GK(ce);
+    // the ropes-only branch
+    GK(cudaStreamBeginCaptureToGraph(cap_body[0], up.conditional.phGraph_out[1], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    EvalParams p{};
+    p.codes = heap;
+    p.items = rope_items_;
+    p.n_items = max_trees;
+    p.n_items_dev = &ctl->n_rope_items;
+    p.counter = &ctl->counter[61];
+    p.x = x_;
+    p.y = y_;
+    p.consts = c_;
+    p.n_cases = n_cases;
+    p.n_consts = n_consts;
+    p.leaf_rows = (uint32_t)rows;
+    p.div0 = div0;
+    p.window = Kr;
+    p.values = bvals_;
+    p.fitness = bfit_;
+    p.hits = bhits_;
+    p.spill = w.spill;
+    p.spill_per_warp = w.spill_per_warp;
+    p.err = &ctl->eval_err[0];
+    if (w.cap_slots) {
+        p.fz_codes = w.fz_codes;
+        p.fz_pt = w.fz_pt;
+        p.fz_len = w.fz_len;
+        p.fz_over = w.fz_over;
+        p.fz_redo = w.fz_redo;
+        p.fz_cap_codes = w.C;
+        p.fz_cap_pt = w.fz_cap_pt;
+    }
+    cudaError_t le = launch_eval(lanes, true, p, sms, (int)Wr, smem_r, cap_body[0]);
+    ce = cudaStreamEndCapture(cap_body[0], &gb);
+    GK(le);
+    GK(ce);
+    kernels_per_level = nl_odd;
+    if (launches) *launches += nl + nl_odd + nl_even + 1;
     return GP_OK;
 }
 
@@ -1216,8 +1417,9 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     (void)mode;
     uint32_t nl = 0;
     GK(cudaMemsetAsync(ctl->counter, 0, sizeof(ctl->counter), s));
-    // err, n_queries, n_tiles, n_items, n_chunks, levels, eval_err[4], n_ropes, pad2
-    GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t) * 12, s));
+    // err, n_queries, n_tiles, n_items, n_chunks, levels, eval_err[4], n_ropes, loop_level,
+    // n_rope_items
+    GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t) * 13, s));
     if (w.cap_slots) {                   // fused slots: overflow flags and the redo list
         GK(cudaMemsetAsync(w.fz_over, 0, sizeof(uint32_t) * max_trees, s));
         GK(cudaMemsetAsync(w.fz_redo, 0, sizeof(uint32_t), s));
@@ -1261,6 +1463,21 @@ gp_status Engine::enqueue(uint32_t mode, const std::vector<uint32_t> &runs, cuda
     return enqueue_body(mode, s, sizing, launches);
 }
 
+// Kernel nodes at the top level of a graph (conditional bodies not included).
+static uint32_t count_kernels(cudaGraph_t graph)
+{
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess || nn == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nn) != cudaSuccess) return 0;
+    uint32_t kernels = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    return kernels;
+}
+
 gp_status Engine::capture(uint32_t mode)
 {
     if (mode > 1) return GP_EINVAL;
@@ -1270,7 +1487,9 @@ gp_status Engine::capture(uint32_t mode)
     }
     cudaGraph_t graph = nullptr;
     GK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    capturing_ = true;
     gp_status st = enqueue_body(mode, cap_stream, false, nullptr);
+    capturing_ = false;
     cudaError_t e = cudaStreamEndCapture(cap_stream, &graph);
     if (st) {
         if (graph) cudaGraphDestroy(graph);
@@ -1278,19 +1497,12 @@ gp_status Engine::capture(uint32_t mode)
     }
     GK(e);
     e = cudaGraphInstantiate(&exec[mode], graph, 0);
-    size_t nn = 0;
-    cudaGraphGetNodes(graph, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    uint32_t kernels = 0;
-    if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess) {
-        for (auto nd : nodes) {
-            cudaGraphNodeType ty;
-            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
-        }
-    }
+    const uint32_t top = count_kernels(graph);
     cudaGraphDestroy(graph);
     GK(e);
-    kernels_per_batch[mode] = kernels;
+    // the branches hold one odd and one even level, or one rope launch
+    kernels_fixed[mode] = top;
+    kernels_per_batch[mode] = top + 2 * kernels_per_level + 1;
     return GP_OK;
 }
 

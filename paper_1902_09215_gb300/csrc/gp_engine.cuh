@@ -73,7 +73,9 @@ struct BatchCtl {
     uint32_t err;                        // batch-level error bits of this batch
     uint32_t n_queries, n_tiles, n_items, n_chunks, levels;
     uint32_t eval_err[4];                // [0] evaluator error word, [1] extent error word
-    uint32_t n_ropes, pad2;              // fused chunks cut at level 0 (their ropes are level 1's)
+    uint32_t n_ropes;                    // fused chunks cut at level 0 (their ropes are level 1's)
+    uint32_t loop_level;                 // upper levels the captured level loop has started
+    uint32_t n_rope_items;               // ropes level 0 listed (a rope-only level 1)
     uint64_t totals[4];                  // plan scan totals of the current level
     uint64_t need_codes[2], need_values[2], need_dedicated, need_items, need_slots;   // sizing records
     uint64_t child_nodes;                // nodes of all children made by this batch
@@ -163,22 +165,37 @@ class Engine {
     uint32_t n_cases = 0, n_consts = 0, max_runs = 0, max_trees = 0, levels_max = 8;
     float div0 = 1.0f;
     uint32_t W = 32, K = 32, Wu = 16, Ku = 128;
+    // a launch of ropes only: few long serial walks, so deeper windows
+    uint32_t Wr = 4, Kr = 192;
     int rows = 128;                      // leaf table rows: 'x' + the constants
-    size_t smem = 0, smem_u = 0;
+    size_t smem = 0, smem_u = 0, smem_r = 0;
     uint64_t heap_bytes = 0;
     uint8_t *heap = nullptr;
     RunDev *runs_dev = nullptr;
     std::vector<RunHost> runs_host;
     Work w;
     uint32_t kernels_per_batch[2] = {0, 0};
+    // kernels of a captured batch outside the level loop, and per loop level
+    uint32_t kernels_fixed[2] = {0, 0}, kernels_per_level = 0;
+    // levels the captured loop may run (its last makes every open tree final)
+    uint32_t levels_cap_graph = 16;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_body[2] = {nullptr, nullptr};
+    EvalItem *rope_items_ = nullptr;     // [max_trees] level 0's rope list, largest first
+    // kernels a replay of the captured batch `mode` runs when it used `levels` levels
+    uint32_t graph_kernels(uint32_t mode, uint32_t levels) const {
+        return kernels_fixed[mode & 1] + kernels_per_level * (levels > 1 ? levels - 1 : 0);
+    }
     BatchCtl *ctl = nullptr;
 
   private:
     gp_status write_head(uint32_t mode, const std::vector<uint32_t> &runs, cudaStream_t s);
     gp_status enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint32_t *launches);
     gp_status enqueue_eval(cudaStream_t s, bool sizing, uint32_t *launches);
+    struct LevelCond;                    // graph conditions a level's check kernel sets
+    gp_status enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool sizing, uint32_t &prev_chunks,
+                            const LevelCond &cond, uint32_t *nl, bool *stop);
+    bool capturing_ = false;             // enqueue_body is recording the batch graph
     uint64_t heap_alloc(uint64_t bytes);
     void heap_release(uint64_t off, uint64_t bytes);
 

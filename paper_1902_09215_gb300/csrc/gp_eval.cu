@@ -323,7 +323,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
     // Fragment output: planned items write at planned offsets; fused chunks
     // right-align their codes in their own slot and number their value
     // entries from the slot's first entry.  Counters of what was emitted:
-    uint32_t n_emit = 0, n_pt = 0;
+    uint32_t n_emit = 0, n_pt = 0, n_op_emit = 0;
     bool pt_full = false;                 // a fused chunk ran out of value slots
     uint32_t prev = 0xFFFFFFFFu;          // code at the position right of the current one
     uint32_t fault = 0;                   // kErr* bits; any fault ends the item
@@ -427,6 +427,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
             // to the next level, so they are copied too).
             if (have) emit((prev >= 4 && prev < kPtCode0) ? prev : new_pt(tos));
             emit(c);
+            ++n_op_emit;
             have = false;
         }
         prev = c;
@@ -612,6 +613,11 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
     for (uint64_t i = 0; i < g; ++i) emit(new_pt(pk(spill[i * LANES + lane])));
     for (int i = 0; i < sp; ++i) emit(new_pt(lds64(wb + i * S)));
     if (have) emit(new_pt(tos));
+    if (P.stat_up && lane == 0) {
+        atomicAdd(P.stat_up, n_emit);
+        atomicAdd(P.stat_up + 1, n_op_emit);
+        atomicAdd(P.stat_up + 2, n_pt);
+    }
     if (fused) {
         if (lane == 0) {
             P.fz_len[IT(frag_off)] = n_emit;

@@ -54,12 +54,11 @@ void order_after_last(gp_generation *G, cudaStream_t s)
 gp_status widen_levels(gp_generation *G, uint32_t used)
 {
     Engine &E = G->eng;
-    if (!G->auto_levels || used < E.levels_max || E.levels_max >= G->levels_cap) return GP_OK;
+    // (a captured generation runs its upper levels in a loop on the device,
+    // up to the cap, so only the plain launch sequence has a budget)
+    if (G->use_graph || !G->auto_levels || used < E.levels_max || E.levels_max >= G->levels_cap) return GP_OK;
     E.levels_max = std::min<uint32_t>(G->levels_cap, E.levels_max + 2);
-    if (!G->use_graph) return GP_OK;
-    gp_status st = E.capture(kModeGenerate);
-    if (!st) G->info.kernels_per_generation = E.kernels_per_batch[kModeGenerate];
-    return st;
+    return GP_OK;
 }
 
 // Synchronise and read the run's state; the run's error (if any) as a status.
@@ -278,6 +277,7 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
     G->auto_levels = params->max_levels == 0;
     if (G->auto_levels) E.levels_max = std::min<uint32_t>(G->levels_cap, std::max<uint32_t>(3, G->info.levels + 2));
     step = "graph capture";
+    E.levels_cap_graph = params->max_levels ? params->max_levels : G->levels_cap;
     if (G->use_graph && (st = E.capture(kModeGenerate))) return fail(st);
     G->info.n_trees = n_trees;
     G->info.chunk_nodes = best_C;
@@ -301,7 +301,7 @@ gp_status gp_generation_step(gp_generation *G, uint32_t n, void *cuda_stream)
         uint32_t nl = 0;
         if (G->use_graph) {
             st = G->eng.launch_graph(kModeGenerate, {G->run}, s);
-            nl = G->eng.kernels_per_batch[kModeGenerate];
+            nl = G->eng.graph_kernels(kModeGenerate, std::max<uint32_t>(G->info.levels, 1));
         } else {
             st = G->eng.enqueue(kModeGenerate, {G->run}, s, false, &nl);
             G->info.kernels_per_generation = nl;

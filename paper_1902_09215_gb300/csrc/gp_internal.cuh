@@ -89,6 +89,8 @@ struct EvalParams {
     uint32_t fz_cap_codes;
     uint32_t fz_cap_pt;
     uint32_t leaf_rows;            // leaf table rows ('x' + constants); 0 = kLeafRows
+    uint32_t *stat_up;             // nullable: [0] codes, [1] operators, [2] value entries
+                                   // that fragments of this launch emitted upward
 };
 
 struct XoChild {                   // child = M[0,i) ++ D[j,e_d) ++ M[e_m,n_m)

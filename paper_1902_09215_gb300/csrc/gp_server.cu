@@ -211,16 +211,17 @@ void worker_main(gp_server *S)
         }
         gp_status st = GP_OK;
         cudaEventRecord(S->ev0, S->stream);
+        uint32_t nl = 0;
         if (S->prm.use_graph) st = S->eng.launch_graph(kModeGenerate, slots, S->stream);
-        else st = S->eng.enqueue(kModeGenerate, slots, S->stream, false, nullptr);
+        else st = S->eng.enqueue(kModeGenerate, slots, S->stream, false, &nl);
         cudaEventRecord(S->ev1, S->stream);
-        gpk::note_launches(S->eng.kernels_per_batch[kModeGenerate]);
         lk.unlock();
         const cudaError_t e = cudaEventSynchronize(S->ev1);
         lk.lock();
         BatchCtl c{};
         if (!st && e != cudaSuccess) st = GP_ECUDA;
         if (!st) st = S->eng.read_ctl(&c, S->stream);
+        gpk::note_launches(S->prm.use_graph ? S->eng.graph_kernels(kModeGenerate, std::max<uint32_t>(c.levels, 1)) : nl);
         if (!st && cudaMemcpy(S->table.data(), S->eng.runs_dev, sizeof(RunDev) * S->table.size(),
                               cudaMemcpyDeviceToHost) != cudaSuccess)
             st = GP_ECUDA;
@@ -506,8 +507,13 @@ gp_status gp_server_get_stats(gp_server *S, gp_server_stats *out)
     std::vector<double> l = S->lat;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
-        s.latency_p50_ms = l[l.size() / 2];
-        s.latency_p99_ms = l[std::min(l.size() - 1, (size_t)(0.99 * (double)l.size()))];
+        // nearest rank: the ceil(q n)-th smallest request latency
+        auto rank = [&](double q) {
+            const size_t k = (size_t)std::ceil(q * (double)l.size());
+            return l[std::min(l.size() - 1, k ? k - 1 : 0)];
+        };
+        s.latency_p50_ms = rank(0.50);
+        s.latency_p99_ms = rank(0.99);
     }
     s.heap_free = S->eng.heap_free();
     s.runs_waiting = 0;

@@ -60,7 +60,7 @@ class gp_population_info(C.Structure):
 
 class gp_eval_stats(C.Structure):
     _fields_ = [("levels", C.c_uint32), ("redone", C.c_uint32), ("items", C.c_uint64),
-                ("upper_codes", C.c_uint64), ("value_entries", C.c_uint64)]
+                ("upper_codes", C.c_uint64), ("value_entries", C.c_uint64), ("upper_ops", C.c_uint64)]
 
 
 class gp_generation_params(C.Structure):
@@ -339,7 +339,7 @@ def gp_eval_stats_get(pop: Population) -> dict:
     s = gp_eval_stats()
     _check(lib().gp_eval_stats_get(pop._h, C.byref(s)), "gp_eval_stats_get")
     return {"levels": s.levels, "redone": s.redone, "items": s.items, "upper_codes": s.upper_codes,
-            "value_entries": s.value_entries}
+            "value_entries": s.value_entries, "upper_ops": s.upper_ops}
 
 
 def gp_kernel_launch_count() -> int:

@@ -78,3 +78,13 @@ def test_measured_peaks_fallback(bench, tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peaks, src = bench.measured_peaks()
     assert src == "fallback" and peaks["hbm_gbs"] == 6800.0
+
+
+def test_nearest_rank_quantiles(bench):
+    """p99 by the nearest-rank rule: the ceil(0.99 n)-th smallest value, so
+    with 20 samples it is the largest and with 200 the second largest."""
+    v = list(range(1, 21))
+    assert bench.nearest_rank(v, 0.99) == 20 and bench.nearest_rank(v, 0.5) == 10
+    w = list(range(200, 0, -1))
+    assert bench.nearest_rank(w, 0.99) == 198 and bench.nearest_rank(w, 0.5) == 100
+    assert bench.nearest_rank([7.0], 0.99) == 7.0

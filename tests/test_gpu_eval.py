@@ -175,3 +175,50 @@ def test_repeat_evaluation_is_deterministic(gpu):
         outs.append(gpu.gp_fitness(pop, case_values=True))
     for f, v, _ in outs[1:]:
         assert same_f32(f, outs[0][0]) and same_f32(v, outs[0][1])
+
+
+def spine_operators(tree, C):
+    """Operators a chunk of C codes cannot evaluate, summed over the chunks
+    of one tree: reading right to left from a chunk's right end, the stack
+    of the whole tree at position j holds P[j] values, P being the walk of
+    open argument slots (P[0] = 1, P[j+1] = P[j] + arity - 1, Sec. 2.1's
+    prefix order).  An operator at j lacks an argument inside the chunk
+    exactly when P[j] is no higher than every P[k] for j < k <= the chunk's
+    end, i.e. when the walk reaches its running minimum there."""
+    n = tree.shape[0]
+    if n <= C:
+        return 0
+    op = tree < 4
+    P = np.concatenate([[1], 1 + np.cumsum(np.where(op, 1, -1))])
+    total = 0
+    for b in range(0, n, C):
+        e = min(b + C, n)
+        run_min = np.minimum.accumulate(P[b + 1:e + 1][::-1])[::-1]   # min of P[j+1 .. e]
+        total += int(np.sum(op[b:e] & (P[b:e] <= run_min)))
+    return total
+
+
+@pytest.mark.parametrize("C", [1024, 4096])
+def test_operators_sent_upward_follow_the_arity_walk(gpu, oracle, C):
+    """The count of operators evaluated above level 0 (gp_eval_stats) equals
+    the spine operators of every chunk, for an uploaded population (levels
+    planned on the host) and for crossover children (planned on the device),
+    and the results stay exact."""
+    import torch
+    s = torch.cuda.current_stream()
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=23, count=60, lo=31, hi=60001)
+    trees = [nodes[int(offs[i]):int(offs[i + 1])] for i in range(60)]
+    st = check(gpu, oracle, nodes, offs, x, y, c, chunk_nodes=C)
+    assert st["upper_ops"] == sum(spine_operators(t, C) for t in trees) > 0
+    pop = gpu.gp_create_population(prob, nodes, offs, s)
+    sizes = np.diff(offs.astype(np.int64))
+    mum, dad, mp, dp = synth.crossover_points(31, sizes, 60)
+    kids = gpu.gp_crossover(pop, (mum, dad, mp, dp), s)
+    gpu.gp_evaluate(kids, s, chunk_nodes=C)
+    fit, _, _ = gpu.gp_fitness(kids)
+    kn, ko = oracle.crossover_population(nodes, offs, mum, dad, mp, dp)
+    assert same_f32(fit, oracle.eval_population(kn, ko, x, y, c, n_threads=8)["fitness"])
+    kt = [kn[int(ko[i]):int(ko[i + 1])] for i in range(60)]
+    assert gpu.gp_eval_stats_get(kids)["upper_ops"] == sum(spine_operators(t, C) for t in kt)
