@@ -356,12 +356,21 @@ def run_ours(args):
         return
 
     cpu = cpu_baseline(nodes, offs, ops, x, y, c, child_nodes) if world == 1 and not args.no_cpu else None
-    batched = batched_compare(gp, prob, nodes, offs, stream, flush, max(10, args.steps // 10)) if world == 1 else None
+    batched = generations_compare(gp, prob, nodes, offs, stream, flush, 10, 5) if world == 1 else None
     configs = None
     if world == 1 and not args.no_extra:
         # the benchmark's other configurations, each measured once here
-        configs = {"smallest_50_trees": config1_latency(gp, prob, stream, 300, not args.no_cpu),
-                   "bloated_48_trees": config3_bloated(gp, prob, stream, not args.no_cpu)}
+        def guarded(fn, *a):
+            # a configuration that fails is reported in the line, not fatal to it
+            try:
+                return fn(*a)
+            except Exception as e:            # noqa: BLE001
+                return {"error": f"{type(e).__name__}: {e}"}
+        configs = {"smallest_50_trees": guarded(config1_latency, gp, prob, stream, 300, not args.no_cpu),
+                   "bloated_48_trees": guarded(config3_bloated, gp, prob, stream, not args.no_cpu),
+                   "batched_4000_parents_1e2_1e8": guarded(config4_batched, gp, prob, stream, flush,
+                                                           not args.no_cpu),
+                   "serving_64_runs": guarded(config5_serving, gp, prob, stream)}
     line = {
         "metric": METRIC,
         "value": value,
@@ -425,48 +434,115 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def batched_compare(gp, prob, nodes, offs, stream, flush, steps):
-    """The same population, one generation made on the device (tournament
-    selection, crossover, evaluation; one graph launch) against the plain
-    host-driven path (the same crossover records through gp_crossover +
-    gp_evaluate), both timed with CUDA events, L2 flushed before each."""
+def generations_compare(gp, prob, nodes, offs, stream, flush, K, reps, chunk=0, arena=0):
+    """K consecutive generations from the same parents, made two ways, with
+    identical results (checked): on the device (one gp_generation_step of K
+    generations: tournaments, crossover and evaluation replayed from the
+    captured graph, the host never waiting) and through the plain API as a
+    host-driven GP loop must run it (per generation: gp_crossover on that
+    generation's records, gp_evaluate, and gp_fitness, the read-back the
+    host needs before it can choose the next parents; the records are
+    given, so the host's own selection costs nothing here).  Wall clock
+    around each block of K generations, L2 flushed before it.  Also the
+    plain path replaying one generation's records without any read-back
+    (device time), a bound no host-driven loop reaches."""
     import torch
-    G = gp.gp_generation_create(prob, nodes, offs, seed=21, use_graph=True, stream=stream)
-
-    def time_steps(fn, after):
-        ms = []
-        for _ in range(steps + 3):                    # the first 3 warm up
-            with torch.cuda.stream(stream):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                out = fn()
-                b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-            after(out)
-        return statistics.median(ms[3:])
-
-    g_ms = time_steps(lambda: gp.gp_generation_step(G, 1, stream), lambda _: gp.gp_generation_rewind(G, stream))
-    gp.gp_generation_step(G, 1, stream)
-    recs = gp.gp_generation_records(G)
-    kid_nodes = int(gp.gp_generation_get_info(G)["total_nodes"])
+    kw = dict(seed=SEED_GEN, use_graph=True, stream=stream)
+    if arena:
+        kw["arena_bytes"] = arena
+    G = gp.gp_generation_create(prob, nodes, offs, chunk_nodes=chunk, **kw)
+    info0 = gp.gp_generation_get_info(G)
+    chunk = int(info0["chunk_nodes"])
+    # the records of each generation (untimed pass, one generation at a time)
+    recs = []
+    for _ in range(K):
+        gp.gp_generation_step(G, 1, stream)
+        recs.append(gp.make_xo(*gp.gp_generation_records(G)))
+    want_nodes, want_offs = gp.gp_generation_trees(G)
+    want_fit, _, _ = gp.gp_generation_fitness(G)
+    child_nodes = []
     gp.gp_generation_destroy(G)
+    del G
+
+    def one_batched():
+        G2 = gp.gp_generation_create(prob, nodes, offs, chunk_nodes=chunk, **kw)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        gp.gp_generation_step(G2, K, stream)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        return G2, el
+
+    b_s = []
+    for r in range(reps):
+        G2, el = one_batched()
+        b_s.append(el)
+        if r == reps - 1:
+            got_nodes, got_offs = gp.gp_generation_trees(G2)
+            same_batched = bool(np.array_equal(got_nodes, want_nodes) and np.array_equal(got_offs, want_offs))
+        gp.gp_generation_destroy(G2)
+        del G2
     with torch.cuda.stream(stream):
-        parents = gp.gp_create_population(prob, nodes, offs, stream)
-    xo = gp.make_xo(*recs)
+        first = gp.gp_create_population(prob, nodes, offs, stream)
+    gp.gp_evaluate(first, stream, chunk_nodes=chunk)
+    gp.gp_fitness(first)
+    p_s = []
+    for r in range(reps):
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pop = first
+        for g in range(K):
+            kids = gp.gp_crossover(pop, recs[g], stream)
+            gp.gp_evaluate(kids, stream, chunk_nodes=chunk)
+            fit, _, _ = gp.gp_fitness(kids)           # the host loop's read-back
+            if r == 0:
+                child_nodes.append(int(gp.gp_population_get_info(kids).total_nodes))
+            pop = kids
+        el = time.perf_counter() - t
+        p_s.append(el)
+    plain_nodes, plain_offs = gp.read_all_trees(pop)
+    same_plain = bool(np.array_equal(plain_nodes, want_nodes) and np.array_equal(plain_offs, want_offs)
+                      and np.array_equal(np.asarray(fit).view(np.uint32), np.asarray(want_fit).view(np.uint32)))
+    del pop, kids
+    # one generation's records replayed with no read-back (device time)
+    xo = recs[0]
 
-    def plain():
-        k = gp.gp_crossover(parents, xo, stream)
-        gp.gp_evaluate(k, stream)
+    def replay():
+        k = gp.gp_crossover(first, xo, stream)
+        gp.gp_evaluate(k, stream, chunk_nodes=chunk)
         return k
-
-    p_ms = time_steps(plain, lambda k: None)
-    units = kid_nodes * prob.n_cases
-    return {"workload": "the same 4000 parents; one generation: size-7 tournaments, 4000 crossovers, evaluation",
-            "batched_graph": {"ms_p50": g_ms, "GPops_per_s": units / (g_ms / 1e3)},
-            "plain_host_driven": {"ms_p50": p_ms, "GPops_per_s": units / (p_ms / 1e3)},
-            "speedup": p_ms / g_ms}
+    ms = []
+    for k in range(max(3, reps) + 2):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kk = replay()
+            b.record(stream)
+        b.synchronize()
+        gp.gp_fitness(kk)
+        if k >= 2:
+            ms.append(a.elapsed_time(b))
+        del kk
+    del first
+    torch.cuda.synchronize()
+    units = sum(child_nodes) * prob.n_cases
+    bs, ps = statistics.median(b_s), statistics.median(p_s)
+    return {"generations": K, "blocks": reps, "chunk_nodes": chunk, "child_nodes": sum(child_nodes),
+            "identical_results": same_batched and same_plain,
+            "batched_graph": {"ms_per_generation": 1e3 * bs / K, "GPops_per_s": units / bs},
+            "plain_host_loop": {"ms_per_generation": 1e3 * ps / K, "GPops_per_s": units / ps},
+            "speedup": ps / bs,
+            "plain_records_replayed_no_readback": {
+                "ms_per_generation": statistics.median(ms),
+                "GPops_per_s": child_nodes[0] * prob.n_cases / (statistics.median(ms) / 1e3),
+                "note": "one generation's records replayed, host never waiting (device time)"}}
 
 
 def cpu_baseline(nodes, offs, ops, x, y, c, child_nodes):
@@ -637,6 +713,209 @@ def config3_bloated(gp, prob, stream, cpu):
                                "kind": "oracle",
                                "sample": f"{k} x oracle evaluation of the {len(pick)} smallest trees "
                                          f"({tot} nodes) on {cores} threads, {el:.1f} s"}
+    return out
+
+
+def config4_batched(gp, prob, stream, flush, cpu, steps=3):
+    """The batched generation at full size: 4000 parents of 1e2..1e8 nodes
+    (2.9e10 nodes), generations made on the device (size-7 tournaments,
+    4000 crossovers, evaluation of the children; graph replays) against the
+    plain path as a host loop runs them (generations_compare).  End to end:
+    from the parents in (page-locked) host memory to the children's fitness
+    on the host, through gp_generation_create (upload, validation, the
+    parents' evaluation), one step and gp_generation_fitness."""
+    import torch
+    x, y, c = prob.x, prob.y, prob.consts
+    desc, make = BATCHED["batched"]
+    t0 = time.perf_counter()
+    nodes, offs = make()
+    build_s = time.perf_counter() - t0
+    n = offs.shape[0] - 1
+    sizes = np.diff(offs.astype(np.int64))
+    arena = int(int(np.sum((sizes + 15) // 16 * 16) + 64) * 1.3) + (64 << 20)
+    t0 = time.perf_counter()
+    G = gp.gp_generation_create(prob, nodes, offs, seed=SEED_GEN, arena_bytes=arena, use_graph=True, stream=stream)
+    create_s = time.perf_counter() - t0
+    info0 = gp.gp_generation_get_info(G)
+    gp.gp_generation_step(G, 1, stream)
+    recs = gp.gp_generation_records(G)
+    info1 = gp.gp_generation_get_info(G)
+    chunk = int(info0["chunk_nodes"])
+    gp.gp_generation_destroy(G)
+    del G
+    torch.cuda.synchronize()
+    cmp = generations_compare(gp, prob, nodes, offs, stream, flush, 2, 1, chunk=chunk, arena=arena)
+    child_nodes = int(info1["total_nodes"])
+    # end to end from page-locked host memory (the parents' own pages registered)
+    try:
+        cudart = torch.cuda.cudart()
+        reg = int(cudart.cudaHostRegister(nodes.ctypes.data, nodes.nbytes, 0)) == 0
+    except (AttributeError, RuntimeError, TypeError):
+        cudart, reg = None, False
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    G = gp.gp_generation_create(prob, nodes, offs, seed=SEED_GEN, chunk_nodes=chunk, arena_bytes=arena,
+                                use_graph=True, stream=stream)
+    gp.gp_generation_step(G, 1, stream)
+    gp.gp_generation_fitness(G)
+    e2e_s = time.perf_counter() - t
+    gp.gp_generation_destroy(G)
+    del G
+    if reg:
+        cudart.cudaHostUnregister(nodes.ctypes.data)
+    units = child_nodes * prob.n_cases
+    out = {"workload": desc, "parent_nodes": int(offs[-1]), "child_nodes": child_nodes,
+           "population_build_s": build_s, "create_s": create_s, "chunk_nodes": chunk,
+           "levels": int(info1["levels"]),
+           "batched_vs_plain": cmp,
+           "e2e": {"value": units / e2e_s, "unit": "GPops/s", "wall_s": e2e_s,
+                   "h2d_bytes_per_step": int(nodes.nbytes + 8 * (n + 1)), "d2h_bytes_per_step": 4 * n,
+                   "host_memory": "page-locked" if reg else "pageable",
+                   "note": "upload, validation and evaluation of the parents, one generation, fitness read-back"}}
+    if cpu:
+        from oracle import oracle
+        k = 20
+        mum, dad, mp, dp = (np.asarray(a)[:k] for a in recs)
+        cores = os.cpu_count() or 1
+        t = time.perf_counter()
+        reps, done = 0, 0
+        while time.perf_counter() - t < 10.0:
+            kn, ko = oracle.crossover_population(nodes, offs, mum, dad, mp, dp)
+            oracle.eval_population(kn, ko, x, y, c, n_threads=cores)
+            done += int(ko[-1])
+            reps += 1
+        el = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": done * prob.n_cases / el, "unit": "GPops/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{reps} x (crossover of the first {k} of the generation's records + "
+                                         f"oracle evaluation of those children on {cores} threads), {el:.1f} s"}
+    return out
+
+
+SERVE_POOL = 2000
+
+
+def config5_serving(gp, prob, stream, gens=1, n_runs=64, rate=200.0, budget=150 * 10 ** 9):
+    """The serving loop at the benchmark's sizes: 64 independent runs, each
+    population U{48..4000} trees drawn (with repeats) from a device pool of
+    2000 seeded trees with odd sizes log-uniform on 11..1e8 (the initial
+    populations average 1.4e10 nodes, 880 GB in all, so they are opened
+    from the device pool, not staged on the host), an HBM budget of 150 GB
+    for the runs' population buffers (a few runs fit at once), generation
+    requests in a closed loop per run with exponential think times (Poisson
+    at `rate` per second in aggregate).  Continuous batching against one
+    run per batch on the same arrivals; two runs are then made alone from
+    the same trees and must end identical (bytes and fitness)."""
+    import threading
+    import torch
+    t0 = time.perf_counter()
+    pn, po, _ = synth.graft_population(seed=6, count=SERVE_POOL, lo=11, hi=10 ** 8, donor_lo=10 ** 5,
+                                       donor_hi=10 ** 6, n_donors=32, chain_depth=0)
+    build_s = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        pool = gp.gp_create_population(prob, pn, po, stream)
+    psize = np.diff(po.astype(np.int64))
+    rng = np.random.default_rng(66)
+    picks = [rng.integers(0, SERVE_POOL, size=int(rng.integers(48, 4001))).astype(np.uint32) for _ in range(n_runs)]
+    run_nodes = [int(np.sum(psize[p])) for p in picks]
+    think = n_runs / rate
+    # upper-level workspace from the pool's own fragment density at this
+    # chunk size (codes and value entries per node, all levels summed) for
+    # batches of at most the largest run's nodes, a fifth more to spare
+    C = 16384
+    gp.gp_evaluate(pool, stream, chunk_nodes=C)
+    gp.gp_fitness(pool)
+    es = gp.gp_eval_stats_get(pool)
+    batch_nodes = int(max(run_nodes))
+    ws_codes = int(1.2 * es["upper_codes"] / int(po[-1]) * batch_nodes) + (1 << 20)
+    ws_values = int(1.2 * es["value_entries"] / int(po[-1]) * batch_nodes) + (1 << 18)
+    torch.cuda.synchronize()
+
+    free_b, total_b = torch.cuda.mem_get_info()
+    print(f"serving: pool {int(po[-1])} nodes, stats {es}, largest run {max(run_nodes)}, batch_nodes {batch_nodes}, "
+          f"workspace codes {ws_codes} ({4 * ws_codes / 1e9:.1f} GB) values {ws_values} "
+          f"({192 * 1.125 * ws_values / 1e9:.1f} GB), device free {free_b / 1e9:.1f} of {total_b / 1e9:.1f} GB",
+          file=sys.stderr, flush=True)
+
+    def session(max_batch_runs):
+        srv = gp.gp_server_create(prob, hbm_budget_bytes=budget, max_runs=n_runs, max_batch_trees=1 << 20,
+                                  max_batch_runs=max_batch_runs, chunk_nodes=C, max_batch_nodes=batch_nodes,
+                                  workspace_codes=ws_codes, workspace_values=ws_values)
+        ids = []
+        for k, p in enumerate(picks):
+            used = int(np.sum((psize[p] + 15) // 16 * 16))
+            ids.append(gp.gp_server_open_run_from(srv, pool, p, seed=9000 + k,
+                                                  arena_bytes=int(1.3 * used) + (64 << 20)))
+        errors = []
+
+        def client(k, rid):
+            r_ = np.random.default_rng(77 + k)
+            try:
+                for _ in range(gens):
+                    time.sleep(float(r_.exponential(think)))
+                    r = gp.gp_server_wait(srv, gp.gp_server_submit(srv, rid, 1), timeout_ms=300000.0)
+                    if r["status"] != gp.GP_OK:
+                        errors.append(r["status"])
+                        break
+            except gp.GpError as e:
+                errors.append(e.status)
+            if k not in check:                # a finished run frees room for the waiting ones
+                gp.gp_server_close_run(srv, rid)
+
+        t = time.perf_counter()
+        th = [threading.Thread(target=client, args=(k, rid), daemon=True) for k, rid in enumerate(ids)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join(timeout=max(1.0, 600.0 - (time.perf_counter() - t)))
+        if any(x.is_alive() for x in th):
+            raise RuntimeError("serving session did not finish within 600 s")
+        wall = time.perf_counter() - t
+        st = gp.gp_server_get_stats(srv)
+        return srv, ids, wall, st, errors
+
+    out = {"workload": f"{n_runs} runs, populations U{{48..4000}} trees drawn from a device pool of {SERVE_POOL} "
+                       "seeded trees (odd sizes log-uniform 11..1e8, grown by crossover chains above 1e6; seed 6); "
+                       f"48 cases; {gens} generation(s) per run, one request each after an exponential think "
+                       f"time (Poisson {rate:g}/s in aggregate); HBM budget {budget / 1e9:.0f} GB",
+           "pool_nodes": int(po[-1]), "pool_build_s": build_s, "chunk_nodes": C,
+           "workspace": {"batch_nodes": batch_nodes, "codes": ws_codes, "value_entries": ws_values,
+                         "device_free_gb_before": free_b / 1e9, "device_total_gb": total_b / 1e9},
+           "run_nodes": {"mean": float(np.mean(run_nodes)), "total": int(np.sum(run_nodes))},
+           "generations_per_run": gens,
+           "reduced": f"{gens} generation(s) per run instead of 100: one generation of a run averages about "
+                      "0.5 s of GPU time here, so 64 runs x 100 generations would take about an hour"}
+    check = set(sorted(range(n_runs), key=lambda k: run_nodes[k])[:2])   # made alone afterwards
+    for name, mbr in (("continuous_batching", 0), ("one_run_per_batch", 1)):
+        srv, ids, wall, st, errors = session(mbr)
+        out[name] = {"wall_s": wall, "GPops_per_s_wall": st["child_nodes"] * prob.n_cases / wall,
+                     "GPops_per_s_device": st["child_nodes"] * prob.n_cases / max(st["device_ms"] / 1e3, 1e-9),
+                     "latency_p50_ms": st["latency_p50_ms"], "latency_p99_ms": st["latency_p99_ms"],
+                     "batches": st["batches"], "mean_runs_per_batch": st["mean_runs_per_batch"],
+                     "runs_admitted": st["runs_admitted"], "child_nodes": st["child_nodes"],
+                     "runs_regrown": st["regrown"], "batch_retries": st["retries"], "failed_requests": len(errors)}
+        if name == "continuous_batching":
+            # the two smallest runs, made alone from the same trees, must end identical
+            small = sorted(check)
+            same = True
+            for k in small:
+                tn, to = gp.gp_server_run_trees(srv, ids[k])
+                fa, _, _ = gp.gp_server_run_fitness(srv, ids[k])
+                nodes_k, offs_k = synth.pack([pn[int(po[t]):int(po[t + 1])] for t in picks[k]])
+                G = gp.gp_generation_create(prob, nodes_k, offs_k, seed=9000 + k, chunk_nodes=16384,
+                                            use_graph=True, stream=stream)
+                gp.gp_generation_step(G, gens, stream)
+                an, ao = gp.gp_generation_trees(G)
+                fb, _, _ = gp.gp_generation_fitness(G)
+                gp.gp_generation_destroy(G)
+                same = same and np.array_equal(tn, an) and np.array_equal(to, ao) and \
+                    np.array_equal(fa.view(np.uint32), fb.view(np.uint32))
+            out["alone_check"] = {"runs": [int(k) for k in small], "identical": bool(same)}
+        for k in check:
+            gp.gp_server_close_run(srv, ids[k])
+        gp.gp_server_destroy(srv)
+        del srv
+    del pool
     return out
 
 
@@ -894,6 +1173,27 @@ def serve_session(gp, prob, runs, gens, budget, max_batch_runs, think_mean_s, se
     return wall, st
 
 
+def run_serving_full(args):
+    """The serving configuration at the benchmark's sizes alone (the same leg
+    as in the default line)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1902_09215_gb300 import gp
+    gp.lib()
+    x, y, c = synth.problem(const_seed=CONST_SEED)
+    prob = gp.Problem(x, y, c)
+    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    with ClockSampler(0) as clk:
+        out = config5_serving(gp, prob, stream, gens=args.serve_gens_full)
+    b = out["continuous_batching"]
+    print(json.dumps({"metric": "GPops/s (tree nodes x fitness cases per second), served generations; p50/p99 latency",
+                      "value": b["GPops_per_s_wall"], "unit": "GPops/s", "n_gpus": 1, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic", "config": {"workload": out["workload"]},
+                      "serving": out, "clocks": clk.summary()}))
+
+
 def run_serving(args):
     import torch
     torch.cuda.set_device(0)
@@ -1035,7 +1335,10 @@ def main():
     ap.add_argument("--generations", type=int, default=200, help="generations of the ltee workload")
     ap.add_argument("--time-limit", type=float, default=120.0,
                     help="the ltee workload stops after this many seconds (bloat makes generations slower)")
-    ap.add_argument("--workload", choices=["step4000", "serving", "ltee"] + sorted(BATCHED), default="step4000",
+    ap.add_argument("--serve-gens-full", type=int, default=1,
+                    help="generations per run in the serving-full workload")
+    ap.add_argument("--workload", choices=["step4000", "serving", "serving-full", "ltee"] + sorted(BATCHED),
+                    default="step4000",
                     help="step4000 (default): crossover + evaluation of the 4000-tree population; "
                          "the others time whole generations made on the device")
     ap.add_argument("--chunk", type=int, default=0, help="evaluator chunk for the batched workloads (0 = autotune)")
@@ -1046,7 +1349,8 @@ def main():
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the step4000 workload only"}))
             return
-        {"serving": run_serving, "ltee": run_ltee}.get(args.workload, run_batched)(args)
+        {"serving": run_serving, "serving-full": run_serving_full, "ltee": run_ltee}.get(args.workload,
+                                                                                       run_batched)(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -393,6 +393,16 @@ gp_status gp_server_create(const gp_problem *problem, const gp_server_params *pa
  * the other fields are ignored.  GP_ENOMEM if the run can never fit. */
 gp_status gp_server_open_run(gp_server *s, const gp_generation_params *params, uint32_t n_trees,
                              const uint8_t *nodes, const uint64_t *offsets, uint64_t *run_id);
+/* Open a run whose initial population is trees[0..n_trees) of the device
+ * population `src` (indices may repeat), for initial populations too large
+ * to stage on the host: nothing is copied now; at admission the trees are
+ * copied on the device from `src`, which must stay alive, and not be
+ * destroyed, until the run is admitted (gp_server_get_stats: runs_admitted)
+ * or closed.  `src` was validated when it was made, so the trees are not
+ * checked again.  Same params and errors as gp_server_open_run; GP_EINVAL
+ * for an index past src's trees or a different number of fitness cases. */
+gp_status gp_server_open_run_from(gp_server *s, const gp_generation_params *params, const gp_population *src,
+                                  uint32_t n_trees, const uint32_t *trees, uint64_t *run_id);
 /* Ask for `n_generations` (>= 1) more generations of a run; returns at
  * once with the request's id.  GP_EINVAL for an unknown run or zero
  * generations; the run's failure status if it has failed. */

@@ -472,6 +472,50 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace gpk {
+
+// Copies trees `trees[0..n)` of population `src` to dst + dst_lo onward, each
+// at a 16-byte aligned offset (enqueued on s; synchronises only to bring a
+// device-only layout to the host).  Writes each tree's offset from dst and
+// size; GP_ENOMEM when they need more than `cap` bytes from dst_lo.
+gp_status gather_trees(const gp_population *srcc, const uint32_t *trees, uint32_t n, uint8_t *dst, uint64_t dst_lo,
+                       uint64_t cap, uint64_t *start, uint64_t *size, cudaStream_t s)
+{
+    gp_population *src = const_cast<gp_population *>(srcc);
+    if (!src || (n && !trees)) return GP_EINVAL;
+    gp_status st = ensure_host_layout(src);
+    if (st) return st;
+    std::vector<XoChild> kids(n);
+    uint64_t pos = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t t = trees[k];
+        if (t >= src->n_trees) return GP_EINVAL;
+        XoChild c{};
+        c.dst = dst_lo + pos;
+        c.n = src->h_size[t];
+        c.head_src = src->h_start[t];
+        c.i = c.n;                            // the whole tree is the head segment
+        kids[k] = c;
+        start[k] = c.dst;
+        size[k] = c.n;
+        pos = round_up(pos + c.n, 16);
+    }
+    if (pos + 64 > cap) return GP_ENOMEM;
+    if (src->stream && src->stream != s) {    // the source's last writer first
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaEventRecord(e, src->stream);
+        cudaStreamWaitEvent(s, e, 0);
+        cudaEventDestroy(e);
+    }
+    DevBufs tmp;
+    st = run_copy(src->d_arena, dst, kids, s, tmp);
+    tmp.release(s);
+    return st;
+}
+
+}  // namespace gpk
+
 // ================================================================= ABI
 
 extern "C" {

@@ -762,6 +762,18 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     heap_bytes = heap_bytes_;
     GK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     for (cudaStream_t &b : cap_body) GK(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+    // The engine's buffers come from cudaMalloc: memory that the stream-ordered
+    // pool kept after earlier populations were freed is handed back first.
+    {
+        cudaMemPool_t pool;
+        if (cudaDeviceSynchronize() == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess)
+            cudaMemPoolTrimTo(pool, 0);
+        const char *vb = std::getenv("GP_VERBOSE");
+        size_t fr = 0, tot = 0;
+        if (vb && vb[0] == '1' && cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+            std::fprintf(stderr, "engine init: %.1f of %.1f GB free; heap %.1f GB\n", fr / 1e9, tot / 1e9,
+                         heap_bytes / 1e9);
+    }
     // launch shape as in gp_evaluate
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -1047,6 +1059,33 @@ gp_status Engine::load_run(uint32_t r, const uint8_t *nodes, const uint64_t *off
     return e == cudaSuccess ? GP_OK : gfail(e);
 }
 
+gp_status Engine::load_run_from(uint32_t r, const gp_population *src, const uint32_t *trees, cudaStream_t s)
+{
+    if (r >= max_runs || !runs_host[r].used || !src || !trees) return GP_EINVAL;
+    RunHost &H = runs_host[r];
+    const uint32_t n = H.n;
+    std::vector<uint64_t> hstart(n), hsize(n);
+    gp_status st = gpk::gather_trees(src, trees, n, heap, H.lo[0], H.arena_cap, hstart.data(), hsize.data(), s);
+    if (st) return st;
+    uint64_t total = 0;
+    for (uint64_t z : hsize) total += z;
+    RunDev D{};
+    cudaError_t e = cudaMemcpyAsync(&D, runs_dev + r, sizeof(D), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(D.buf[0].start, hstart.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(D.buf[0].size, hsize.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s);
+    D.gen = 0;
+    D.cur = 0;
+    D.err = 0;
+    D.err_gen = 0;
+    D.nodes = total;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(runs_dev + r, &D, sizeof(D), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);    // the host arrays are read by then
+    return e == cudaSuccess ? GP_OK : gfail(e);
+}
+
 gp_status Engine::set_slots(uint64_t cap_slots, uint32_t fz_cap_pt)
 {
     cudaDeviceSynchronize();
@@ -1106,6 +1145,12 @@ gp_status Engine::set_workspace(uint32_t C, const uint64_t cap_codes[2], const u
     }
     if ((st = galloc(v, (void **)&w.spill, sizeof(float2) * lanes * (w.spill_base + w.cap_dedicated)))) return st;
     if ((st = set_slots(cap_slots, fz_cap_pt))) return st;
+    const char *vb = std::getenv("GP_VERBOSE");
+    size_t fr = 0, tot = 0;
+    if (vb && vb[0] == '1' && cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+        std::fprintf(stderr, "engine workspace: codes %.1f GB, values %.1f GB, spill %.1f GB; %.1f GB free\n",
+                     4.0 * (cap_codes[0] + cap_codes[1]) / 1e9, 8.0 * lanes * (cap_values[0] + cap_values[1]) / 1e9,
+                     8.0 * lanes * (w.spill_base + w.cap_dedicated) / 1e9, fr / 1e9);
     // the graphs captured the old workspace
     for (auto &e : exec)
         if (e) {

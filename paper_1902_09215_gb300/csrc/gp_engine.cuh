@@ -17,6 +17,13 @@
 #include "gp.h"
 #include "gp_internal.cuh"
 
+namespace gpk {
+// Trees of a device population copied into device memory at 16-byte aligned
+// offsets from dst + dst_lo (gp_api.cu).
+gp_status gather_trees(const gp_population *src, const uint32_t *trees, uint32_t n, uint8_t *dst, uint64_t dst_lo,
+                       uint64_t cap, uint64_t *start, uint64_t *size, cudaStream_t s);
+}  // namespace gpk
+
 namespace gpe {
 
 using gpk::EvalItem;
@@ -131,6 +138,8 @@ class Engine {
     // Upload, validate and lay out a run's initial population (generation 0,
     // not evaluated).
     gp_status load_run(uint32_t run, const uint8_t *nodes, const uint64_t *offsets, cudaStream_t s);
+    // The same from trees of a device population (validated when it was made).
+    gp_status load_run_from(uint32_t run, const gp_population *src, const uint32_t *trees, cudaStream_t s);
     // cap_slots: fused chunk slots (0: every multi-chunk tree is planned);
     // fz_cap_pt: value entries per slot (0: max(128, C / 8)).
     gp_status set_workspace(uint32_t C, const uint64_t cap_codes[2], const uint64_t cap_values[2],

@@ -51,6 +51,8 @@ struct Run {
     uint64_t nodes = 0, arena = 0, seed = 0;
     std::vector<uint8_t> h_nodes;      // the initial trees, until admitted
     std::vector<uint64_t> h_offs;
+    const gp_population *src = nullptr; // or trees of a device population, until admitted
+    std::vector<uint32_t> src_trees;
     std::deque<uint64_t> pending;      // request ids, oldest first
     bool in_batch = false;
     bool needs_room = false;           // outgrew its buffers; waits for a larger pair
@@ -112,7 +114,9 @@ void admit(gp_server *S)
         uint32_t slot = 0;
         gp_status st = S->eng.open_run(R.n, R.arena, R.seed, R.tsize, S->max_nodes, &slot);
         if (st == GP_ENOMEM) break;                          // first come, first served
-        if (!st) st = S->eng.load_run(slot, R.h_nodes.data(), R.h_offs.data(), S->stream);
+        if (!st)
+            st = R.src ? S->eng.load_run_from(slot, R.src, R.src_trees.data(), S->stream)
+                       : S->eng.load_run(slot, R.h_nodes.data(), R.h_offs.data(), S->stream);
         if (!st) st = S->eng.enqueue(kModeEvaluate, {slot}, S->stream, false, nullptr);
         RunDev D{};
         if (!st) st = S->eng.read_run(slot, &D, S->stream);
@@ -127,6 +131,8 @@ void admit(gp_server *S)
         R.nodes = D.nodes;
         std::vector<uint8_t>().swap(R.h_nodes);
         std::vector<uint64_t>().swap(R.h_offs);
+        std::vector<uint32_t>().swap(R.src_trees);
+        R.src = nullptr;
         ++S->st.runs_admitted;
     }
 }
@@ -348,7 +354,9 @@ gp_status gp_server_create(const gp_problem *problem, const gp_server_params *pa
     // they last, the rest planned): one per chunk of about an eighth of a
     // full batch, at most 8192
     const uint64_t fz_slots = std::max<uint64_t>(256, std::min<uint64_t>(N / p.chunk_nodes / 8, 8192));
-    if (!st) st = S->eng.set_workspace(p.chunk_nodes, codes, vals, std::max<uint64_t>(codes[0] / 4, 1u << 20),
+    // dedicated spill for upper-tree finals above one chunk: a sixteenth of
+    // the code workspace (entries of 8 B per lane each)
+    if (!st) st = S->eng.set_workspace(p.chunk_nodes, codes, vals, std::max<uint64_t>(codes[0] / 16, 1u << 20),
                                        N / p.chunk_nodes + p.max_batch_trees + 1024, fz_slots);
     if (!st && p.use_graph) st = S->eng.capture(kModeGenerate);
     if (!st && (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -386,6 +394,42 @@ gp_status gp_server_open_run(gp_server *S, const gp_generation_params *params, u
     R.h_nodes.assign(nodes, nodes + offsets[n_trees]);
     R.h_offs.assign(offsets, offsets + n_trees + 1);
     R.nodes = offsets[n_trees];
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        R.id = S->next_run++;
+        *run_id = R.id;
+        S->runs.emplace(R.id, std::move(R));
+    }
+    S->cv_work.notify_all();
+    return GP_OK;
+}
+
+gp_status gp_server_open_run_from(gp_server *S, const gp_generation_params *params, const gp_population *src,
+                                  uint32_t n_trees, const uint32_t *trees, uint64_t *run_id)
+{
+    if (!S || !params || !src || !trees || !run_id || n_trees == 0) return GP_EINVAL;
+    if (params->tournament_size < 1 || params->tournament_size > 32) return GP_EINVAL;
+    if (n_trees > S->prm.max_batch_trees) return GP_EINVAL;
+    gp_population_info pi{};
+    if (gp_population_get_info(src, &pi) != GP_OK) return GP_EINVAL;
+    if (pi.n_cases != S->eng.n_cases) return GP_EINVAL;
+    uint64_t used = 0, nodes = 0;
+    for (uint32_t k = 0; k < n_trees; ++k) {
+        uint64_t z = 0;
+        if (trees[k] >= pi.n_trees || gp_tree_size(src, trees[k], &z) != GP_OK) return GP_EINVAL;
+        used = (used + z + 15) & ~15ull;
+        nodes += z;
+    }
+    Run R;
+    R.n = n_trees;
+    R.tsize = params->tournament_size;
+    R.seed = params->seed;
+    R.arena = params->arena_bytes ? params->arena_bytes : 2 * used + 16ull * n_trees + (1u << 20);
+    if (R.arena < used + 64) return GP_ENOMEM;
+    if (2 * ((R.arena + 255) & ~255ull) > S->prm.hbm_budget_bytes) return GP_ENOMEM;   // can never fit
+    R.src = src;
+    R.src_trees.assign(trees, trees + n_trees);
+    R.nodes = nodes;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         R.id = S->next_run++;

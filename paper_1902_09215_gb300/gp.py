@@ -28,7 +28,7 @@ EXPORTED = [
     "gp_generation_records", "gp_generation_trees", "gp_generation_tree_read", "gp_generation_get_info",
     "gp_generation_destroy",
     "gp_generation_recover",
-    "gp_server_create", "gp_server_open_run", "gp_server_submit", "gp_server_wait", "gp_server_run_fitness",
+    "gp_server_create", "gp_server_open_run", "gp_server_open_run_from", "gp_server_submit", "gp_server_wait", "gp_server_run_fitness",
     "gp_server_run_trees", "gp_server_close_run", "gp_server_get_stats", "gp_server_destroy",
 ]
 NOALLOC_MAX_TREES = 16384
@@ -158,6 +158,8 @@ def lib():
             L.gp_server_create.argtypes = [P(gp_problem), P(gp_server_params), P(vp)]
             L.gp_server_open_run.argtypes = [vp, P(gp_generation_params), C.c_uint32, P(C.c_uint8),
                                              P(C.c_uint64), P(C.c_uint64)]
+            L.gp_server_open_run_from.argtypes = [vp, P(gp_generation_params), vp, C.c_uint32, P(C.c_uint32),
+                                                  P(C.c_uint64)]
             L.gp_server_submit.argtypes = [vp, C.c_uint64, C.c_uint32, P(C.c_uint64)]
             L.gp_server_wait.argtypes = [vp, C.c_uint64, C.c_double, P(gp_server_result)]
             L.gp_server_run_fitness.argtypes = [vp, C.c_uint64, P(C.c_float), P(C.c_float), P(C.c_uint32)]
@@ -478,6 +480,7 @@ class Server:
         self.n_cases = n_cases
         self.problem = None          # kept alive with the server
         self.run_trees = {}          # run id -> number of trees
+        self.sources = {}            # run id -> the population its initial trees come from
 
     def __del__(self):
         h, self._h = getattr(self, "_h", None), None
@@ -507,6 +510,19 @@ def gp_server_open_run(srv: Server, nodes, offsets, seed, tournament_size=7, are
     _check(lib().gp_server_open_run(srv._h, C.byref(prm), n, _ptr(nodes, C.c_uint8), _ptr(offsets, C.c_uint64),
                                     C.byref(rid)), "gp_server_open_run")
     srv.run_trees[rid.value] = n
+    return rid.value
+
+
+def gp_server_open_run_from(srv: Server, pop: Population, trees, seed, tournament_size=7, arena_bytes=0) -> int:
+    """A run whose initial trees are `trees` (indices into `pop`, which must
+    stay alive until the run is admitted or closed)."""
+    trees = np.ascontiguousarray(trees, dtype=np.uint32)
+    prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), 0, int(arena_bytes), 0, 0, 0, 0)
+    rid = C.c_uint64()
+    _check(lib().gp_server_open_run_from(srv._h, C.byref(prm), pop._h, trees.shape[0], _ptr(trees, C.c_uint32),
+                                         C.byref(rid)), "gp_server_open_run_from")
+    srv.run_trees[rid.value] = int(trees.shape[0])
+    srv.sources[rid.value] = pop              # kept alive with the run
     return rid.value
 
 
@@ -546,6 +562,7 @@ def gp_server_run_trees(srv: Server, run_id):
 def gp_server_close_run(srv: Server, run_id):
     _check(lib().gp_server_close_run(srv._h, int(run_id)), "gp_server_close_run")
     srv.run_trees.pop(run_id, None)
+    srv.sources.pop(run_id, None)
 
 
 def gp_server_get_stats(srv: Server) -> dict:

@@ -287,3 +287,38 @@ def test_two_waiters_on_one_request(gpu):
     assert sorted(outcome) == sorted([gpu.GP_OK, gpu.GP_EINVAL])
     gpu.gp_server_close_run(srv, rid)
     gpu.gp_server_destroy(srv)
+
+
+def test_runs_opened_from_a_device_population_equal_runs_from_host_trees(gpu):
+    """A run whose initial trees are picked (with repeats) from a device
+    population ends, after two served generations, exactly where the same
+    trees opened from host memory end: every tree's bytes and fitness."""
+    import torch
+    s = torch.cuda.current_stream()
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    pool_nodes, pool_offs = synth.population_loguniform(seed=61, count=300, lo=11, hi=20001)
+    pool = gpu.gp_create_population(prob, pool_nodes, pool_offs, s)
+    rng = np.random.default_rng(5)
+    picks = [rng.integers(0, 300, size=int(rng.integers(48, 200))).astype(np.uint32) for _ in range(3)]
+    srv = gpu.gp_server_create(prob, hbm_budget_bytes=1 << 30, max_runs=8, chunk_nodes=4096)
+    dev_ids = [gpu.gp_server_open_run_from(srv, pool, p, seed=700 + k) for k, p in enumerate(picks)]
+    host_ids = []
+    for k, p in enumerate(picks):
+        nodes, offs = synth.pack([pool_nodes[int(pool_offs[t]):int(pool_offs[t + 1])] for t in p])
+        host_ids.append(gpu.gp_server_open_run(srv, nodes, offs, seed=700 + k))
+    reqs = [gpu.gp_server_submit(srv, rid, 2) for rid in dev_ids + host_ids]
+    for q in reqs:
+        assert gpu.gp_server_wait(srv, q)["status"] == gpu.GP_OK
+    for a, b in zip(dev_ids, host_ids):
+        ta, tb = gpu.gp_server_run_trees(srv, a), gpu.gp_server_run_trees(srv, b)
+        assert np.array_equal(ta[0], tb[0]) and np.array_equal(ta[1], tb[1])
+        fa, _, _ = gpu.gp_server_run_fitness(srv, a)
+        fb, _, _ = gpu.gp_server_run_fitness(srv, b)
+        assert same_f32(fa, fb)
+    with pytest.raises(gpu.GpError) as e:                 # an index past the population
+        gpu.gp_server_open_run_from(srv, pool, np.array([0, 300], np.uint32), seed=1)
+    assert e.value.status == gpu.GP_EINVAL
+    for rid in dev_ids + host_ids:
+        gpu.gp_server_close_run(srv, rid)
+    gpu.gp_server_destroy(srv)
