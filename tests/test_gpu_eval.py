@@ -222,3 +222,34 @@ def test_operators_sent_upward_follow_the_arity_walk(gpu, oracle, C):
     assert same_f32(fit, oracle.eval_population(kn, ko, x, y, c, n_threads=8)["fitness"])
     kt = [kn[int(ko[i]):int(ko[i + 1])] for i in range(60)]
     assert gpu.gp_eval_stats_get(kids)["upper_ops"] == sum(spine_operators(t, C) for t in kt)
+
+
+def test_slot_overflow_is_evaluated_again_in_gp_fitness(gpu, oracle):
+    """Left-spine trees whose chunks leave more complete subtrees on the
+    stack than a fused chunk's slot holds (a slot keeps max(128, C/8) value
+    entries): gp_evaluate queues them, gp_fitness evaluates them again
+    through planned levels (redone > 0), and every result equals the
+    oracle's; for uploaded trees and for crossover children sized on the
+    device (mum point 0 and dad point 0 copy the dad whole)."""
+    import torch
+    s = torch.cuda.current_stream()
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    rng = np.random.default_rng(17)
+    trees = [synth.left_spine_tree(rng, 3000, 3) for _ in range(3)] + \
+        [synth.random_tree(rng, int(n)) for n in (31, 4095, 9001, 20001)]
+    nodes, offs = synth.pack(trees)
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=8)
+    st = check(gpu, oracle, nodes, offs, x, y, c, chunk_nodes=4096)
+    assert st["redone"] >= 3
+    pop = gpu.gp_create_population(prob, nodes, offs, s)
+    n = len(trees)
+    idx = np.arange(n, dtype=np.uint32)
+    zero = np.zeros(n, np.uint64)
+    kids = gpu.gp_crossover(pop, (idx, idx, zero, zero), s)
+    gpu.gp_evaluate(kids, s, chunk_nodes=4096)
+    fit, vals, hits = gpu.gp_fitness(kids, case_values=True, hits=True)
+    assert gpu.gp_eval_stats_get(kids)["redone"] >= 3
+    assert same_f32(vals, ref["out"]), first_mismatch(vals, ref["out"])
+    assert same_f32(fit, ref["fitness"])
+    assert np.array_equal(hits, ref["hits"])
