@@ -368,6 +368,7 @@ def run_ours(args):
                 return {"error": f"{type(e).__name__}: {e}"}
         configs = {"smallest_50_trees": guarded(config1_latency, gp, prob, stream, 300, not args.no_cpu),
                    "bloated_48_trees": guarded(config3_bloated, gp, prob, stream, not args.no_cpu),
+                   "crossover_large_children": guarded(crossover_large, gp, prob, stream, flush),
                    "batched_4000_parents_1e2_1e8": guarded(config4_batched, gp, prob, stream, flush,
                                                            not args.no_cpu),
                    "serving_64_runs": guarded(config5_serving, gp, prob, stream)}
@@ -535,6 +536,8 @@ def generations_compare(gp, prob, nodes, offs, stream, flush, K, reps, chunk=0, 
     units = sum(child_nodes) * prob.n_cases
     bs, ps = statistics.median(b_s), statistics.median(p_s)
     return {"generations": K, "blocks": reps, "chunk_nodes": chunk, "child_nodes": sum(child_nodes),
+            "launch_shape": {"level0": [info0["warps_per_cta"], info0["window_entries"]],
+                             "upper": [info0["upper_warps"], info0["upper_window_entries"]]},
             "identical_results": same_batched and same_plain,
             "batched_graph": {"ms_per_generation": 1e3 * bs / K, "GPops_per_s": units / bs},
             "plain_host_loop": {"ms_per_generation": 1e3 * ps / K, "GPops_per_s": units / ps},
@@ -790,6 +793,51 @@ def config4_batched(gp, prob, stream, flush, cpu, steps=3):
                                "sample": f"{reps} x (crossover of the first {k} of the generation's records + "
                                          f"oracle evaluation of those children on {cores} threads), {el:.1f} s"}
     return out
+
+
+def crossover_large(gp, prob, stream, flush, reps=10):
+    """Subtree crossover alone on large children: 2000 parents of 1e4..1e6
+    nodes (crossover chains from 32 random donors of 1e4..1e5 nodes; seed 8),
+    2000 children at uniform points (seed 13).  The copy kernel is bound by
+    HBM: algorithmic bytes = the child bytes read + written."""
+    import torch
+    nodes, offs, _ = synth.graft_population(seed=8, count=2000, lo=10 ** 4, hi=10 ** 6, donor_lo=10 ** 4,
+                                            donor_hi=10 ** 5, n_donors=32, chain_depth=0)
+    with torch.cuda.stream(stream):
+        parents = gp.gp_create_population(prob, nodes, offs, stream)
+    sizes = np.diff(offs.astype(np.int64))
+    xo = gp.make_xo(*synth.crossover_points(13, sizes, 2000))
+    for _ in range(2):
+        k = gp.gp_crossover(parents, xo, stream)
+    child_bytes = int(gp.gp_population_get_info(k).total_nodes)
+    del k
+    torch.cuda.synchronize()
+    gp.gp_profile_read(reset=True)
+    gp.gp_profile_enable(True)
+    ms = []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            k = gp.gp_crossover(parents, xo, stream)
+            b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        del k
+    gp.gp_profile_enable(False)
+    prof = gp.gp_profile_read(reset=True)
+    del parents
+    copy_ms = prof["copy"]["ms"] / max(prof["copy"]["launches"], 1)
+    peaks, src = measured_peaks()
+    gbs = 2 * child_bytes / (copy_ms / 1e3) / 1e9
+    return {"workload": "2000 parents, odd sizes log-uniform 1e4..1e6 (seed 8), 2000 children at uniform points "
+                        "(seed 13), L2 flushed before each crossover",
+            "child_bytes": child_bytes, "gp_crossover_ms_p50": statistics.median(ms),
+            "kernel_ms_per_launch": {k_: v["ms"] / v["launches"] for k_, v in prof.items() if v["launches"]},
+            "roofline": {"bound": "hbm", "kernel": "xo_copy_map_kernel", "achieved": gbs,
+                         "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": gbs / float(peaks["hbm_gbs"]),
+                         "note": f"child bytes read + written / copy launch time; peak {src}"}}
 
 
 SERVE_POOL = 2000
@@ -1101,6 +1149,11 @@ def run_batched(args):
                    "population_build_s": gen_s, "create_s": create_s},
         "latency_ms": {"p50": med, "p99": nearest_rank(ms, 0.99), "rule": f"nearest rank over {len(ms)} steps"},
         "autotune": {str(k): v for k, v in zip(info0["autotune_chunk"], info0["autotune_ms"]) if k},
+        "autotune_shape": {f"{w}x{k}": v for (w, k), v in zip(info0["autotune_shape"], info0["autotune_shape_ms"])
+                           if w},
+        "launch_shape": {"level0": [info0["warps_per_cta"], info0["window_entries"]],
+                         "upper": [info0["upper_warps"], info0["upper_window_entries"]],
+                         "ropes": [info0["rope_warps"], info0["rope_window_entries"]]},
         "clocks": clk.summary(),
         "e2e": {"value": units / statistics.median(te), "unit": "GPops/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * n, "wall_s_p50": statistics.median(te),

@@ -89,8 +89,10 @@ typedef struct gp_population gp_population;
 /* Upload `n_trees` trees (packed: tree t is nodes[offsets[t] .. offsets[t+1]),
  * offsets has n_trees+1 entries, offsets[0] = 0) and validate them on the
  * device (Sec. 2.1 encoding: every tree is exactly one prefix tree and uses
- * only codes < 5 + n_consts).  Synchronises with `cuda_stream` once to read
- * the validation result.  n_trees may be 0.
+ * only codes < 5 + n_consts).  `nodes` may be host memory or device memory
+ * of this device (e.g. trees received from another process); `offsets` is
+ * host memory.  Synchronises with `cuda_stream` once to read the validation
+ * result.  n_trees may be 0.
  * Errors: GP_EINVAL (null/inconsistent arguments), GP_EMALFORMED (a tree
  * fails validation), GP_ENOMEM (allocation or budget), GP_ECUDA. */
 gp_status gp_create_population(const gp_problem *problem, uint32_t n_trees,
@@ -161,6 +163,23 @@ void gp_destroy_population(gp_population *pop);
 
 /* Static, human-readable name of a status. */
 const char *gp_status_string(gp_status st);
+
+/* Tournament selection of both parents and uniform crossover points
+ * (Table gp.details: tournaments of `tournament_size`, lowest MAE wins, NaN
+ * worst, ties to the entrant drawn first; Sec. 3.1: points uniform over each
+ * parent's nodes) for children [child_lo, child_lo + n_children) of
+ * generation `generation` of a run seeded `seed`, from the fitness and node
+ * counts of the whole population of n_pop trees: the same counter-based
+ * draws a gp_generation step makes, so a population sharded over processes
+ * selects each process's children from gathered fitness and sizes and gets
+ * the records a single process would.  d_fitness [n_pop], d_sizes [n_pop]
+ * and d_out [n_children] (global parent indices and points) are device
+ * memory; asynchronous on cuda_stream.  Errors: GP_EINVAL (null pointers,
+ * tournament size outside 1..32, generation >= 2^24, children past 2^28),
+ * GP_ECUDA. */
+gp_status gp_select(const float *d_fitness, const uint64_t *d_sizes, uint32_t n_pop, uint64_t seed,
+                    uint32_t generation, uint32_t child_lo, uint32_t n_children, uint32_t tournament_size,
+                    gp_xo *d_out, void *cuda_stream);
 
 /* ---- Introspection and measurement (not part of the paper's method). ---- */
 
@@ -245,9 +264,16 @@ typedef struct gp_generation_params {
                                     initial population needs, at least 2^20             */
     uint64_t workspace_values;   /* value-buffer entries per level; 0 = as above        */
     uint32_t use_graph;          /* nonzero: replay one CUDA graph per generation        */
-    uint32_t max_levels;         /* evaluation levels per generation (2..16); 0 = those
-                                    of generation 0 plus two (3..8), widened by two
+    uint32_t max_levels;         /* evaluation levels per generation (2..16); 0 = eight
+                                    for the captured level loop, those of generation 0
+                                    plus two (3..8) for plain launches, widened by two
                                     when a generation uses them all                     */
+    uint32_t warps_per_cta;      /* level-0 evaluator warps per SM (1..32) and       */
+    uint32_t window_entries;     /* shared-memory stack entries per warp (even, >= 16);
+                                    both 0 = autotuned on the initial population      */
+    uint32_t upper_window_entries; /* upper-level window (its warps: as many as fit,
+                                    at most 16); 0 = autotuned                         */
+    uint32_t pad;
 } gp_generation_params;
 
 typedef struct gp_generation_info {
@@ -262,6 +288,12 @@ typedef struct gp_generation_info {
     uint64_t arena_bytes, workspace_codes, workspace_values;
     uint32_t autotune_chunk[8];  /* candidate chunk sizes tried (0 = unused slot)       */
     float autotune_ms[8];        /* their evaluation time on the initial population     */
+    uint32_t warps_per_cta, window_entries;             /* level 0's launch shape in use  */
+    uint32_t upper_warps, upper_window_entries;         /* upper levels'                  */
+    uint32_t rope_warps, rope_window_entries;           /* a rope-only level's            */
+    uint32_t autotune_shape[8];  /* shapes tried, (warps << 16) | window entries: level 0's
+                                    first, then the upper levels' (0 = unused slot)     */
+    float autotune_shape_ms[8];  /* their evaluation time on the initial population     */
 } gp_generation_info;
 
 /* Upload, validate and evaluate the initial population (generation 0) of

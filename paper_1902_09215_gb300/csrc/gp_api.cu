@@ -566,7 +566,7 @@ gp_status gp_create_population(const gp_problem *problem, uint32_t n_trees, cons
         std::vector<XoChild> kids(n_trees);
         auto run = [&]() -> gp_status {
             CK(tmp.alloc((void **)&d_stage, packed + 64, s));
-            CK(cudaMemcpyAsync(d_stage, nodes, packed, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(d_stage, nodes, packed, cudaMemcpyDefault, s));   // host or device bytes
             for (uint32_t t = 0; t < n_trees; ++t) {
                 XoChild &k = kids[t];
                 k = XoChild{};

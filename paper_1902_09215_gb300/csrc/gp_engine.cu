@@ -127,6 +127,23 @@ __global__ void select_kernel(BatchCtl *ctl, RunDev *runs, const uint32_t *__res
     }
 }
 
+// Records of children [lo, lo + n) of generation g, from the whole
+// population's fitness and sizes (gp_select).
+__global__ void select_range_kernel(const float *__restrict__ fit, const uint64_t *__restrict__ size,
+                                    uint32_t n_pop, uint64_t seed, uint32_t g, uint32_t lo, uint32_t n,
+                                    uint32_t tsize, gp_xo *__restrict__ out)
+{
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t c = lo + k;
+        gp_xo r;
+        r.mum = tournament(fit, n_pop, seed, g, c, 0, tsize);
+        r.dad = tournament(fit, n_pop, seed, g, c, 1, tsize);
+        r.mum_point = bounded(seed, draw_counter(g, c, 2, 0), size[r.mum]);
+        r.dad_point = bounded(seed, draw_counter(g, c, 3, 0), size[r.dad]);
+        out[k] = r;
+    }
+}
+
 // Block-wide inclusive scan of two 64-bit values per thread (kScanT
 // threads): warp scans by shuffles, a scan of the 32 warp totals by warp 0,
 // then each thread's warp offset; the results land in sa[t], sb[t] (the
@@ -728,6 +745,16 @@ int lanes_of(uint32_t n_cases)
 
 }  // namespace
 
+cudaError_t launch_select_range(const float *fit, const uint64_t *size, uint32_t n_pop, uint64_t seed, uint32_t g,
+                                uint32_t lo, uint32_t n, uint32_t tsize, gp_xo *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint32_t blocks = std::min<uint32_t>((n + 127) / 128, 4096);
+    select_range_kernel<<<blocks, 128, 0, s>>>(fit, size, n_pop, seed, g, lo, n, tsize, out);
+    return cudaGetLastError();
+}
+
+
 // ---- Engine -----------------------------------------------------------------
 
 Engine::~Engine()
@@ -1086,6 +1113,34 @@ gp_status Engine::load_run_from(uint32_t r, const gp_population *src, const uint
     return e == cudaSuccess ? GP_OK : gfail(e);
 }
 
+gp_status Engine::set_shape(uint32_t W_, uint32_t K_, uint32_t Wu_, uint32_t Ku_, uint32_t Wr_, uint32_t Kr_)
+{
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    auto ok = [&](uint32_t w, uint32_t k, bool wide) {
+        return w >= 1 && w <= 32 && k >= 16 && k % 2 == 0 && k <= 1024 && (!wide || w <= 16) &&
+               eval_smem_bytes(lanes, (int)w, (int)k, wide, rows) <= (size_t)maxsm;
+    };
+    if (!ok(W_, K_, false) || !ok(Wu_, Ku_, true) || !ok(Wr_, Kr_, true)) return GP_EINVAL;
+    W = W_;
+    K = K_;
+    Wu = Wu_;
+    Ku = Ku_;
+    Wr = Wr_;
+    Kr = Kr_;
+    smem = eval_smem_bytes(lanes, (int)W, (int)K, false, rows);
+    smem_u = eval_smem_bytes(lanes, (int)Wu, (int)Ku, true, rows);
+    smem_r = eval_smem_bytes(lanes, (int)Wr, (int)Kr, true, rows);
+    GK(eval_prepare_at_least(lanes, false, smem));
+    GK(eval_prepare_at_least(lanes, true, std::max(smem_u, smem_r)));
+    for (auto &e : exec)                 // the graphs captured the old shapes
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    return GP_OK;
+}
+
 gp_status Engine::set_slots(uint64_t cap_slots, uint32_t fz_cap_pt)
 {
     cudaDeviceSynchronize();
@@ -1131,7 +1186,7 @@ gp_status Engine::set_workspace(uint32_t C, const uint64_t cap_codes[2], const u
     w.cap_items = cap_items;
     w.cap_dedicated = cap_dedicated;
     if (w.cap_items > 0xffffffffull) return GP_ENOMEM;
-    const uint64_t warps = (uint64_t)sms * std::max(W, Wu);
+    const uint64_t warps = (uint64_t)sms * std::max(W, std::max(Wu, Wr));
     w.spill_per_warp = C;
     w.spill_base = warps * C;
     auto &v = work_allocs_;

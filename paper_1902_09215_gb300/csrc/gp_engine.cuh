@@ -117,6 +117,12 @@ struct Work {
     float2 *fz_pt = nullptr;
 };
 
+// Records (size-`tsize` tournaments of both parents, uniform points) of
+// children [lo, lo + n) of generation g from the whole population's
+// fitness and sizes, as a generation step draws them (gp_select).
+cudaError_t launch_select_range(const float *fit, const uint64_t *size, uint32_t n_pop, uint64_t seed, uint32_t g,
+                                uint32_t lo, uint32_t n, uint32_t tsize, gp_xo *out, cudaStream_t s);
+
 class Engine {
   public:
     ~Engine();
@@ -147,6 +153,12 @@ class Engine {
                             uint32_t fz_cap_pt = 0);
     // Replace the fused slots by cap_slots slots of fz_cap_pt entries each.
     gp_status set_slots(uint64_t cap_slots, uint32_t fz_cap_pt);
+    // Evaluator launch shapes: warps per SM and window entries of level 0
+    // (W, K), of the upper levels (Wu, Ku) and of a rope-only launch (Wr,
+    // Kr); GP_EINVAL if a shape does not fit shared memory.  Call
+    // set_workspace afterwards (the per-warp spill areas follow W) and
+    // capture again.
+    gp_status set_shape(uint32_t W, uint32_t K, uint32_t Wu, uint32_t Ku, uint32_t Wr, uint32_t Kr);
     // Enqueue one batch; `sizing` reads each level's totals back and grows
     // the workspace (never inside a capture).
     gp_status enqueue(uint32_t mode, const std::vector<uint32_t> &runs, cudaStream_t s, bool sizing,

@@ -250,10 +250,73 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
                                                : std::max<uint64_t>(best_vals[k] * 3 / 2 + 1024, 1u << 18);
     }
     const uint64_t cap_ded = std::max<uint64_t>(2 * best_ded, 1u << 20);
+    const uint64_t cap_items = cap_arena / best_C + 2ull * n_trees + 1024;
+
+    // launch shapes: the given ones, or the fastest of a few on generation 0
+    // with the chosen chunk: level 0's warps per SM x window entries (deeper
+    // windows spill less, more warps hide more latency; the sum is bounded
+    // by shared memory), then, when some tree has upper levels, the upper
+    // levels' window (with as many warps as fit, at most 16)
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, E.device);
+    auto upper_warps = [&](uint32_t Ku) {
+        uint32_t w = 16;
+        while (w > 1 && gpk::eval_smem_bytes(E.lanes, (int)w, (int)Ku, true, E.rows) > (size_t)maxsm) --w;
+        return w;
+    };
+    uint32_t shape_k = 0;
+    auto time_shape = [&](uint32_t W, uint32_t K, uint32_t Ku, float *ms) -> gp_status {
+        gp_status e = E.set_shape(W, K, upper_warps(Ku), Ku, E.Wr, E.Kr);
+        if (e) return e;
+        if ((e = E.set_workspace(best_C, cap_codes, cap_vals, cap_ded, cap_items, best_slots, best_pt))) return e;
+        float t = -1.f;
+        for (int rep = 0; rep < 2; ++rep) t = time_eval(G, cs);
+        RunDev R{};
+        if ((e = E.read_run(G->run, &R, cs))) return e;
+        if (t < 0.f || R.err) return R.err ? map_err(R.err, 0) : GP_ECUDA;
+        if (shape_k < 8) {
+            G->info.autotune_shape[shape_k] = (W << 16) | K;
+            G->info.autotune_shape_ms[shape_k] = t;
+            ++shape_k;
+        }
+        *ms = t;
+        return GP_OK;
+    };
+    uint32_t bW = params->warps_per_cta ? params->warps_per_cta : 32;
+    uint32_t bK = params->window_entries ? params->window_entries : 32;
+    uint32_t bKu = params->upper_window_entries ? params->upper_window_entries : 128;
+    if (!params->warps_per_cta && !params->window_entries) {
+        step = "autotune level-0 shape";
+        const uint32_t cand[3][2] = {{32, 32}, {28, 36}, {16, 64}};
+        float best = -1.f;
+        for (auto &c : cand) {
+            if (gpk::eval_smem_bytes(E.lanes, (int)c[0], (int)c[1], false, E.rows) > (size_t)maxsm) continue;
+            float ms = 0.f;
+            if ((st = time_shape(c[0], c[1], bKu, &ms))) return fail(st);
+            if (best < 0.f || ms < best) {
+                best = ms;
+                bW = c[0];
+                bK = c[1];
+            }
+        }
+    }
+    if (!params->upper_window_entries && maxn > best_C) {
+        step = "autotune upper shape";
+        const uint32_t cand[3] = {128, 96, 192};
+        float best = -1.f;
+        for (uint32_t Ku : cand) {
+            float ms = 0.f;
+            if ((st = time_shape(bW, bK, Ku, &ms))) return fail(st);
+            if (best < 0.f || ms < best) {
+                best = ms;
+                bKu = Ku;
+            }
+        }
+    }
+    step = "launch shape";
+    if ((st = E.set_shape(bW, bK, upper_warps(bKu), bKu, E.Wr, E.Kr))) return fail(st);
     step = "final workspace";
-    if ((st = E.set_workspace(best_C, cap_codes, cap_vals, cap_ded, cap_arena / best_C + 2ull * n_trees + 1024,
-                              best_slots, best_pt)))
-        return fail(st);
+    if ((st = E.set_workspace(best_C, cap_codes, cap_vals, cap_ded, cap_items, best_slots, best_pt))) return fail(st);
     step = "generation 0 evaluation";
     if ((st = E.enqueue(kModeEvaluate, {G->run}, cs, false, nullptr))) return fail(st);
     {
@@ -283,6 +346,12 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
     G->info.chunk_nodes = best_C;
     G->info.graph = G->use_graph ? 1u : 0u;
     G->info.kernels_per_generation = G->use_graph ? E.kernels_per_batch[kModeGenerate] : 0;
+    G->info.warps_per_cta = E.W;
+    G->info.window_entries = E.K;
+    G->info.upper_warps = E.Wu;
+    G->info.upper_window_entries = E.Ku;
+    G->info.rope_warps = E.Wr;
+    G->info.rope_window_entries = E.Kr;
     G->info.arena_bytes = cap_arena;
     G->info.workspace_codes = E.w.cap_codes[0] + E.w.cap_codes[1];
     G->info.workspace_values = E.w.cap_values[0] + E.w.cap_values[1];
@@ -444,5 +513,20 @@ gp_status gp_generation_get_info(gp_generation *G, gp_generation_info *info)
 }
 
 void gp_generation_destroy(gp_generation *G) { delete G; }
+
+gp_status gp_select(const float *d_fitness, const uint64_t *d_sizes, uint32_t n_pop, uint64_t seed,
+                    uint32_t generation, uint32_t child_lo, uint32_t n_children, uint32_t tournament_size,
+                    gp_xo *d_out, void *cuda_stream)
+{
+    if (n_children == 0) return GP_OK;
+    if (!d_fitness || !d_sizes || !d_out || n_pop == 0 || tournament_size < 1 || tournament_size > 32)
+        return GP_EINVAL;
+    if ((uint64_t)child_lo + n_children > (1ull << 28) || generation >= (1u << 24)) return GP_EINVAL;
+    const cudaError_t e = gpe::launch_select_range(d_fitness, d_sizes, n_pop, seed, generation, child_lo, n_children,
+                                                   tournament_size, d_out, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return GP_ECUDA;
+    gpk::note_launches(1);
+    return GP_OK;
+}
 
 }  // extern "C"

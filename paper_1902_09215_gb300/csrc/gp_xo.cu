@@ -139,36 +139,41 @@ __device__ __forceinline__ uint64_t xo_src(const XoChild &c, uint64_t p) {
     return c.tail_src + (p - c.i - c.ld);
 }
 
-// Four source bytes starting at byte address a (any alignment), from two
+// Sixteen source bytes starting at byte address a (any alignment), from five
 // aligned words.  Sources are padded by at least 8 bytes on both ends.
-__device__ __forceinline__ uint32_t load4_unaligned(const uint8_t *src, uint64_t a) {
-    const uint64_t al = a & ~3ull;
-    const uint32_t w0 = __ldg(reinterpret_cast<const uint32_t *>(src + al));
-    const uint32_t w1 = __ldg(reinterpret_cast<const uint32_t *>(src + al + 4));
-    const uint32_t sh = (uint32_t)(a & 3);
-    return __byte_perm(w0, w1, 0x3210u + 0x1111u * sh);
+__device__ __forceinline__ uint4 load16_unaligned(const uint8_t *src, uint64_t a) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(src + (a & ~3ull));
+    const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3), w4 = __ldg(w + 4);
+    const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(a & 3);
+    return make_uint4(__byte_perm(w0, w1, sel), __byte_perm(w1, w2, sel), __byte_perm(w2, w3, sel),
+                      __byte_perm(w3, w4, sel));
 }
 
-// One CTA per tile of one child; every thread writes aligned 32-bit words.
+// One CTA per tile of one child; every thread writes aligned 16-byte words
+// (children start 16-byte aligned, tiles are multiples of 16 bytes; the
+// bytes from the child's end to the next 16-byte boundary are its padding
+// and are written as zeros).  A word inside one of the child's three
+// segments is assembled from aligned loads; the few words across a segment
+// boundary or the child's end go byte by byte.
 __device__ __forceinline__ void copy_tile(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
                                           const XoChild &c, uint64_t tbegin, uint32_t tile_bytes)
 {
-    const uint64_t tend = umin64(tbegin + tile_bytes, (c.n + 3) & ~3ull);
-    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + c.dst);
+    const uint64_t tend = umin64(tbegin + tile_bytes, (c.n + 15) & ~15ull);
+    uint4 *d16 = reinterpret_cast<uint4 *>(dst + c.dst);
     const uint64_t b1 = c.i, b2 = c.i + c.ld;
-    for (uint64_t p = tbegin + 4ull * threadIdx.x; p < tend; p += 4ull * blockDim.x) {
-        uint32_t word;
-        const uint64_t q = p + 3;
+    for (uint64_t p = tbegin + 16ull * threadIdx.x; p < tend; p += 16ull * blockDim.x) {
+        uint4 v;
+        const uint64_t q = p + 15;
         const bool one_seg = (q < c.n) && ((q < b1) || (p >= b1 && q < b2) || (p >= b2));
         if (one_seg) {
-            word = load4_unaligned(src, xo_src(c, p));
+            v = load16_unaligned(src, xo_src(c, p));
         } else {
-            word = 0;
-            for (int k = 0; k < 4; ++k) {
-                if (p + k < c.n) word |= (uint32_t)src[xo_src(c, p + k)] << (8 * k);
-            }
+            uint32_t w[4] = {0, 0, 0, 0};
+            for (int k = 0; k < 16; ++k)
+                if (p + k < c.n) w[k >> 2] |= (uint32_t)src[xo_src(c, p + k)] << (8 * (k & 3));
+            v = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        d32[p >> 2] = word;
+        d16[p >> 4] = v;
     }
 }
 

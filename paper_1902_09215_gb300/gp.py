@@ -23,7 +23,7 @@ EXPORTED = [
     "gp_create_population", "gp_crossover", "gp_evaluate", "gp_evaluate_ex", "gp_fitness",
     "gp_tree_size", "gp_tree_read", "gp_population_get_info", "gp_destroy_population",
     "gp_status_string", "gp_eval_stats_get", "gp_kernel_launch_count", "gp_profile_enable",
-    "gp_profile_read", "gp_evaluate_noalloc",
+    "gp_profile_read", "gp_evaluate_noalloc", "gp_select",
     "gp_generation_create", "gp_generation_step", "gp_generation_rewind", "gp_generation_fitness",
     "gp_generation_records", "gp_generation_trees", "gp_generation_tree_read", "gp_generation_get_info",
     "gp_generation_destroy",
@@ -66,7 +66,9 @@ class gp_eval_stats(C.Structure):
 class gp_generation_params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("tournament_size", C.c_uint32), ("chunk_nodes", C.c_uint32),
                 ("arena_bytes", C.c_uint64), ("workspace_codes", C.c_uint64),
-                ("workspace_values", C.c_uint64), ("use_graph", C.c_uint32), ("max_levels", C.c_uint32)]
+                ("workspace_values", C.c_uint64), ("use_graph", C.c_uint32), ("max_levels", C.c_uint32),
+                ("warps_per_cta", C.c_uint32), ("window_entries", C.c_uint32),
+                ("upper_window_entries", C.c_uint32), ("pad", C.c_uint32)]
 
 
 class gp_generation_info(C.Structure):
@@ -75,7 +77,10 @@ class gp_generation_info(C.Structure):
                 ("kernels_per_generation", C.c_uint32), ("error_generation", C.c_uint32),
                 ("arena_bytes", C.c_uint64), ("workspace_codes", C.c_uint64),
                 ("workspace_values", C.c_uint64), ("autotune_chunk", C.c_uint32 * 8),
-                ("autotune_ms", C.c_float * 8)]
+                ("autotune_ms", C.c_float * 8), ("warps_per_cta", C.c_uint32), ("window_entries", C.c_uint32),
+                ("upper_warps", C.c_uint32), ("upper_window_entries", C.c_uint32),
+                ("rope_warps", C.c_uint32), ("rope_window_entries", C.c_uint32),
+                ("autotune_shape", C.c_uint32 * 8), ("autotune_shape_ms", C.c_float * 8)]
 
 
 class gp_server_params(C.Structure):
@@ -143,6 +148,8 @@ def lib():
             L.gp_profile_enable.argtypes = [C.c_int]
             L.gp_profile_read.argtypes = [P(gp_kernel_profile), C.c_int]
             L.gp_evaluate_noalloc.argtypes = [P(gp_problem), C.c_uint32, vp, P(C.c_uint64), vp, vp, vp, vp]
+            L.gp_select.argtypes = [vp, vp, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                    vp, vp]
             L.gp_generation_create.argtypes = [P(gp_problem), P(gp_generation_params), C.c_uint32,
                                                P(C.c_uint8), P(C.c_uint64), vp, P(vp)]
             L.gp_generation_step.argtypes = [vp, C.c_uint32, vp]
@@ -235,14 +242,19 @@ class Population:
 
 
 def gp_create_population(problem: Problem, nodes, offsets, stream=None) -> Population:
-    nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+    """nodes: a host array, or the device address (int) of packed trees on
+    this device; offsets: host array of n_trees + 1 entries."""
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
     n = offsets.shape[0] - 1
     if n < 0:
         raise ValueError("offsets needs n_trees + 1 entries")
-    nb = nodes if nodes.size else np.zeros(1, np.uint8)
+    if isinstance(nodes, int):
+        nb = C.cast(C.c_void_p(nodes), C.POINTER(C.c_uint8))
+    else:
+        nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+        nb = _ptr(nodes if nodes.size else np.zeros(1, np.uint8), C.c_uint8)
     out = C.c_void_p()
-    st = lib().gp_create_population(C.byref(problem.struct), n, _ptr(nb, C.c_uint8),
+    st = lib().gp_create_population(C.byref(problem.struct), n, nb,
                                     _ptr(offsets, C.c_uint64), _stream(stream), C.byref(out))
     _check(st, "gp_create_population")
     return Population(out, n, problem.n_cases)
@@ -373,6 +385,19 @@ def gp_evaluate_noalloc(problem: Problem, offsets, d_nodes: int, d_fitness: int,
     _check(st, "gp_evaluate_noalloc")
 
 
+def gp_select(d_fitness: int, d_sizes: int, n_pop: int, seed, generation: int, child_lo: int, n_children: int,
+              d_out: int, tournament_size=7, stream=None):
+    """Selection records of children [child_lo, child_lo + n_children) from a
+    whole population's fitness and sizes (device addresses, e.g. torch
+    tensors' data_ptr()); writes n_children gp_xo records at d_out."""
+    _check(lib().gp_select(C.c_void_p(int(d_fitness)), C.c_void_p(int(d_sizes)), int(n_pop),
+                           int(seed) & ((1 << 64) - 1), int(generation), int(child_lo), int(n_children),
+                           int(tournament_size), C.c_void_p(int(d_out)), _stream(stream)), "gp_select")
+
+
+XO_RECORD_BYTES = C.sizeof(gp_xo)
+
+
 class Generation:
     """Owns one gp_generation handle (a device-resident evolving population)."""
 
@@ -389,13 +414,15 @@ class Generation:
 
 def gp_generation_create(problem: Problem, nodes, offsets, seed, tournament_size=7, chunk_nodes=0,
                          arena_bytes=0, workspace_codes=0, workspace_values=0, use_graph=True,
-                         max_levels=0, stream=None) -> Generation:
+                         max_levels=0, stream=None, warps_per_cta=0, window_entries=0,
+                         upper_window_entries=0) -> Generation:
     nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
     n = offsets.shape[0] - 1
     prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), int(chunk_nodes),
                                int(arena_bytes), int(workspace_codes), int(workspace_values),
-                               1 if use_graph else 0, int(max_levels))
+                               1 if use_graph else 0, int(max_levels), int(warps_per_cta), int(window_entries),
+                               int(upper_window_entries), 0)
     h = C.c_void_p()
     st = lib().gp_generation_create(C.byref(problem.struct), C.byref(prm), n, _ptr(nodes, C.c_uint8),
                                     _ptr(offsets, C.c_uint64), _stream(stream), C.byref(h))
@@ -463,6 +490,8 @@ def gp_generation_get_info(g: Generation) -> dict:
     d = {k: getattr(i, k) for k, _ in gp_generation_info._fields_}
     d["autotune_chunk"] = list(i.autotune_chunk)
     d["autotune_ms"] = list(i.autotune_ms)
+    d["autotune_shape"] = [(v >> 16, v & 0xFFFF) for v in i.autotune_shape]
+    d["autotune_shape_ms"] = list(i.autotune_shape_ms)
     return d
 
 
@@ -505,7 +534,8 @@ def gp_server_open_run(srv: Server, nodes, offsets, seed, tournament_size=7, are
     nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
     n = offsets.shape[0] - 1
-    prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), 0, int(arena_bytes), 0, 0, 0, 0)
+    prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), 0, int(arena_bytes), 0, 0, 0, 0,
+                               0, 0, 0, 0)
     rid = C.c_uint64()
     _check(lib().gp_server_open_run(srv._h, C.byref(prm), n, _ptr(nodes, C.c_uint8), _ptr(offsets, C.c_uint64),
                                     C.byref(rid)), "gp_server_open_run")
@@ -517,7 +547,8 @@ def gp_server_open_run_from(srv: Server, pop: Population, trees, seed, tournamen
     """A run whose initial trees are `trees` (indices into `pop`, which must
     stay alive until the run is admitted or closed)."""
     trees = np.ascontiguousarray(trees, dtype=np.uint32)
-    prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), 0, int(arena_bytes), 0, 0, 0, 0)
+    prm = gp_generation_params(int(seed) & ((1 << 64) - 1), int(tournament_size), 0, int(arena_bytes), 0, 0, 0, 0,
+                               0, 0, 0, 0)
     rid = C.c_uint64()
     _check(lib().gp_server_open_run_from(srv._h, C.byref(prm), pop._h, trees.shape[0], _ptr(trees, C.c_uint32),
                                          C.byref(rid)), "gp_server_open_run_from")

@@ -324,3 +324,87 @@ def test_degenerate_populations(gpu, oracle, trees):
         assert_same_eval(gpu, G, ref_next)
         nodes, offs, ref = kids, koffs, ref_next
     gpu.gp_generation_destroy(G)
+
+
+def test_launch_shapes_are_exact_and_reported(gpu, oracle):
+    """Every launch shape the creation may choose (level 0's warps per SM x
+    window entries, the upper levels' window) gives the oracle's
+    generations exactly; get_info reports the shape in use and the
+    autotuner's candidates and times."""
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=19, count=250, lo=31, hi=70001)
+    seed = 33
+    ref = oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)
+    want = []
+    n, o, r = nodes, offs, ref
+    for g in range(2):
+        _, n, o, r = oracle_step(oracle, n, o, r["fitness"], seed, g, (x, y, c))
+        want.append((n, o, r))
+    shapes = [(32, 32, 128), (28, 36, 96), (16, 64, 192), (0, 0, 0)]     # the last one autotuned
+    for W, K, Ku in shapes:
+        G = gpu.gp_generation_create(prob, nodes, offs, seed=seed, chunk_nodes=4096, warps_per_cta=W,
+                                     window_entries=K, upper_window_entries=Ku)
+        info = gpu.gp_generation_get_info(G)
+        if W:
+            assert (info["warps_per_cta"], info["window_entries"], info["upper_window_entries"]) == (W, K, Ku)
+        else:
+            tried = [s for s in info["autotune_shape"] if s != (0, 0)]
+            assert len(tried) >= 4 and (info["warps_per_cta"], info["window_entries"]) in tried
+            assert info["upper_window_entries"] in (96, 128, 192)
+            assert all(t > 0 for t in info["autotune_shape_ms"][:len(tried)])
+        for g in range(2):
+            gpu.gp_generation_step(G)
+            gn, go = gpu.gp_generation_trees(G)
+            assert np.array_equal(go, want[g][1]) and np.array_equal(gn, want[g][0]), (W, K, Ku, g)
+            assert_same_eval(gpu, G, want[g][2])
+        gpu.gp_generation_destroy(G)
+    with pytest.raises(gpu.GpError) as e:                 # does not fit shared memory
+        gpu.gp_generation_create(prob, nodes, offs, seed=seed, warps_per_cta=32, window_entries=64)
+    assert e.value.status == gpu.GP_EINVAL
+
+
+def test_select_range_matches_the_oracle_draws(gpu, oracle):
+    """gp_select, for any range of children, gives the records the oracle's
+    generation draws (size-7 tournaments with NaN worst, uniform points)."""
+    import torch
+    x, y, c = synth.problem()
+    nodes, offs = synth.population_loguniform(seed=29, count=500, lo=31, hi=4001)
+    fit = np.asarray(oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)["fitness"], np.float32)
+    fit[::37] = np.nan                                    # unfit trees rank worst
+    sizes = np.diff(offs.astype(np.int64)).astype(np.uint64)
+    seed, g = 77, 3
+    want = oracle.generation_records(fit, sizes, 500, seed=seed, g=g)
+    d_fit = torch.from_numpy(fit).cuda()
+    d_sz = torch.from_numpy(sizes.view(np.int64)).cuda()
+    for lo, n in ((0, 500), (123, 77), (499, 1)):
+        out = torch.zeros(n * gpu.XO_RECORD_BYTES, dtype=torch.uint8, device="cuda")
+        gpu.gp_select(d_fit.data_ptr(), d_sz.data_ptr(), 500, seed, g, lo, n, out.data_ptr())
+        torch.cuda.synchronize()
+        got = np.frombuffer(out.cpu().numpy().tobytes(), dtype=gpu._XO_DTYPE)
+        for name, w in zip(("mum", "dad", "mum_point", "dad_point"), want):
+            assert np.array_equal(got[name].astype(np.uint64), np.asarray(w)[lo:lo + n].astype(np.uint64)), (lo, name)
+
+
+def test_population_from_device_bytes(gpu, oracle):
+    """gp_create_population takes packed trees already in device memory (e.g.
+    received from another process) and validates them as host ones."""
+    import torch
+    x, y, c = synth.problem()
+    prob = gpu.Problem(x, y, c)
+    nodes, offs = synth.population_loguniform(seed=31, count=200, lo=31, hi=9001)
+    d = torch.zeros(nodes.shape[0] + 64, dtype=torch.uint8, device="cuda")
+    d[:nodes.shape[0]] = torch.from_numpy(nodes).cuda()
+    torch.cuda.synchronize()
+    pop = gpu.gp_create_population(prob, d.data_ptr(), offs)
+    gpu.gp_evaluate(pop)
+    fit, _, _ = gpu.gp_fitness(pop)
+    assert same_f32(fit, oracle.eval_population(nodes, offs, x, y, c, n_threads=THREADS)["fitness"])
+    kn, ko = gpu.read_all_trees(pop)
+    assert np.array_equal(kn, nodes) and np.array_equal(ko, offs)
+    bad = d.clone()
+    bad[0] = 200                                          # an undefined code
+    torch.cuda.synchronize()
+    with pytest.raises(gpu.GpError) as e:
+        gpu.gp_create_population(prob, bad.data_ptr(), offs)
+    assert e.value.status == gpu.GP_EMALFORMED
