@@ -435,7 +435,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def generations_compare(gp, prob, nodes, offs, stream, flush, K, reps, chunk=0, arena=0):
+def generations_compare(gp, prob, nodes, offs, stream, flush, K, reps, chunk=0, arena=0, shape=None):
     """K consecutive generations from the same parents, made two ways, with
     identical results (checked): on the device (one gp_generation_step of K
     generations: tournaments, crossover and evaluation replayed from the
@@ -451,9 +451,14 @@ def generations_compare(gp, prob, nodes, offs, stream, flush, K, reps, chunk=0, 
     kw = dict(seed=SEED_GEN, use_graph=True, stream=stream)
     if arena:
         kw["arena_bytes"] = arena
+    if shape:
+        kw.update(warps_per_cta=shape[0], window_entries=shape[1], upper_window_entries=shape[2])
     G = gp.gp_generation_create(prob, nodes, offs, chunk_nodes=chunk, **kw)
     info0 = gp.gp_generation_get_info(G)
     chunk = int(info0["chunk_nodes"])
+    # later creations take the chosen chunk and launch shapes (no autotuning)
+    kw.update(warps_per_cta=info0["warps_per_cta"], window_entries=info0["window_entries"],
+              upper_window_entries=info0["upper_window_entries"])
     # the records of each generation (untimed pass, one generation at a time)
     recs = []
     for _ in range(K):
@@ -747,7 +752,8 @@ def config4_batched(gp, prob, stream, flush, cpu, steps=3):
     gp.gp_generation_destroy(G)
     del G
     torch.cuda.synchronize()
-    cmp = generations_compare(gp, prob, nodes, offs, stream, flush, 2, 1, chunk=chunk, arena=arena)
+    cmp = generations_compare(gp, prob, nodes, offs, stream, flush, 2, 1, chunk=chunk, arena=arena,
+                              shape=(info0["warps_per_cta"], info0["window_entries"], info0["upper_window_entries"]))
     child_nodes = int(info1["total_nodes"])
     # end to end from page-locked host memory (the parents' own pages registered)
     try:
@@ -758,7 +764,9 @@ def config4_batched(gp, prob, stream, flush, cpu, steps=3):
     torch.cuda.synchronize()
     t = time.perf_counter()
     G = gp.gp_generation_create(prob, nodes, offs, seed=SEED_GEN, chunk_nodes=chunk, arena_bytes=arena,
-                                use_graph=True, stream=stream)
+                                use_graph=True, stream=stream, warps_per_cta=info0["warps_per_cta"],
+                                window_entries=info0["window_entries"],
+                                upper_window_entries=info0["upper_window_entries"])
     gp.gp_generation_step(G, 1, stream)
     gp.gp_generation_fitness(G)
     e2e_s = time.perf_counter() - t
@@ -769,6 +777,9 @@ def config4_batched(gp, prob, stream, flush, cpu, steps=3):
     units = child_nodes * prob.n_cases
     out = {"workload": desc, "parent_nodes": int(offs[-1]), "child_nodes": child_nodes,
            "population_build_s": build_s, "create_s": create_s, "chunk_nodes": chunk,
+           "autotune": {"chunk": {str(k): v for k, v in zip(info0["autotune_chunk"], info0["autotune_ms"]) if k},
+                        "shape": {f"{w}x{k}": v for (w, k), v in zip(info0["autotune_shape"],
+                                                                      info0["autotune_shape_ms"]) if w}},
            "levels": int(info1["levels"]),
            "batched_vs_plain": cmp,
            "e2e": {"value": units / e2e_s, "unit": "GPops/s", "wall_s": e2e_s,

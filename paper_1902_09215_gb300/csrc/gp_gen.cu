@@ -282,21 +282,29 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
         *ms = t;
         return GP_OK;
     };
-    uint32_t bW = params->warps_per_cta ? params->warps_per_cta : 32;
-    uint32_t bK = params->window_entries ? params->window_entries : 32;
+    // (the engine's starting shape already fits this problem's leaf table)
+    uint32_t bW = params->warps_per_cta ? params->warps_per_cta : E.W;
+    uint32_t bK = params->window_entries ? params->window_entries : E.K;
     uint32_t bKu = params->upper_window_entries ? params->upper_window_entries : 128;
     if (!params->warps_per_cta && !params->window_entries) {
         step = "autotune level-0 shape";
         const uint32_t cand[3][2] = {{32, 32}, {28, 36}, {16, 64}};
         float best = -1.f;
-        for (auto &c : cand) {
-            if (gpk::eval_smem_bytes(E.lanes, (int)c[0], (int)c[1], false, E.rows) > (size_t)maxsm) continue;
+        uint32_t done[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i) {
+            uint32_t W = cand[i][0];
+            const uint32_t K = cand[i][1];
+            // fewer warps when a large leaf table leaves less shared memory
+            while (W > 1 && gpk::eval_smem_bytes(E.lanes, (int)W, (int)K, false, E.rows) > (size_t)maxsm) --W;
+            if (gpk::eval_smem_bytes(E.lanes, (int)W, (int)K, false, E.rows) > (size_t)maxsm) continue;
+            if (done[0] == ((W << 16) | K) || done[1] == ((W << 16) | K)) continue;
+            done[i] = (W << 16) | K;
             float ms = 0.f;
-            if ((st = time_shape(c[0], c[1], bKu, &ms))) return fail(st);
+            if ((st = time_shape(W, K, bKu, &ms))) return fail(st);
             if (best < 0.f || ms < best) {
                 best = ms;
-                bW = c[0];
-                bK = c[1];
+                bW = W;
+                bK = K;
             }
         }
     }
