@@ -133,12 +133,14 @@ class ClockSampler:
 
 
 def kernel_source_sha():
-    """Hash of what the evaluator kernels compile from: gp_eval.cu and the
-    types and constants of gp_internal.cuh (launcher declarations after them
-    do not change the kernels)."""
+    """Hash of what the level-0 launch of the step depends on: gp_eval.cu,
+    gp_plan0.cu (which chunks the launch gets) and the types, constants and
+    device helpers of gp_internal.cuh (launcher declarations after them do
+    not change the kernels)."""
     csrc = os.path.join(ROOT, "paper_1902_09215_gb300", "csrc")
     h = hashlib.sha256()
     h.update(open(os.path.join(csrc, "gp_eval.cu"), "rb").read())
+    h.update(open(os.path.join(csrc, "gp_plan0.cu"), "rb").read())
     hdr = open(os.path.join(csrc, "gp_internal.cuh"), "rb").read()
     cut = hdr.find(b"// Launchers")
     h.update(hdr if cut < 0 else hdr[:cut])

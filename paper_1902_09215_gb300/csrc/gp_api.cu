@@ -995,7 +995,12 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
             ++max_ropes;
         }
     }
-    if (max_items > 0x7fffffffull) return GP_ENOMEM;
+    // cut at low points of the arity walk, a multi-chunk tree may take one
+    // chunk more than ceil(size / C): room for one more item and slot each
+    const uint64_t max_cuts = max_slots;
+    max_items += max_ropes;
+    max_slots += max_ropes;
+    if (max_items > 0x7fffffffull || max_cuts >= (1ull << 27)) return GP_ENOMEM;
     const uint32_t pt_cap = fuse_pt_cap(C);
     const uint64_t warps_total = (uint64_t)sms * cfg.W, spill_per_warp = C;
     DevBufs ws;
@@ -1010,6 +1015,8 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
         };
         const uint64_t o_cls = take(4ull * plan_level0_scratch_words());
         const uint64_t o_cnt = take(256 + 16 + 4ull * P->n_trees);
+        const uint64_t o_meta = take(4ull * P->n_trees);
+        const uint64_t o_cuts = take(4ull * max_cuts + 4);
         const uint64_t o_len = take(4ull * max_slots);
         const uint64_t o_codes = take(4ull * (max_slots * C + 32));
         const uint64_t o_pt = take(8ull * (max_slots * pt_cap * lanes + 1));
@@ -1023,8 +1030,10 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
         uint32_t *d_counts = d_counter + 64;
         EvalItem *items = reinterpret_cast<EvalItem *>(blk + o_items);
         EvalItem *ropes = reinterpret_cast<EvalItem *>(blk + o_ropes);
-        CK(launch_plan_level0(P->d_start, P->d_size, P->n_trees, C, items, ropes, d_counts,
-                              reinterpret_cast<uint32_t *>(blk + o_cls), sms, s));
+        CK(launch_plan_level0(P->d_arena, P->d_start, P->d_size, P->n_trees, C, kFuseMaxChunks, items, ropes,
+                              d_counts, reinterpret_cast<uint32_t *>(blk + o_cls),
+                              reinterpret_cast<uint32_t *>(blk + o_meta), reinterpret_cast<uint32_t *>(blk + o_cuts),
+                              sms, s));
         note_launches(3);
         EvalParams p{};
         p.codes = P->d_arena;

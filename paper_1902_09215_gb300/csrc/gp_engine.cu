@@ -356,6 +356,34 @@ __device__ __forceinline__ uint32_t size_bucket(uint64_t len)
     return min(b, kBuckets - 1);
 }
 
+// Level 0, before its items: every tree of 2..kFuseMaxChunks chunks is cut
+// where its arity walk is low (cut_low; one chunk more than ceil(size / C)
+// at most, never more than kFuseMaxChunks), a warp per tree.  t_nch[i]: the
+// tree's chunk count (0 for the other trees); t_cut[i * (kFuseMaxChunks - 1)
+// + j]: the end of its chunk j, relative to the tree's start.
+__global__ void cut_fused_kernel(const BatchCtl *ctl, uint32_t C, const uint8_t *__restrict__ heap,
+                                 const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
+                                 uint32_t *__restrict__ t_nch, uint32_t *__restrict__ t_cut)
+{
+    if (ctl->err != 0) return;
+    const uint32_t n = ctl->head.n_trees;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = warp; i < n; i += warps) {
+        const uint64_t z = bsize[i];
+        uint32_t k = 0;
+        if (z > C && z <= (uint64_t)kFuseMaxChunks * C) {
+            const uint64_t b = bstart[i];
+            const uint32_t m = (uint32_t)((z + C - 1) / C);
+            uint32_t *cut = t_cut + (uint64_t)i * (kFuseMaxChunks - 1);
+            k = cut_low(heap, b, z, C, min(m + 1, kFuseMaxChunks), lane, [&](uint32_t j, uint64_t e) {
+                if (lane == 0) cut[j - 1] = (uint32_t)(e - b);
+            });
+        }
+        if (lane == 0) t_nch[i] = k;
+    }
+}
+
 // One CTA.  Level 0: every tree of the batch (size 0: none); a tree of at
 // most C nodes is one final item; a tree of 2..kFuseMaxChunks chunks (when
 // the workspace has fused slots) becomes fused chunks, each writing its
@@ -365,7 +393,8 @@ __device__ __forceinline__ uint32_t size_bucket(uint64_t len)
 // level k-1 now has an upper tree of codes [frag_off[first chunk],
 // frag_off[one past its last chunk]); it becomes a final item when it fits
 // one chunk, did not at least halve, or this is the last level (a final
-// above C gets a dedicated spill area); otherwise it is cut again.
+// above C gets a dedicated spill area); otherwise it is cut again.  A fused
+// tree's chunks are the ones cut_fused_kernel chose (t_nch, t_cut).
 // Items: planned chunks first in tree order (their fragments must be
 // contiguous per tree), then fused chunks, then finals (ropes included)
 // from the largest size bucket down.
@@ -375,7 +404,8 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     BatchCtl *ctl, LevelArgs A, const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
     const uint64_t *__restrict__ frag_off, uint64_t *__restrict__ t_lo, uint64_t *__restrict__ t_hi,
     uint64_t *__restrict__ t_prev, uint32_t *__restrict__ t_first, uint32_t *__restrict__ t_state,
-    EvalItem *__restrict__ items, EvalItem *__restrict__ rope_items)
+    const uint32_t *__restrict__ t_nch, const uint32_t *__restrict__ t_cut, EvalItem *__restrict__ items,
+    EvalItem *__restrict__ rope_items)
 {
     __shared__ uint64_t sa[kScanT], sb[kScanT];
     __shared__ uint32_t s_cnt[kBuckets], s_fill[kBuckets];
@@ -426,7 +456,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     if (fuse_hi) {
         for (uint32_t i = lo; i < hi; ++i) {
             const uint64_t len = t_hi[i] - t_lo[i];
-            if (t_state[i] == 1 && len > C && len <= fuse_hi) ncand += (len + C - 1) / C;
+            if (t_state[i] == 1 && len > C && len <= fuse_hi) ncand += t_nch[i];
         }
     }
     block_scan2(sa, sb, ncand, 0);
@@ -437,7 +467,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         for (uint32_t i = lo; i < hi; ++i) {
             const uint64_t len = t_hi[i] - t_lo[i];
             if (t_state[i] != 1 || len <= C || len > fuse_hi) continue;
-            const uint64_t m = (len + C - 1) / C;
+            const uint64_t m = t_nch[i];
             if (run_c + m <= A.cap_slots) t_state[i] = 3;
             run_c += m;
         }
@@ -453,7 +483,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         }
         const uint64_t len = t_hi[i] - t_lo[i];
         if (t_state[i] == 3) {
-            nfz += (len + C - 1) / C;
+            nfz += t_nch[i];
             atomicAdd(&s_rcnt[size_bucket(len)], 1u);
         } else if (last || len <= C || 2 * len > t_prev[i]) {
             atomicAdd(&s_cnt[size_bucket(len)], 1u);
@@ -536,11 +566,12 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             items[s_base[b] + atomicAdd(&s_fill[b], 1u)] = it;
             t_state[i] = 0;
         } else if (t_state[i] == 3) {
-            const uint32_t m = (uint32_t)((len + C - 1) / C);
+            const uint32_t m = t_nch[i];
+            const uint32_t *cut = t_cut + (uint64_t)i * (kFuseMaxChunks - 1);
             for (uint32_t j = 0; j < m; ++j) {
                 EvalItem it{};
-                it.begin = t_lo[i] + (uint64_t)j * C;
-                it.end = umin64(t_hi[i], it.begin + C);
+                it.begin = t_lo[i] + (j ? cut[j - 1] : 0u);
+                it.end = j + 1 < m ? t_lo[i] + cut[j] : t_hi[i];
                 it.tree = i;
                 it.flags = gpk::kItemFused;
                 it.frag_off = ex_fz + j;
@@ -852,6 +883,8 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     if ((st = galloc(v, (void **)&t_prev_, sizeof(uint64_t) * T))) return st;
     if ((st = galloc(v, (void **)&t_first_, sizeof(uint32_t) * (T + 1)))) return st;
     if ((st = galloc(v, (void **)&t_state_, sizeof(uint32_t) * T))) return st;
+    if ((st = galloc(v, (void **)&t_nch_, sizeof(uint32_t) * T))) return st;
+    if ((st = galloc(v, (void **)&t_cut_, sizeof(uint32_t) * T * (kFuseMaxChunks - 1)))) return st;
     if ((st = galloc(v, (void **)&rope_items_, sizeof(EvalItem) * T))) return st;
     if ((st = galloc(v, (void **)&x_, sizeof(float) * 2 * lanes))) return st;
     if ((st = galloc(v, (void **)&y_, sizeof(float) * 2 * lanes))) return st;
@@ -1258,8 +1291,13 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
     LevelArgs A{dyn ? kDynLevel : level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu),
                 dyn ? levels_cap_graph : (level + 1 == levels_max ? 1u : 0u), w.spill_base, w.cap_dedicated,
                 w.cap_slots};
+    if (level == 0 && !dyn) {
+        cut_fused_kernel<<<sms * 8, 256, 0, s>>>(ctl, w.C, heap, bstart_, bsize_, t_nch_, t_cut_);
+        GK(cudaGetLastError());
+        ++nl;
+    }
     items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
-                                      t_state_, w.items, rope_items_);
+                                      t_state_, t_nch_, t_cut_, w.items, rope_items_);
     GK(cudaGetLastError());
     if (sizing) {
         // a dedicated spill pool too small for this level's oversized
@@ -1278,7 +1316,7 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
             GK(cudaMemsetAsync(w.fz_over, 0, sizeof(uint32_t) * max_trees, s));
             GK(cudaMemsetAsync(w.fz_redo, 0, sizeof(uint32_t), s));
             items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
-                                              t_first_, t_state_, w.items, rope_items_);
+                                              t_first_, t_state_, t_nch_, t_cut_, w.items, rope_items_);
             GK(cudaGetLastError());
             GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             GK(cudaStreamSynchronize(s));
@@ -1296,7 +1334,7 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
             GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
             GK(cudaMemcpyAsync(&ctl->n_chunks, &prev_chunks, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
             items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
-                                              t_first_, t_state_, w.items, rope_items_);
+                                              t_first_, t_state_, t_nch_, t_cut_, w.items, rope_items_);
             GK(cudaGetLastError());
             GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             GK(cudaStreamSynchronize(s));

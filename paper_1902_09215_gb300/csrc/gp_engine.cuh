@@ -233,7 +233,7 @@ class Engine {
     float *bfit_ = nullptr, *bvals_ = nullptr;
     uint32_t *bhits_ = nullptr;
     uint64_t *t_lo_ = nullptr, *t_hi_ = nullptr, *t_prev_ = nullptr;
-    uint32_t *t_first_ = nullptr, *t_state_ = nullptr;
+    uint32_t *t_first_ = nullptr, *t_state_ = nullptr, *t_nch_ = nullptr, *t_cut_ = nullptr;
     float *x_ = nullptr, *y_ = nullptr, *c_ = nullptr;
     // the last head written (a batch whose head is unchanged skips the copies)
     uint32_t last_mode_ = ~0u;

@@ -21,6 +21,63 @@ constexpr uint32_t kErrPlan = 4u;       // fragment emitted a different shape th
 constexpr uint32_t kErrExtent = 8u;     // subtree extent walked off the end of a tree
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+constexpr uint32_t kLowWindow = 512;       // codes searched before a chunk's longest end (16 per lane)
+
+// Ends of the chunks of one tree (codes [s, s + n), n > C), chosen by the
+// calling warp (all 32 lanes).  P(e) = 1 + (operators - leaves among the
+// first e - s codes) is the number of subtrees that start at or after e and
+// are arguments of operators before it (Sec. 2.1's prefix order, arity 2 or
+// 0).  A chunk that ends where P is low has fewer operators whose arguments
+// reach past its end, so it sends fewer operators and values up to its
+// tree's rope.  Each next end is the 16-aligned position among the last
+// kLowWindow codes before the longest chunk allowed (C codes) where P is
+// lowest, the rightmost of equals, among the ends that leave the rest of
+// the tree within the chunks still allowed (mcap in all); without such a
+// position it is the longest chunk's end.  `arena` is 16-byte aligned.
+// f(j, e) receives end j (1-based, absolute); returns the number of chunks.
+template <typename F>
+__device__ __forceinline__ uint32_t cut_low(const uint8_t *__restrict__ arena, uint64_t s, uint64_t n, uint32_t C,
+                                            uint32_t mcap, int lane, F f)
+{
+    uint64_t a = s;
+    uint32_t j = 1;
+    while (s + n - a > C) {
+        const uint64_t left = (uint64_t)(mcap - j) * C;          // codes the later chunks can hold
+        uint64_t lo = a + 1;
+        if (C > kLowWindow) lo = umax64(lo, a + C - kLowWindow);
+        if (n > left) lo = umax64(lo, s + n - left);
+        lo = (lo + 15) & ~15ull;
+        const uint64_t hi = (a + C) & ~15ull;
+        uint64_t e = a + C;
+        if (lo <= hi) {
+            const uint32_t groups = (uint32_t)((hi - lo) >> 4);  // at most kLowWindow / 16 = 32
+            int d = 0;
+            if ((uint32_t)lane < groups) {
+                const uint4 w = __ldg(reinterpret_cast<const uint4 *>(arena + lo) + lane);
+                const uint32_t op_bits = __popc(__vcmpltu4(w.x, 0x04040404u)) + __popc(__vcmpltu4(w.y, 0x04040404u)) +
+                                         __popc(__vcmpltu4(w.z, 0x04040404u)) + __popc(__vcmpltu4(w.w, 0x04040404u));
+                d = 2 * (int)(op_bits >> 3) - 16;                 // P(lo + 16 (lane + 1)) - P(lo + 16 lane)
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, d, o);
+                if (lane >= o) d += v;
+            }
+            // lowest P first, then the largest candidate index k (e = lo + 16 k)
+            uint32_t key = (uint32_t)lane < groups ? ((uint32_t)(d + 1024) << 8) | (255u - (uint32_t)(lane + 1))
+                                                   : 0xffffffffu;
+            if (lane == 0) key = min(key, (1024u << 8) | 255u);  // k = 0: P(lo) - P(lo) = 0
+            key = __reduce_min_sync(0xffffffffu, key);
+            e = lo + 16ull * (255u - (key & 255u));
+        }
+        f(j, e);
+        a = e;
+        ++j;
+    }
+    return j;
+}
 
 // One unit of evaluator work: a contiguous range of a level's code array.
 // A final item covers a whole tree (level 0) or a whole upper tree and
@@ -134,13 +191,17 @@ cudaError_t launch_plan_dev(bool wide, const void *codes, const EvalItem *items,
 cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uint32_t *n_dev,
                                  uint64_t *frag_off, uint64_t *totals, cudaStream_t s);
 // Level-0 items of trees whose sizes are on the device, all at most
-// kFuseMaxChunks chunks: counts[0] items (fused chunks, then finals),
-// counts[1] ropes (next launch), counts[2] slots.  Three launches; `cls`:
-// plan_level0_scratch_words() zeroed words.
+// max_chunks chunks of C codes: counts[0] items (fused chunks, then
+// finals), counts[1] ropes (next launch), counts[2] slots.  A multi-chunk
+// tree of m = ceil(n / C) chunks is cut where its arity walk is low and may
+// take m + 1 chunks (never more than max_chunks), so items and slots need
+// room for one more chunk per multi-chunk tree.  Three launches; `cls`:
+// plan_level0_scratch_words() zeroed words; `meta`: one word per tree;
+// `cuts`: the multi-chunk trees' chunk counts summed (the slot bound).
 uint32_t plan_level0_scratch_words();
-cudaError_t launch_plan_level0(const uint64_t *start, const uint64_t *size, uint32_t n, uint32_t C,
-                               EvalItem *items, EvalItem *ropes, uint32_t *counts, uint32_t *cls, int sms,
-                               cudaStream_t s);
+cudaError_t launch_plan_level0(const uint8_t *arena, const uint64_t *start, const uint64_t *size, uint32_t n,
+                               uint32_t C, uint32_t max_chunks, EvalItem *items, EvalItem *ropes, uint32_t *counts,
+                               uint32_t *cls, uint32_t *meta, uint32_t *cuts, int sms, cudaStream_t s);
 // Children laid out on the device from their extents: copy records, starts,
 // sizes, per-child first copy tile ([n+1]) and the tile count (three
 // launches; part_len / part_tiles: scratch of xo_layout_parts(n) entries).

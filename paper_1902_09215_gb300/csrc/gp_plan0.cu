@@ -9,30 +9,49 @@ namespace gpk {
 
 // Level-0 items of a population whose tree sizes are on the device only and
 // at most max_chunks chunks of C codes, in three grid-wide steps: (1) every
-// tree adds its chunk count (multi-chunk trees, also one rope) or one final
-// to its size class (floor of log2); (2) one thread turns the class counts
-// into cursors, larger classes first: the chunks of every multi-chunk tree
-// (fused items, the tree's slots consecutive), then every single-chunk tree
-// as a final item, and the ropes for the next launch; (3) every tree takes
-// its places from the cursors.  counts: [0] level-0 items, [1] ropes,
-// [2] slots (one per chunk).  `cls` (3 x 64 cursors and the slot cursor)
-// starts zeroed.
+// multi-chunk tree is cut into chunks (`cut_low`) and adds its chunk count
+// and one rope to its size class (floor of log2), every other tree one final
+// item; (2) one thread turns the class counts into cursors, larger classes
+// first: the chunks of every multi-chunk tree (fused items, the tree's slots
+// consecutive), then every single-chunk tree as a final item, and the ropes
+// for the next launch; (3) every tree takes its places from the cursors.
+// counts: [0] level-0 items, [1] ropes, [2] slots (one per chunk).  `cls`
+// (3 x 64 cursors, the slot cursor and the cut cursor) starts zeroed.
 // Items of one class are in no particular order (the results do not depend
 // on the order).
 constexpr int kCls = 64;
 
 __device__ __forceinline__ int size_class(uint64_t z) { return 63 - __clzll((long long)(z | 1)); }
 
-__global__ void plan0_count_kernel(const uint64_t *__restrict__ size, uint32_t n, uint32_t C, uint32_t *cls)
+// One warp per tree.  A multi-chunk tree's ends go to cuts[base .. base +
+// chunks - 2] (relative to the tree's start), base from the cut cursor;
+// meta[t] = base << 5 | (chunks - 1).
+__global__ void plan0_count_kernel(const uint8_t *__restrict__ arena, const uint64_t *__restrict__ start,
+                                   const uint64_t *__restrict__ size, uint32_t n, uint32_t C, uint32_t mcap_max,
+                                   uint32_t *cls, uint32_t *meta, uint32_t *cuts)
 {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t t = warp; t < n; t += warps) {
         const uint64_t z = size[t];
         const int c = size_class(z);
-        if (z > C) {
-            atomicAdd(&cls[c], (uint32_t)((z + C - 1) / C));
+        if (z <= C) {
+            if (lane == 0) atomicAdd(&cls[kCls + c], 1u);
+            continue;
+        }
+        const uint64_t b = start[t];
+        const uint32_t m = (uint32_t)((z + C - 1) / C);
+        const uint32_t mcap = min(m + 1, max(m, mcap_max));
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&cls[3 * kCls + 1], mcap - 1);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const uint32_t k = cut_low(arena, b, z, C, mcap, lane, [&](uint32_t j, uint64_t e) {
+            if (lane == 0) cuts[base + j - 1] = (uint32_t)(e - b);
+        });
+        if (lane == 0) {
+            meta[t] = (base << 5) | (k - 1);
+            atomicAdd(&cls[c], k);
             atomicAdd(&cls[2 * kCls + c], 1u);
-        } else {
-            atomicAdd(&cls[kCls + c], 1u);
         }
     }
 }
@@ -68,20 +87,23 @@ __global__ void plan0_bases_kernel(uint32_t *cls, uint32_t *counts)
 }
 
 __global__ void plan0_place_kernel(const uint64_t *__restrict__ start, const uint64_t *__restrict__ size, uint32_t n,
-                                   uint32_t C, EvalItem *__restrict__ items, EvalItem *__restrict__ ropes, uint32_t *cls)
+                                   uint32_t C, const uint32_t *__restrict__ meta, const uint32_t *__restrict__ cuts,
+                                   EvalItem *__restrict__ items, EvalItem *__restrict__ ropes, uint32_t *cls)
 {
     uint32_t *slots = cls + 3 * kCls;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint64_t z = size[t], b = start[t];
         const int c = size_class(z);
         if (z > C) {
-            const uint32_t m = (uint32_t)((z + C - 1) / C);
+            const uint32_t mt = meta[t], m = (mt & 31u) + 1, base = mt >> 5;
             const uint32_t p = atomicAdd(&cls[c], m);
             const uint32_t slot = atomicAdd(slots, m);
+            uint64_t lo = b;
             for (uint32_t j = 0; j < m; ++j) {
+                const uint64_t hi = j + 1 < m ? b + cuts[base + j] : b + z;
                 EvalItem it{};
-                it.begin = b + (uint64_t)j * C;
-                it.end = b + umin64(z, (uint64_t)(j + 1) * C);
+                it.begin = lo;
+                it.end = hi;
                 it.tree = t;
                 it.flags = kItemFused;
                 it.frag_off = slot + j;
@@ -89,6 +111,7 @@ __global__ void plan0_place_kernel(const uint64_t *__restrict__ start, const uin
                 it.frag_len = m;
                 it.spill_off = kNoSpill;
                 items[p + j] = it;
+                lo = hi;
             }
             EvalItem r{};
             r.tree = t;
@@ -109,17 +132,18 @@ __global__ void plan0_place_kernel(const uint64_t *__restrict__ start, const uin
     }
 }
 
-uint32_t plan_level0_scratch_words() { return 3 * kCls + 1; }
+uint32_t plan_level0_scratch_words() { return 3 * kCls + 2; }
 
-cudaError_t launch_plan_level0(const uint64_t *start, const uint64_t *size, uint32_t n, uint32_t C,
-                               EvalItem *items, EvalItem *ropes, uint32_t *counts, uint32_t *cls, int sms,
-                               cudaStream_t s)
+cudaError_t launch_plan_level0(const uint8_t *arena, const uint64_t *start, const uint64_t *size, uint32_t n,
+                               uint32_t C, uint32_t max_chunks, EvalItem *items, EvalItem *ropes, uint32_t *counts,
+                               uint32_t *cls, uint32_t *meta, uint32_t *cuts, int sms, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)umin64((n + 255) / 256, (uint64_t)sms * 4);
-    plan0_count_kernel<<<blocks, 256, 0, s>>>(size, n, C, cls);
+    const uint32_t warp_blocks = (uint32_t)umin64((n + 7) / 8, (uint64_t)sms * 16);   // a warp per tree
+    plan0_count_kernel<<<warp_blocks, 256, 0, s>>>(arena, start, size, n, C, max_chunks, cls, meta, cuts);
     plan0_bases_kernel<<<1, 3 * kCls, 0, s>>>(cls, counts);
-    plan0_place_kernel<<<blocks, 256, 0, s>>>(start, size, n, C, items, ropes, cls);
+    plan0_place_kernel<<<blocks, 256, 0, s>>>(start, size, n, C, meta, cuts, items, ropes, cls);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from paper_1902_09215_gb300 import synth
+from tests.chunk_rules import low_point_ends, spine_operators
 from tests.gpu_util import first_mismatch, gpu, same_f32  # noqa: F401
 
 pytestmark = pytest.mark.gpu
@@ -177,27 +178,6 @@ def test_repeat_evaluation_is_deterministic(gpu):
         assert same_f32(f, outs[0][0]) and same_f32(v, outs[0][1])
 
 
-def spine_operators(tree, C):
-    """Operators a chunk of C codes cannot evaluate, summed over the chunks
-    of one tree: reading right to left from a chunk's right end, the stack
-    of the whole tree at position j holds P[j] values, P being the walk of
-    open argument slots (P[0] = 1, P[j+1] = P[j] + arity - 1, Sec. 2.1's
-    prefix order).  An operator at j lacks an argument inside the chunk
-    exactly when P[j] is no higher than every P[k] for j < k <= the chunk's
-    end, i.e. when the walk reaches its running minimum there."""
-    n = tree.shape[0]
-    if n <= C:
-        return 0
-    op = tree < 4
-    P = np.concatenate([[1], 1 + np.cumsum(np.where(op, 1, -1))])
-    total = 0
-    for b in range(0, n, C):
-        e = min(b + C, n)
-        run_min = np.minimum.accumulate(P[b + 1:e + 1][::-1])[::-1]   # min of P[j+1 .. e]
-        total += int(np.sum(op[b:e] & (P[b:e] <= run_min)))
-    return total
-
-
 @pytest.mark.parametrize("C", [1024, 4096])
 def test_operators_sent_upward_follow_the_arity_walk(gpu, oracle, C):
     """The count of operators evaluated above level 0 (gp_eval_stats) equals
@@ -221,7 +201,14 @@ def test_operators_sent_upward_follow_the_arity_walk(gpu, oracle, C):
     kn, ko = oracle.crossover_population(nodes, offs, mum, dad, mp, dp)
     assert same_f32(fit, oracle.eval_population(kn, ko, x, y, c, n_threads=8)["fitness"])
     kt = [kn[int(ko[i]):int(ko[i + 1])] for i in range(60)]
-    assert gpu.gp_eval_stats_get(kids)["upper_ops"] == sum(spine_operators(t, C) for t in kt)
+    # children whose size bounds stay within 32 chunks are planned on the
+    # device, where chunks end at low points of the arity walk
+    bound = sizes[mum] + sizes[dad] - dp.astype(np.int64) - 1
+    if bound.max() <= 32 * C:
+        want = sum(spine_operators(t, C, low_point_ends(t, C)) for t in kt)
+    else:
+        want = sum(spine_operators(t, C) for t in kt)
+    assert gpu.gp_eval_stats_get(kids)["upper_ops"] == want
 
 
 def test_slot_overflow_is_evaluated_again_in_gp_fitness(gpu, oracle):
