@@ -1268,19 +1268,24 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
         const uint64_t o_pl = round_up(o_tb + sizeof(uint32_t) * (n_ops + 1), 256);
         const uint64_t o_pt = round_up(o_pl + sizeof(uint64_t) * parts, 256);
         const uint64_t o_tc = round_up(o_pt + sizeof(uint32_t) * parts, 256);
+        const uint64_t o_long = round_up(o_tc + sizeof(uint32_t) * max_tiles, 256);
         uint8_t *blk;
-        CK(tmp.alloc((void **)&blk, o_tc + sizeof(uint32_t) * max_tiles, s));
+        CK(tmp.alloc((void **)&blk, o_long + sizeof(ExtentLong) * q.size(), s));
         uint32_t *d_ntiles = reinterpret_cast<uint32_t *>(blk);
         uint64_t *d_end = reinterpret_cast<uint64_t *>(blk + o_end);
         ExtentQuery *d_q = reinterpret_cast<ExtentQuery *>(blk + o_q);
         XoChild *d_kids = reinterpret_cast<XoChild *>(blk + o_kids);
         uint32_t *d_tb = reinterpret_cast<uint32_t *>(blk + o_tb);
         uint32_t *d_lerr = C->d_stat + 3;
+        uint32_t *d_nlong = reinterpret_cast<uint32_t *>(blk + 64);
         CK(h2d(d_q, q.data(), sizeof(ExtentQuery) * q.size(), s));
+        CK(cudaMemsetAsync(d_nlong, 0, sizeof(uint32_t), s));
         {
             ProfScope ps(GP_KERNEL_EXTENT, s);
-            CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_lerr, s));
+            CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_lerr,
+                             reinterpret_cast<ExtentLong *>(blk + o_long), d_nlong, sm_count(M->device), s));
         }
+        note_launches(1);                      // the long-walk launch (the scope counts one)
         uint32_t *d_tc = reinterpret_cast<uint32_t *>(blk + o_tc);
         CK(launch_xo_layout(d_q, d_end, n_ops, tile, C->arena_bytes, d_kids, C->d_start, C->d_size, d_tb, d_tc,
                             d_ntiles, reinterpret_cast<uint64_t *>(blk + o_pl),
@@ -1303,17 +1308,21 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
             }
             // one block: error word, ends, queries
             const uint64_t o_end = 256, o_q = round_up(o_end + sizeof(uint64_t) * q.size(), 256);
+            const uint64_t o_long = round_up(o_q + sizeof(ExtentQuery) * q.size(), 256);
             uint8_t *blk;
-            CK(tmp.alloc((void **)&blk, o_q + sizeof(ExtentQuery) * q.size(), s));
+            CK(tmp.alloc((void **)&blk, o_long + sizeof(ExtentLong) * q.size(), s));
             uint32_t *d_err = reinterpret_cast<uint32_t *>(blk);
+            uint32_t *d_nlong = reinterpret_cast<uint32_t *>(blk + 64);
             uint64_t *d_end = reinterpret_cast<uint64_t *>(blk + o_end);
             ExtentQuery *d_q = reinterpret_cast<ExtentQuery *>(blk + o_q);
-            CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
+            CK(cudaMemsetAsync(d_err, 0, 128, s));          // error word and long-walk counter
             CK(h2d(d_q, q.data(), sizeof(ExtentQuery) * q.size(), s));
             {
                 ProfScope ps(GP_KERNEL_EXTENT, s);
-                CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_err, s));
+                CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_err,
+                                 reinterpret_cast<ExtentLong *>(blk + o_long), d_nlong, sm_count(M->device), s));
             }
+            note_launches(1);
             // error word and ends in one read-back
             std::vector<uint64_t> back(32 + q.size());
             CK(cudaMemcpyAsync(back.data(), blk, o_end + sizeof(uint64_t) * q.size(), cudaMemcpyDeviceToHost, s));

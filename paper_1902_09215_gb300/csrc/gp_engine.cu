@@ -870,6 +870,7 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     if ((st = galloc(v, (void **)&run_tiles_, sizeof(uint32_t) * (max_runs + 1)))) return st;
     if ((st = galloc(v, (void **)&recs_, sizeof(gp_xo) * T))) return st;
     if ((st = galloc(v, (void **)&q_, sizeof(ExtentQuery) * 2 * T))) return st;
+    if ((st = galloc(v, (void **)&xlong_, sizeof(ExtentLong) * 2 * T))) return st;
     if ((st = galloc(v, (void **)&ends_, sizeof(uint64_t) * 2 * T))) return st;
     if ((st = galloc(v, (void **)&kids_, sizeof(XoChild) * T))) return st;
     if ((st = galloc(v, (void **)&tile_local_, sizeof(uint32_t) * T))) return st;
@@ -1566,7 +1567,9 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     const uint32_t blocks = std::max<uint32_t>(1, std::min<uint32_t>((max_trees + 127) / 128, sms * 8));
     select_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, recs_, q_);
     GK(cudaGetLastError());
-    GK(launch_extent_dev(heap, q_, 2 * max_trees, &ctl->n_queries, ends_, &ctl->eval_err[1], sms, s));
+    // (eval_err[3], zeroed above, counts the walks left to the long-walk launch)
+    GK(launch_extent_dev(heap, q_, 2 * max_trees, &ctl->n_queries, ends_, &ctl->eval_err[1], xlong_,
+                         &ctl->eval_err[3], sms, s));
     children_size_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, q_, ends_, bstart_, bsize_);
     GK(cudaGetLastError());
     children_scan_kernel<<<max_runs, kScanT, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, tile_local_, run_tiles_,
@@ -1579,7 +1582,7 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     GK(cudaGetLastError());
     GK(launch_xo_copy_runs(heap, kids_, tile_local_, tree_base_, run_tiles_, &ctl->head.n_runs, &ctl->n_tiles,
                            kTile, sms, s));
-    nl += 7;
+    nl += 8;
     gp_status st = enqueue_eval(s, sizing, &nl);
     if (st) return st;
     const uint32_t sblocks =

@@ -28,6 +28,7 @@ namespace gpe {
 
 using gpk::EvalItem;
 using gpk::ExtentQuery;
+using gpk::ExtentLong;
 using gpk::PlanOut;
 using gpk::XoChild;
 
@@ -79,7 +80,8 @@ struct BatchCtl {
     BatchHead head;
     uint32_t err;                        // batch-level error bits of this batch
     uint32_t n_queries, n_tiles, n_items, n_chunks, levels;
-    uint32_t eval_err[4];                // [0] evaluator error word, [1] extent error word
+    uint32_t eval_err[4];                // [0] evaluator error word, [1] extent error word,
+                                         // [3] subtree walks left to the long-walk launch
     uint32_t n_ropes;                    // fused chunks cut at level 0 (their ropes are level 1's)
     uint32_t loop_level;                 // upper levels the captured level loop has started
     uint32_t n_rope_items;               // ropes level 0 listed (a rope-only level 1)
@@ -234,6 +236,7 @@ class Engine {
     uint32_t *bhits_ = nullptr;
     uint64_t *t_lo_ = nullptr, *t_hi_ = nullptr, *t_prev_ = nullptr;
     uint32_t *t_first_ = nullptr, *t_state_ = nullptr, *t_nch_ = nullptr, *t_cut_ = nullptr;
+    ExtentLong *xlong_ = nullptr;
     float *x_ = nullptr, *y_ = nullptr, *c_ = nullptr;
     // the last head written (a batch whose head is unchanged skips the copies)
     uint32_t last_mode_ = ~0u;

@@ -170,6 +170,13 @@ struct XoTile {
 struct ExtentQuery {
     uint64_t tree_start, tree_size, point;
 };
+// A subtree walk still open after its first step: where the next step
+// starts (16-aligned) and the subtrees still to be read there.
+struct ExtentLong {
+    uint64_t base;
+    int64_t need;
+    uint32_t w, pad;
+};
 
 // Adds n to the library's count of kernel launches (gp_kernel_launch_count).
 void note_launches(uint64_t n);
@@ -219,10 +226,13 @@ cudaError_t launch_validate(const uint8_t *codes, const EvalItem *chunks, uint32
                             uint32_t n_consts, ValOut *out, cudaStream_t s);
 cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,
                                   uint32_t n_trees, uint32_t *bad_count, cudaStream_t s);
-cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n,
-                          uint64_t *end, uint32_t *err, cudaStream_t s);
-cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32_t n_max,
-                              const uint32_t *n_dev, uint64_t *end, uint32_t *err, int sms,
+// Subtree ends of n queries (two launches: a warp step per query, then a
+// CTA per query still open; `list`: n entries of scratch, *n_long: a zeroed
+// counter).
+cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n, uint64_t *end, uint32_t *err,
+                          ExtentLong *list, uint32_t *n_long, int sms, cudaStream_t s);
+cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32_t n_max, const uint32_t *n_dev,
+                              uint64_t *end, uint32_t *err, ExtentLong *list, uint32_t *n_long, int sms,
                               cudaStream_t s);
 // Copy of children whose tiles are numbered on the device: child c owns
 // tiles [tile_base[c], tile_base[c+1]); *n_tiles_dev tiles in all.

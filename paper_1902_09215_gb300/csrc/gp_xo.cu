@@ -8,129 +8,248 @@
 
 namespace gpk {
 
-// One warp per query: the end (exclusive) of the subtree rooted at `point`.
-// Reading left to right, `need` counts subtrees still to be read: an
-// operator adds one, a leaf removes one; the subtree ends where it reaches
-// zero.  Each step covers 32 lanes x 64 bytes from a 16-byte aligned base,
-// every lane with four 16-byte loads issued together (bytes before `point`
-// or past the tree do not count; a lane loads only if its first byte is
-// inside the tree, and trees are followed by at least 64 padding bytes).
+// The end (exclusive) of the subtree rooted at `point`.  Reading left to
+// right, `need` counts subtrees still to be read: an operator adds one, a
+// leaf removes one; the subtree ends where it reaches zero.  Two phases:
+// every query first takes one step of one warp (32 lanes x 64 bytes from a
+// 16-byte aligned base, every lane with four 16-byte loads issued
+// together); a query still open after it goes to a list that the second
+// kernel walks with a whole CTA per query (512 threads x 32 bytes: 16 KB
+// per step), since a query's time is its number of dependent steps and few
+// subtrees are long.  Bytes before `point` or past the tree do not count; a
+// lane loads only if its first byte is inside the tree, and trees are
+// followed by at least 64 padding bytes.
 constexpr uint32_t kExtLane = 64;
+constexpr int kExtT = 512;                  // threads of a long-query CTA
+constexpr uint32_t kExtThr = 32;            // bytes per thread and step there
+
+// Arity walk over the four bytes of w (byte 0 first): +1 for an operator
+// (code < 4), -1 for a leaf, 0 for a byte whose byte in `cm` is zero.
+// *net: the change over the word; returns the lowest running value after
+// each of its bytes.  Byte-wise, without carries between bytes: bit 7 of
+// ((w & 0x7c) + 0x7f) | w is set exactly when the byte is >= 4; e = 2 for
+// an operator, 0 for a leaf, 1 for a byte that does not count; multiplying
+// by 0x01010101 puts e_0 + ... + e_k (at most 8) in byte k, and the
+// running value after byte k is that sum - (k + 1).
+__device__ __forceinline__ int walk_word(uint32_t w, uint32_t cm, int *net)
+{
+    const uint32_t nz = ((w & 0x7c7c7c7cu) + 0x7f7f7f7fu) | w;
+    uint32_t e = (~nz & 0x80808080u) >> 6;
+    e = (e & cm) | (0x01010101u & ~cm);
+    const uint32_t E = e * 0x01010101u;
+    const uint32_t M = E + 0x00010203u;          // byte k: running value after byte k, + 4
+    uint32_t m = __vminu4(M, M >> 16);
+    m = __vminu4(m, m >> 8);
+    *net = (int)(E >> 24) - 4;
+    return (int)(m & 0xffu) - 4;
+}
+
+// Bytes x.. of a word (x <= 0: all four, x >= 4: none).
+__device__ __forceinline__ uint32_t bytes_from(int x)
+{
+    return __funnelshift_lc(0u, 0xffffffffu, 8u * (uint32_t)max(x, 0));
+}
+
+// (net change, lowest running value) over bytes [ia, ib) of the NW words
+// of v; the lowest value is no higher than the value before the first
+// counted byte (a word with no counted byte reports that value), which
+// cannot close a walk that has not closed before.
+template <int NW>
+__device__ __forceinline__ void walk_bytes(const uint32_t *v, int ia, int ib, int &s, int &mn)
+{
+    s = 0;
+    mn = 1 << 30;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const uint32_t cm = bytes_from(ia - 4 * k) & ~bytes_from(ib - 4 * k);
+        int net;
+        const int wm = walk_word(v[k], cm, &net);
+        mn = min(mn, s + wm);
+        s += net;
+    }
+}
+
+// First byte j in [ia, ib) of v's bytes where the running value, starting
+// from r, reaches zero (-1 if none).
+template <int NB>
+__device__ __forceinline__ int first_close(const uint32_t *v, int ia, int ib, int64_t r)
+{
+    int e = -1;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (e < 0 && j >= ia && j < ib) {
+            r += ((v[j >> 2] >> (8 * (j & 3))) & 0xFFu) < 4 ? 1 : -1;
+            if (r == 0) e = j;
+        }
+    }
+    return e;
+}
 
 __device__ __forceinline__ void extent_one(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
                                            uint32_t w, int lane, uint64_t *__restrict__ end_out,
-                                           uint32_t *err)
+                                           uint32_t *err, ExtentLong *__restrict__ list, uint32_t *n_long)
 {
     const ExtentQuery Q = q[w];
     const uint64_t tend = Q.tree_start + Q.tree_size;
     const uint64_t p0 = Q.tree_start + Q.point;
-    uint64_t base = p0 & ~15ull;
-    int64_t need = 1;
-    for (;;) {
-        if (base >= tend) {
-            if (lane == 0) {
-                atomicOr(err, kErrExtent);
-                end_out[w] = Q.tree_size;
-            }
-            return;
+    const uint64_t base = p0 & ~15ull;
+    if (base >= tend) {
+        if (lane == 0) {
+            atomicOr(err, kErrExtent);
+            end_out[w] = Q.tree_size;
         }
-        const uint64_t lo = base + (uint64_t)kExtLane * lane;
-        uint4 v[kExtLane / 16];
+        return;
+    }
+    const uint64_t lo = base + (uint64_t)kExtLane * lane;
+    uint32_t v[kExtLane / 4];
 #pragma unroll
-        for (int k = 0; k < (int)(kExtLane / 16); ++k)
-            v[k] = lo < tend ? __ldg(reinterpret_cast<const uint4 *>(arena + lo) + k) : make_uint4(0, 0, 0, 0);
-        // bytes [ia, ib) of this lane's 64 count
-        const int ia = p0 > lo ? (int)umin64(p0 - lo, kExtLane) : 0;
-        const int ib = tend > lo ? (int)umin64(tend - lo, kExtLane) : 0;
-        // this lane's net change and lowest running value over its bytes
-        int s = 0, mn = 1 << 30;
-#pragma unroll
-        for (int k = 0; k < (int)(kExtLane / 16); ++k) {
-            const uint32_t wd[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int j = 16 * k + i;
-                if (j >= ia && j < ib) {
-                    s += ((wd[i >> 2] >> (8 * (i & 3))) & 0xFFu) < 4 ? 1 : -1;
-                    mn = min(mn, s);
+    for (int k = 0; k < (int)(kExtLane / 16); ++k) {
+        const uint4 x = lo < tend ? __ldg(reinterpret_cast<const uint4 *>(arena + lo) + k) : make_uint4(0, 0, 0, 0);
+        v[4 * k] = x.x;
+        v[4 * k + 1] = x.y;
+        v[4 * k + 2] = x.z;
+        v[4 * k + 3] = x.w;
+    }
+    // bytes [ia, ib) of this lane's 64 count
+    const int ia = p0 > lo ? (int)umin64(p0 - lo, kExtLane) : 0;
+    const int ib = tend > lo ? (int)umin64(tend - lo, kExtLane) : 0;
+    int s, mn;
+    walk_bytes<kExtLane / 4>(v, ia, ib, s, mn);
+    // exclusive prefix of s over lanes
+    int incl = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    const int excl = incl - s;
+    const bool closes = 1 + excl + mn <= 0;
+    const unsigned ball = __ballot_sync(0xffffffffu, closes);
+    if (ball) {
+        if (lane == __ffs(ball) - 1)
+            end_out[w] = lo + (uint64_t)first_close<kExtLane>(v, ia, ib, 1 + excl) + 1 - Q.tree_start;
+        return;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) list[atomicAdd(n_long, 1u)] = ExtentLong{base + 32ull * kExtLane, 1 + (int64_t)total, w, 0};
+}
+
+// A CTA per query of the list: 16 KB per step, a block scan of the
+// threads' net changes, the first thread whose bytes close the walk.
+__global__ void __launch_bounds__(kExtT) extent_long_kernel(const uint8_t *__restrict__ arena,
+                                                          const ExtentQuery *__restrict__ q,
+                                                          const ExtentLong *__restrict__ list,
+                                                          const uint32_t *n_long, uint64_t *__restrict__ end_out,
+                                                          uint32_t *err)
+{
+    __shared__ int s_wsum[kExtT / 32];
+    __shared__ int s_first;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t n = *n_long;
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const ExtentLong L = list[i];
+        const ExtentQuery Q = q[L.w];
+        const uint64_t tend = Q.tree_start + Q.tree_size;
+        uint64_t base = L.base;                        // 16-aligned, past the query's point
+        int64_t need = L.need;
+        for (;;) {
+            if (base >= tend) {
+                if (tid == 0) {
+                    atomicOr(err, kErrExtent);
+                    end_out[L.w] = Q.tree_size;
                 }
+                break;
             }
-        }
-        // exclusive prefix of s over lanes
-        int incl = s;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += o;
-        }
-        const int excl = incl - s;
-        const bool closes = need + excl + mn <= 0;
-        const unsigned ball = __ballot_sync(0xffffffffu, closes);
-        if (ball) {
-            const int f = __ffs(ball) - 1;
-            if (lane == f) {
-                int64_t r = need + excl;
-                int e = -1;
+            if (tid == 0) s_first = kExtT;
+            const uint64_t lo = base + (uint64_t)kExtThr * tid;
+            uint32_t v[kExtThr / 4];
 #pragma unroll
-                for (int k = 0; k < (int)(kExtLane / 16); ++k) {
-                    const uint32_t wd[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int j = 16 * k + i;
-                        if (e < 0 && j >= ia && j < ib) {
-                            r += ((wd[i >> 2] >> (8 * (i & 3))) & 0xFFu) < 4 ? 1 : -1;
-                            if (r == 0) e = j;
-                        }
-                    }
-                }
-                end_out[w] = lo + (uint64_t)e + 1 - Q.tree_start;
+            for (int k = 0; k < (int)(kExtThr / 16); ++k) {
+                const uint4 x =
+                    lo < tend ? __ldg(reinterpret_cast<const uint4 *>(arena + lo) + k) : make_uint4(0, 0, 0, 0);
+                v[4 * k] = x.x;
+                v[4 * k + 1] = x.y;
+                v[4 * k + 2] = x.z;
+                v[4 * k + 3] = x.w;
             }
-            return;
+            const int ib = tend > lo ? (int)umin64(tend - lo, kExtThr) : 0;
+            int s, mn;
+            walk_bytes<kExtThr / 4>(v, 0, ib, s, mn);
+            int incl = s;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += o;
+            }
+            if (lane == 31) s_wsum[wid] = incl;
+            __syncthreads();
+            int before = 0, total = 0;
+#pragma unroll
+            for (int k = 0; k < kExtT / 32; ++k) {
+                const int x = s_wsum[k];
+                before += k < wid ? x : 0;
+                total += x;
+            }
+            const int64_t r0 = need + before + incl - s;   // the running value before this thread's bytes
+            if (r0 + mn <= 0) atomicMin(&s_first, tid);
+            __syncthreads();
+            const int f = s_first;
+            if (f < kExtT) {
+                if (tid == f) end_out[L.w] = lo + (uint64_t)first_close<kExtThr>(v, 0, ib, r0) + 1 - Q.tree_start;
+                break;
+            }
+            need += total;
+            base += (uint64_t)kExtT * kExtThr;
+            __syncthreads();                               // s_wsum and s_first are written again
         }
-        need += __shfl_sync(0xffffffffu, incl, 31);
-        base += 32ull * kExtLane;
+        __syncthreads();
     }
 }
 
-__global__ void extent_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
-                              uint32_t n, uint64_t *__restrict__ end_out, uint32_t *err)
+// (8 CTAs of 256 per SM: the 8000 queries of 4000 children in one wave)
+__global__ void __launch_bounds__(256, 8) extent_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
+                              uint32_t n, uint64_t *__restrict__ end_out, uint32_t *err,
+                              ExtentLong *__restrict__ list, uint32_t *n_long)
 {
     const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= n) return;
-    extent_one(arena, q, w, threadIdx.x & 31, end_out, err);
+    extent_one(arena, q, w, threadIdx.x & 31, end_out, err, list, n_long);
 }
 
 // Same, with the query count read on the device and a grid-stride loop.
-__global__ void extent_dev_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
+__global__ void __launch_bounds__(256, 8) extent_dev_kernel(const uint8_t *__restrict__ arena, const ExtentQuery *__restrict__ q,
                                   uint32_t n_max, const uint32_t *n_dev, uint64_t *__restrict__ end_out,
-                                  uint32_t *err)
+                                  uint32_t *err, ExtentLong *__restrict__ list, uint32_t *n_long)
 {
     const uint32_t n = min(n_max, *n_dev);
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += n_warps)
-        extent_one(arena, q, w, threadIdx.x & 31, end_out, err);
+        extent_one(arena, q, w, threadIdx.x & 31, end_out, err, list, n_long);
 }
 
-cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n,
-                          uint64_t *end, uint32_t *err, cudaStream_t s)
+cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n, uint64_t *end, uint32_t *err,
+                          ExtentLong *list, uint32_t *n_long, int sms, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const uint32_t blocks = (uint32_t)(((uint64_t)n * 32 + threads - 1) / threads);
-    extent_kernel<<<blocks, threads, 0, s>>>(arena, q, n, end, err);
+    extent_kernel<<<blocks, threads, 0, s>>>(arena, q, n, end, err, list, n_long);
+    extent_long_kernel<<<(uint32_t)umin64(n, (uint64_t)sms * 4), kExtT, 0, s>>>(arena, q, list, n_long, end, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32_t n_max,
-                              const uint32_t *n_dev, uint64_t *end, uint32_t *err, int sms,
+cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32_t n_max, const uint32_t *n_dev,
+                              uint64_t *end, uint32_t *err, ExtentLong *list, uint32_t *n_long, int sms,
                               cudaStream_t s)
 {
     if (n_max == 0) return cudaSuccess;
     const int threads = 256;
     const uint64_t want = ((uint64_t)n_max * 32 + threads - 1) / threads;
     const uint32_t blocks = (uint32_t)umin64(want, (uint64_t)sms * 16);
-    extent_dev_kernel<<<blocks, threads, 0, s>>>(arena, q, n_max, n_dev, end, err);
+    extent_dev_kernel<<<blocks, threads, 0, s>>>(arena, q, n_max, n_dev, end, err, list, n_long);
+    extent_long_kernel<<<(uint32_t)umin64(n_max, (uint64_t)sms * 4), kExtT, 0, s>>>(arena, q, list, n_long, end,
+                                                                                   err);
     return cudaGetLastError();
 }
+
 
 // Source byte of child byte p.
 __device__ __forceinline__ uint64_t xo_src(const XoChild &c, uint64_t p) {
