@@ -780,8 +780,8 @@ def config4_batched(gp, prob, stream, flush, cpu, steps=3):
     out = {"workload": desc, "parent_nodes": int(offs[-1]), "child_nodes": child_nodes,
            "population_build_s": build_s, "create_s": create_s, "chunk_nodes": chunk,
            "autotune": {"chunk": {str(k): v for k, v in zip(info0["autotune_chunk"], info0["autotune_ms"]) if k},
-                        "shape": {f"{w}x{k}": v for (w, k), v in zip(info0["autotune_shape"],
-                                                                      info0["autotune_shape_ms"]) if w}},
+                        "shape": {f"{lv} {w}x{k}": v for (w, k, lv), v in zip(info0["autotune_shape"],
+                                                                              info0["autotune_shape_ms"]) if w}},
            "levels": int(info1["levels"]),
            "batched_vs_plain": cmp,
            "e2e": {"value": units / e2e_s, "unit": "GPops/s", "wall_s": e2e_s,
@@ -1162,7 +1162,7 @@ def run_batched(args):
                    "population_build_s": gen_s, "create_s": create_s},
         "latency_ms": {"p50": med, "p99": nearest_rank(ms, 0.99), "rule": f"nearest rank over {len(ms)} steps"},
         "autotune": {str(k): v for k, v in zip(info0["autotune_chunk"], info0["autotune_ms"]) if k},
-        "autotune_shape": {f"{w}x{k}": v for (w, k), v in zip(info0["autotune_shape"], info0["autotune_shape_ms"])
+        "autotune_shape": {f"{lv} {w}x{k}": v for (w, k, lv), v in zip(info0["autotune_shape"], info0["autotune_shape_ms"])
                            if w},
         "launch_shape": {"level0": [info0["warps_per_cta"], info0["window_entries"]],
                          "upper": [info0["upper_warps"], info0["upper_window_entries"]],

@@ -292,7 +292,8 @@ typedef struct gp_generation_info {
     uint32_t upper_warps, upper_window_entries;         /* upper levels'                  */
     uint32_t rope_warps, rope_window_entries;           /* a rope-only level's            */
     uint32_t autotune_shape[8];  /* shapes tried, (warps << 16) | window entries: level 0's
-                                    first, then the upper levels' (0 = unused slot)     */
+                                    first, then the upper levels' with 0x8000 added to
+                                    the window entries (0 = unused slot)                */
     float autotune_shape_ms[8];  /* their evaluation time on the initial population     */
 } gp_generation_info;
 

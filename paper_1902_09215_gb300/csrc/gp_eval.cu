@@ -345,6 +345,20 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
     const float2 *pt_src = P.pt_in;       // value entries read by the current range
     uint64_t rb = IT(begin), re = IT(end);  // the current range
     auto stage = [&](const Group<Code> &grp, int64_t gbase, uint32_t into) {
+        const uint32_t sbase = stage_sa + into * 16 * S;
+        const float2 *src = pt_src + lane;
+        if ((uint64_t)gbase >= rb && (uint64_t)gbase + 16 <= re) {   // a whole group of the range
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const typename Group<Code>::Sub v = grp.sub(q);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t c = Group<Code>::code(v, k);
+                    if (c >= kPtCode0) cp_async8(sbase + (4 * q + k) * S, src + (uint64_t)(c - kPtCode0) * LANES);
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const typename Group<Code>::Sub v = grp.sub(q);
@@ -353,8 +367,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
                 const uint32_t c = Group<Code>::code(v, k);
                 const uint64_t pos = (uint64_t)gbase + 4 * q + k;
                 if (pos >= rb && pos < re && c >= kPtCode0)
-                    cp_async8(stage_sa + (into * 16 + 4 * q + k) * S,
-                              pt_src + (uint64_t)(c - kPtCode0) * LANES + lane);
+                    cp_async8(sbase + (4 * q + k) * S, src + (uint64_t)(c - kPtCode0) * LANES);
             }
         }
     };

@@ -265,7 +265,7 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
         return w;
     };
     uint32_t shape_k = 0;
-    auto time_shape = [&](uint32_t W, uint32_t K, uint32_t Ku, float *ms) -> gp_status {
+    auto time_shape = [&](uint32_t W, uint32_t K, uint32_t Ku, bool upper, float *ms) -> gp_status {
         gp_status e = E.set_shape(W, K, upper_warps(Ku), Ku, E.Wr, E.Kr);
         if (e) return e;
         if ((e = E.set_workspace(best_C, cap_codes, cap_vals, cap_ded, cap_items, best_slots, best_pt))) return e;
@@ -275,7 +275,7 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
         if ((e = E.read_run(G->run, &R, cs))) return e;
         if (t < 0.f || R.err) return R.err ? map_err(R.err, 0) : GP_ECUDA;
         if (shape_k < 8) {
-            G->info.autotune_shape[shape_k] = (W << 16) | K;
+            G->info.autotune_shape[shape_k] = upper ? (upper_warps(Ku) << 16) | 0x8000u | Ku : (W << 16) | K;
             G->info.autotune_shape_ms[shape_k] = t;
             ++shape_k;
         }
@@ -300,7 +300,7 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
             if (done[0] == ((W << 16) | K) || done[1] == ((W << 16) | K)) continue;
             done[i] = (W << 16) | K;
             float ms = 0.f;
-            if ((st = time_shape(W, K, bKu, &ms))) return fail(st);
+            if ((st = time_shape(W, K, bKu, false, &ms))) return fail(st);
             if (best < 0.f || ms < best) {
                 best = ms;
                 bW = W;
@@ -314,7 +314,7 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
         float best = -1.f;
         for (uint32_t Ku : cand) {
             float ms = 0.f;
-            if ((st = time_shape(bW, bK, Ku, &ms))) return fail(st);
+            if ((st = time_shape(bW, bK, Ku, true, &ms))) return fail(st);
             if (best < 0.f || ms < best) {
                 best = ms;
                 bKu = Ku;

@@ -490,7 +490,9 @@ def gp_generation_get_info(g: Generation) -> dict:
     d = {k: getattr(i, k) for k, _ in gp_generation_info._fields_}
     d["autotune_chunk"] = list(i.autotune_chunk)
     d["autotune_ms"] = list(i.autotune_ms)
-    d["autotune_shape"] = [(v >> 16, v & 0xFFFF) for v in i.autotune_shape]
+    # (warps, window entries, "level0" | "upper"); (0, 0, "") for an unused slot
+    d["autotune_shape"] = [(v >> 16, v & 0x7FFF, ("upper" if v & 0x8000 else "level0") if v else "")
+                           for v in i.autotune_shape]
     d["autotune_shape_ms"] = list(i.autotune_shape_ms)
     return d
 

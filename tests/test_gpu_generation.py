@@ -349,8 +349,12 @@ def test_launch_shapes_are_exact_and_reported(gpu, oracle):
         if W:
             assert (info["warps_per_cta"], info["window_entries"], info["upper_window_entries"]) == (W, K, Ku)
         else:
-            tried = [s for s in info["autotune_shape"] if s != (0, 0)]
-            assert len(tried) >= 4 and (info["warps_per_cta"], info["window_entries"]) in tried
+            tried = [s for s in info["autotune_shape"] if s[0]]
+            level0 = [(w, k) for w, k, lv in tried if lv == "level0"]
+            upper = [(w, k) for w, k, lv in tried if lv == "upper"]
+            assert len(level0) >= 1 and len(upper) == 3, tried
+            assert (info["warps_per_cta"], info["window_entries"]) in level0
+            assert (info["upper_warps"], info["upper_window_entries"]) in upper
             assert info["upper_window_entries"] in (96, 128, 192)
             assert all(t > 0 for t in info["autotune_shape_ms"][:len(tried)])
         for g in range(2):
