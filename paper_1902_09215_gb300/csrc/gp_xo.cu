@@ -11,15 +11,14 @@ namespace gpk {
 // The end (exclusive) of the subtree rooted at `point`.  Reading left to
 // right, `need` counts subtrees still to be read: an operator adds one, a
 // leaf removes one; the subtree ends where it reaches zero.  Two phases:
-// every query first takes one step of one warp (32 lanes x 64 bytes from a
-// 16-byte aligned base, every lane with four 16-byte loads issued
-// together); a query still open after it goes to a list that the second
-// kernel walks with a whole CTA per query (512 threads x 32 bytes: 16 KB
-// per step), since a query's time is its number of dependent steps and few
-// subtrees are long.  Bytes before `point` or past the tree do not count; a
+// every query first takes one step of one warp (32 lanes x 16 bytes from a
+// 16-byte aligned base: most subtrees are a few nodes); a query still open
+// after it goes to a list that the second kernel walks with a whole CTA
+// per query (512 threads x 32 bytes: 16 KB per step), since a query's time
+// is its number of dependent steps and few subtrees are long.  Bytes before `point` or past the tree do not count; a
 // lane loads only if its first byte is inside the tree, and trees are
 // followed by at least 64 padding bytes.
-constexpr uint32_t kExtLane = 64;
+constexpr uint32_t kExtLane = 16;
 constexpr int kExtT = 512;                  // threads of a long-query CTA
 constexpr uint32_t kExtThr = 32;            // bytes per thread and step there
 
@@ -110,7 +109,7 @@ __device__ __forceinline__ void extent_one(const uint8_t *__restrict__ arena, co
         v[4 * k + 2] = x.z;
         v[4 * k + 3] = x.w;
     }
-    // bytes [ia, ib) of this lane's 64 count
+    // bytes [ia, ib) of this lane's kExtLane count
     const int ia = p0 > lo ? (int)umin64(p0 - lo, kExtLane) : 0;
     const int ib = tend > lo ? (int)umin64(tend - lo, kExtLane) : 0;
     int s, mn;
