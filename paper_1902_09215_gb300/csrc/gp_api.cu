@@ -1261,7 +1261,11 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
         const uint64_t o_kids = round_up(o_q + sizeof(ExtentQuery) * q.size(), 256);
         const uint64_t o_tb = round_up(o_kids + sizeof(XoChild) * n_ops, 256);
         const uint32_t parts = xo_layout_parts(n_ops);
-        const uint32_t tile = 16384;
+        // copy tiles: a warp per 2 KB tile when the children are small (mean
+        // bound under 8 KB; a CTA per tile would idle most of its threads),
+        // else a CTA per 16 KB tile
+        const bool warp_tiles = (bound_arena - 64) < 8192ull * n_ops;
+        const uint32_t tile = warp_tiles ? 2048 : 16384;
         uint64_t max_tiles = 0;                // children are no larger than their bounds
         for (uint64_t b : C->h_bound) max_tiles += (b + tile - 1) / tile;
         if (max_tiles > 0x7fffffffull) return GP_ENOMEM;
@@ -1292,7 +1296,8 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
                             reinterpret_cast<uint32_t *>(blk + o_pt), d_lerr, s));
         {
             ProfScope ps(GP_KERNEL_COPY, s);
-            CK(launch_xo_copy_map(M->d_arena, C->d_arena, d_kids, d_tb, d_tc, d_ntiles, (uint32_t)max_tiles, tile, s));
+            CK(launch_xo_copy_map(M->d_arena, C->d_arena, d_kids, d_tb, d_tc, d_ntiles, (uint32_t)max_tiles, tile,
+                                  warp_tiles, s));
         }
         note_launches(3);                      // the layout kernels (the others are counted by scope)
         return GP_OK;

@@ -217,11 +217,12 @@ cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_
                              uint64_t arena_cap, XoChild *kids, uint64_t *cstart, uint64_t *csize,
                              uint32_t *tile_base, uint32_t *tile_child, uint32_t *n_tiles, uint64_t *part_len,
                              uint32_t *part_tiles, uint32_t *err, cudaStream_t s);
-// Copy of children laid out by launch_xo_layout (tile -> child map); one CTA
-// per tile up to max_tiles (at least the tile count the layout finds).
+// Copy of children laid out by launch_xo_layout (tile -> child map); a CTA
+// per tile, or a warp per tile when warp_tiles, over up to max_tiles tiles
+// (at least the tile count the layout finds).
 cudaError_t launch_xo_copy_map(const uint8_t *src, uint8_t *dst, const XoChild *children, const uint32_t *tile_base,
                                const uint32_t *tile_child, const uint32_t *n_tiles_dev, uint32_t max_tiles,
-                               uint32_t tile_bytes, cudaStream_t s);
+                               uint32_t tile_bytes, bool warp_tiles, cudaStream_t s);
 cudaError_t launch_validate(const uint8_t *codes, const EvalItem *chunks, uint32_t n_chunks,
                             uint32_t n_consts, ValOut *out, cudaStream_t s);
 cudaError_t launch_validate_trees(const ValOut *chunk_out, const uint32_t *tree_first_chunk,

@@ -267,19 +267,22 @@ __device__ __forceinline__ uint4 load16_unaligned(const uint8_t *src, uint64_t a
                       __byte_perm(w3, w4, sel));
 }
 
-// One CTA per tile of one child; every thread writes aligned 16-byte words
+// One tile of one child, by the threads first, first + stride, ... of a
+// CTA or a warp; every thread writes aligned 16-byte words
 // (children start 16-byte aligned, tiles are multiples of 16 bytes; the
 // bytes from the child's end to the next 16-byte boundary are its padding
 // and are written as zeros).  A word inside one of the child's three
 // segments is assembled from aligned loads; the few words across a segment
 // boundary or the child's end go byte by byte.
 __device__ __forceinline__ void copy_tile(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
-                                          const XoChild &c, uint64_t tbegin, uint32_t tile_bytes)
+                                          const XoChild &c, uint64_t tbegin, uint32_t tile_bytes,
+                                          uint32_t first, uint32_t stride)
 {
     const uint64_t tend = umin64(tbegin + tile_bytes, (c.n + 15) & ~15ull);
     uint4 *d16 = reinterpret_cast<uint4 *>(dst + c.dst);
     const uint64_t b1 = c.i, b2 = c.i + c.ld;
-    for (uint64_t p = tbegin + 16ull * threadIdx.x; p < tend; p += 16ull * blockDim.x) {
+#pragma unroll 4
+    for (uint64_t p = tbegin + 16ull * first; p < tend; p += 16ull * stride) {
         uint4 v;
         const uint64_t q = p + 15;
         const bool one_seg = (q < c.n) && ((q < b1) || (p >= b1 && q < b2) || (p >= b2));
@@ -300,7 +303,7 @@ __global__ void xo_copy_kernel(const uint8_t *__restrict__ src, uint8_t *__restr
                                uint32_t tile_bytes)
 {
     const XoTile T = tiles[blockIdx.x];
-    copy_tile(src, dst, children[T.child], T.begin, tile_bytes);
+    copy_tile(src, dst, children[T.child], T.begin, tile_bytes, threadIdx.x, blockDim.x);
 }
 
 // Tiles numbered on the device: a CTA takes tiles t = blockIdx.x, +gridDim.x,
@@ -318,7 +321,8 @@ __global__ void xo_copy_dev_kernel(const uint8_t *__restrict__ src, uint8_t *__r
             if (tile_base[mid] <= t) lo = mid;
             else hi = mid;
         }
-        copy_tile(src, dst, children[lo], (uint64_t)(t - tile_base[lo]) * tile_bytes, tile_bytes);
+        copy_tile(src, dst, children[lo], (uint64_t)(t - tile_base[lo]) * tile_bytes, tile_bytes, threadIdx.x,
+                  blockDim.x);
     }
 }
 
@@ -354,7 +358,8 @@ __global__ void xo_copy_runs_kernel(uint8_t *__restrict__ heap, const XoChild *_
             if (tile_local[mid] <= lt) a = mid;
             else b = mid;
         }
-        copy_tile(heap, heap, kids[a], (uint64_t)(lt - tile_local[a]) * tile_bytes, tile_bytes);
+        copy_tile(heap, heap, kids[a], (uint64_t)(lt - tile_local[a]) * tile_bytes, tile_bytes, threadIdx.x,
+                  blockDim.x);
     }
 }
 
@@ -541,25 +546,35 @@ cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_
 
 // Copy tiles numbered on the device, each tile's child read from the map the
 // layout wrote: a CTA takes tiles t = blockIdx.x, +gridDim.x, ...
+// A CTA per tile (large children), or a warp per tile (small children:
+// a CTA per tile would leave most of its threads idle).
+template <bool WARP>
 __global__ void xo_copy_map_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
                                    const XoChild *__restrict__ children, const uint32_t *__restrict__ tile_base,
                                    const uint32_t *__restrict__ tile_child, const uint32_t *n_tiles_dev,
                                    uint32_t tile_bytes)
 {
     const uint32_t n_tiles = *n_tiles_dev;
-    for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint32_t first = WARP ? (threadIdx.x & 31) : threadIdx.x, stride = WARP ? 32 : blockDim.x;
+    const uint32_t unit = WARP ? (blockIdx.x * blockDim.x + threadIdx.x) >> 5 : blockIdx.x;
+    const uint32_t units = WARP ? (gridDim.x * blockDim.x) >> 5 : gridDim.x;
+    for (uint32_t t = unit; t < n_tiles; t += units) {
         const uint32_t k = tile_child[t];
-        copy_tile(src, dst, children[k], (uint64_t)(t - tile_base[k]) * tile_bytes, tile_bytes);
+        copy_tile(src, dst, children[k], (uint64_t)(t - tile_base[k]) * tile_bytes, tile_bytes, first, stride);
     }
 }
 
 cudaError_t launch_xo_copy_map(const uint8_t *src, uint8_t *dst, const XoChild *children, const uint32_t *tile_base,
                                const uint32_t *tile_child, const uint32_t *n_tiles_dev, uint32_t max_tiles,
-                               uint32_t tile_bytes, cudaStream_t s)
+                               uint32_t tile_bytes, bool warp_tiles, cudaStream_t s)
 {
     if (max_tiles == 0) return cudaSuccess;
-    xo_copy_map_kernel<<<(uint32_t)umin64(max_tiles, 8192), 256, 0, s>>>(src, dst, children, tile_base, tile_child,
-                                                                         n_tiles_dev, tile_bytes);
+    if (warp_tiles)
+        xo_copy_map_kernel<true><<<(uint32_t)umin64((max_tiles + 7) / 8, 2048), 256, 0, s>>>(
+            src, dst, children, tile_base, tile_child, n_tiles_dev, tile_bytes);
+    else
+        xo_copy_map_kernel<false><<<(uint32_t)umin64(max_tiles, 8192), 256, 0, s>>>(
+            src, dst, children, tile_base, tile_child, n_tiles_dev, tile_bytes);
     return cudaGetLastError();
 }
 
