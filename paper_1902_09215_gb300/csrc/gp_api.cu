@@ -1025,16 +1025,19 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
         const uint64_t o_spill = take(8ull * lanes * warps_total * spill_per_warp);
         uint8_t *blk;
         CK(ws.alloc((void **)&blk, off, s));
-        CK(cudaMemsetAsync(blk, 0, o_cnt + 256 + 16 + 4ull * P->n_trees, s));   // cursors, counters, flags
         uint32_t *d_counter = reinterpret_cast<uint32_t *>(blk + o_cnt);
         uint32_t *d_counts = d_counter + 64;
         EvalItem *items = reinterpret_cast<EvalItem *>(blk + o_items);
         EvalItem *ropes = reinterpret_cast<EvalItem *>(blk + o_ropes);
+        // one launch zeroes the cursors, counters and flags of `blk` and the
+        // population's error, stat and redo words; the planned counts go to
+        // d_stat[0..2] from the planner itself
         CK(launch_plan_level0(P->d_arena, P->d_start, P->d_size, P->n_trees, C, kFuseMaxChunks, items, ropes,
                               d_counts, reinterpret_cast<uint32_t *>(blk + o_cls),
                               reinterpret_cast<uint32_t *>(blk + o_meta), reinterpret_cast<uint32_t *>(blk + o_cuts),
-                              sms, s));
-        note_launches(3);
+                              reinterpret_cast<uint32_t *>(blk), (uint32_t)((o_cnt + 256 + 16 + 4ull * P->n_trees) / 4),
+                              P->d_err, P->d_stat, sms, s));
+        note_launches(4);
         EvalParams p{};
         p.codes = P->d_arena;
         p.items = items;
@@ -1079,7 +1082,6 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
             CK(launch_eval(lanes, true, p, sms, (int)cfg.Wr, cfg.smem_r, s));
             P->redo_pending = true;
         }
-        CK(cudaMemcpyAsync(P->d_stat, d_counts, sizeof(uint32_t) * 3, cudaMemcpyDeviceToDevice, s));
         P->stat_pending = true;
         return GP_OK;
     };
@@ -1110,14 +1112,12 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
     gp_status st = eval_config(P, opt, &cfg);
     if (st) return st;
     P->cfg = cfg;
-    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
-    CK(cudaMemsetAsync(P->d_stat + 4, 0, sizeof(uint32_t) * 3, s));
-    CK(cudaMemsetAsync(P->d_redo, 0, sizeof(uint32_t), s));
     P->up_read = false;
     if (!P->host_layout) {
         uint64_t bmax = 0;
         for (uint64_t b : P->h_bound) bmax = std::max(bmax, b);
         if (bmax <= (uint64_t)kFuseMaxChunks * cfg.C) {
+            // (the planner's first launch zeroes the error, stat and redo words)
             st = eval_device_planned(P, cfg, s);
             if (st) return st;
             CK(cudaEventRecord(P->ev, s));
@@ -1126,6 +1126,9 @@ gp_status gp_evaluate_ex(gp_population *P, const gp_eval_options *opt, void *cud
         }
         if ((st = ensure_host_layout(P))) return st;
     }
+    CK(cudaMemsetAsync(P->d_err, 0, sizeof(uint32_t) * 4, s));
+    CK(cudaMemsetAsync(P->d_stat + 4, 0, sizeof(uint32_t) * 3, s));
+    CK(cudaMemsetAsync(P->d_redo, 0, sizeof(uint32_t), s));
     std::vector<uint32_t> all(P->n_trees);
     for (uint32_t t = 0; t < P->n_trees; ++t) all[t] = t;
     st = eval_trees(P, all, cfg, true, s);
@@ -1251,13 +1254,16 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
         C->arena_bytes = bound_arena;
         gp_status r = alloc_population(C, s);
         if (r) return r;
-        std::vector<ExtentQuery> q(2 * (size_t)n_ops);
+        // the queries go up with one zeroed entry after them, whose first
+        // word is the long-walk counter of the extent launches
+        const uint32_t n_q = 2 * n_ops;
+        std::vector<ExtentQuery> q(n_q + 1, ExtentQuery{0, 0, 0});
         for (uint32_t k = 0; k < n_ops; ++k) {
             q[2 * k] = ExtentQuery{M->h_start[ops[k].mum], M->h_size[ops[k].mum], ops[k].mum_point};
             q[2 * k + 1] = ExtentQuery{M->h_start[ops[k].dad], M->h_size[ops[k].dad], ops[k].dad_point};
         }
         // one block: tile count, ends, queries, copy records, first tiles
-        const uint64_t o_end = 256, o_q = round_up(o_end + sizeof(uint64_t) * q.size(), 256);
+        const uint64_t o_end = 256, o_q = round_up(o_end + sizeof(uint64_t) * n_q, 256);
         const uint64_t o_kids = round_up(o_q + sizeof(ExtentQuery) * q.size(), 256);
         const uint64_t o_tb = round_up(o_kids + sizeof(XoChild) * n_ops, 256);
         const uint32_t parts = xo_layout_parts(n_ops);
@@ -1274,19 +1280,18 @@ gp_status gp_crossover(const gp_population *M, const gp_xo *ops, uint32_t n_ops,
         const uint64_t o_tc = round_up(o_pt + sizeof(uint32_t) * parts, 256);
         const uint64_t o_long = round_up(o_tc + sizeof(uint32_t) * max_tiles, 256);
         uint8_t *blk;
-        CK(tmp.alloc((void **)&blk, o_long + sizeof(ExtentLong) * q.size(), s));
+        CK(tmp.alloc((void **)&blk, o_long + sizeof(ExtentLong) * n_q, s));
         uint32_t *d_ntiles = reinterpret_cast<uint32_t *>(blk);
         uint64_t *d_end = reinterpret_cast<uint64_t *>(blk + o_end);
         ExtentQuery *d_q = reinterpret_cast<ExtentQuery *>(blk + o_q);
         XoChild *d_kids = reinterpret_cast<XoChild *>(blk + o_kids);
         uint32_t *d_tb = reinterpret_cast<uint32_t *>(blk + o_tb);
         uint32_t *d_lerr = C->d_stat + 3;
-        uint32_t *d_nlong = reinterpret_cast<uint32_t *>(blk + 64);
+        uint32_t *d_nlong = reinterpret_cast<uint32_t *>(d_q + n_q);
         CK(h2d(d_q, q.data(), sizeof(ExtentQuery) * q.size(), s));
-        CK(cudaMemsetAsync(d_nlong, 0, sizeof(uint32_t), s));
         {
             ProfScope ps(GP_KERNEL_EXTENT, s);
-            CK(launch_extent(M->d_arena, d_q, (uint32_t)q.size(), d_end, d_lerr,
+            CK(launch_extent(M->d_arena, d_q, n_q, d_end, d_lerr,
                              reinterpret_cast<ExtentLong *>(blk + o_long), d_nlong, sm_count(M->device), s));
         }
         note_launches(1);                      // the long-walk launch (the scope counts one)

@@ -202,13 +202,17 @@ cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uin
 // finals), counts[1] ropes (next launch), counts[2] slots.  A multi-chunk
 // tree of m = ceil(n / C) chunks is cut where its arity walk is low and may
 // take m + 1 chunks (never more than max_chunks), so items and slots need
-// room for one more chunk per multi-chunk tree.  Three launches; `cls`:
-// plan_level0_scratch_words() zeroed words; `meta`: one word per tree;
-// `cuts`: the multi-chunk trees' chunk counts summed (the slot bound).
+// room for one more chunk per multi-chunk tree.  Four launches: the first
+// zeroes zero[0 .. n_zero) (which must hold `cls`, plan_level0_scratch_
+// words() words, and whatever else the caller needs zeroed), err[0..3],
+// err[12] and stat[4..6]; the planned counts also go to stat[0..2].
+// `meta`: one word per tree; `cuts`: the multi-chunk trees' chunk counts
+// summed (the slot bound).
 uint32_t plan_level0_scratch_words();
 cudaError_t launch_plan_level0(const uint8_t *arena, const uint64_t *start, const uint64_t *size, uint32_t n,
                                uint32_t C, uint32_t max_chunks, EvalItem *items, EvalItem *ropes, uint32_t *counts,
-                               uint32_t *cls, uint32_t *meta, uint32_t *cuts, int sms, cudaStream_t s);
+                               uint32_t *cls, uint32_t *meta, uint32_t *cuts, uint32_t *zero, uint32_t n_zero,
+                               uint32_t *err, uint32_t *stat, int sms, cudaStream_t s);
 // Children laid out on the device from their extents: copy records, starts,
 // sizes, per-child first copy tile ([n+1]) and the tile count (three
 // launches; part_len / part_tiles: scratch of xo_layout_parts(n) entries).

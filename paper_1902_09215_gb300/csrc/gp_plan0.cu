@@ -56,7 +56,19 @@ __global__ void plan0_count_kernel(const uint8_t *__restrict__ arena, const uint
     }
 }
 
-__global__ void plan0_bases_kernel(uint32_t *cls, uint32_t *counts)
+// Zeroes the planner's scratch words and the population's evaluation
+// words: err[0..3] (error words), stat[4..6] (what level 0 sends upward),
+// err[12] (the redo count); stat[3] (the crossover layout's error) stays.
+__global__ void plan0_zero_kernel(uint32_t *__restrict__ zero, uint32_t n_zero, uint32_t *err, uint32_t *stat)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_zero; i += gridDim.x * blockDim.x) zero[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 4) err[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x >= 4 && threadIdx.x < 7) stat[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 7) err[12] = 0;
+}
+
+// counts[0..2] (and stat[0..2] when given) from the class counts.
+__global__ void plan0_bases_kernel(uint32_t *cls, uint32_t *counts, uint32_t *stat)
 {
     __shared__ uint32_t v[3 * kCls];
     for (int i = threadIdx.x; i < 3 * kCls; i += blockDim.x) v[i] = cls[i];
@@ -81,6 +93,11 @@ __global__ void plan0_bases_kernel(uint32_t *cls, uint32_t *counts)
         }
         counts[0] = pos;
         counts[1] = r;
+        if (stat) {
+            stat[0] = pos;
+            stat[1] = r;
+            stat[2] = counts[2];
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * kCls; i += blockDim.x) cls[i] = v[i];
@@ -136,13 +153,16 @@ uint32_t plan_level0_scratch_words() { return 3 * kCls + 2; }
 
 cudaError_t launch_plan_level0(const uint8_t *arena, const uint64_t *start, const uint64_t *size, uint32_t n,
                                uint32_t C, uint32_t max_chunks, EvalItem *items, EvalItem *ropes, uint32_t *counts,
-                               uint32_t *cls, uint32_t *meta, uint32_t *cuts, int sms, cudaStream_t s)
+                               uint32_t *cls, uint32_t *meta, uint32_t *cuts, uint32_t *zero, uint32_t n_zero,
+                               uint32_t *err, uint32_t *stat, int sms, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)umin64((n + 255) / 256, (uint64_t)sms * 4);
     const uint32_t warp_blocks = (uint32_t)umin64((n + 7) / 8, (uint64_t)sms * 16);   // a warp per tree
+    plan0_zero_kernel<<<(uint32_t)umin64((n_zero + 255) / 256 + 1, (uint64_t)sms * 4), 256, 0, s>>>(zero, n_zero, err,
+                                                                                                   stat);
     plan0_count_kernel<<<warp_blocks, 256, 0, s>>>(arena, start, size, n, C, max_chunks, cls, meta, cuts);
-    plan0_bases_kernel<<<1, 3 * kCls, 0, s>>>(cls, counts);
+    plan0_bases_kernel<<<1, 3 * kCls, 0, s>>>(cls, counts, stat);
     plan0_place_kernel<<<blocks, 256, 0, s>>>(start, size, n, C, meta, cuts, items, ropes, cls);
     return cudaGetLastError();
 }
