@@ -1070,7 +1070,7 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
         }
         {
             ProfScope ps(GP_KERNEL_EVAL, s);
-            CK(launch_eval(lanes, false, p, sms, (int)cfg.W, cfg.smem, s));
+            CK(launch_eval(lanes, false, p, sms, (int)cfg.W, cfg.smem, s, true));
         }
         if (max_ropes) {
             p.items = ropes;
@@ -1079,7 +1079,7 @@ gp_status eval_device_planned(gp_population *P, const EvalCfg &cfg, cudaStream_t
             p.counter = d_counter + 1;
             p.window = cfg.Kr;
             ProfScope ps(GP_KERNEL_EVAL_UPPER, s);
-            CK(launch_eval(lanes, true, p, sms, (int)cfg.Wr, cfg.smem_r, s));
+            CK(launch_eval(lanes, true, p, sms, (int)cfg.Wr, cfg.smem_r, s, true));
             P->redo_pending = true;
         }
         P->stat_pending = true;

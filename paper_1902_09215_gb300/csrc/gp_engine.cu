@@ -202,6 +202,7 @@ __global__ void children_size_kernel(const BatchCtl *ctl, RunDev *runs, const ui
                                      const uint64_t *__restrict__ ends, uint64_t *__restrict__ bstart,
                                      uint64_t *__restrict__ bsize)
 {
+    pdl_wait();
     const BatchHead h = ctl->head;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < h.n_trees; g += gridDim.x * blockDim.x) {
         const uint32_t slot = slot_of(tree_base, h.n_runs, g);
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(kScanT) children_scan_kernel(
     uint32_t *__restrict__ tile_local, uint32_t *__restrict__ run_tiles, uint64_t *__restrict__ bstart,
     uint64_t *__restrict__ bsize)
 {
+    pdl_wait();
     __shared__ uint64_t sa[kScanT], sb[kScanT];
     __shared__ uint32_t s_bad;
     __shared__ unsigned long long s_nodes;
@@ -267,7 +269,11 @@ __global__ void __launch_bounds__(kScanT) children_scan_kernel(
         __syncthreads();                      // sa / sb are rewritten by the next round
     }
     if (bad) atomicOr(&s_bad, bad);
-    atomicAdd(&s_nodes, (unsigned long long)nodes);
+    // the run's node total: a warp sum, then one shared atomic per warp (a
+    // 64-bit shared atomic from every thread of the CTA serialises)
+    unsigned long long wsum = nodes;
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_down_sync(0xffffffffu, wsum, o);
+    if ((t & 31) == 0) atomicAdd(&s_nodes, wsum);
     __syncthreads();
     uint32_t err = s_bad;
     if (carry_a + 64 > Cb.cap || carry_b >= 0x7fffffffull) err |= kGErrArena;
@@ -291,6 +297,7 @@ __global__ void children_place_kernel(const BatchCtl *ctl, RunDev *runs, const u
                                       const uint64_t *__restrict__ ends, XoChild *__restrict__ kids,
                                       uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize)
 {
+    pdl_wait();
     const BatchHead h = ctl->head;
     if (h.mode != kModeGenerate || ctl->eval_err[1] != 0) return;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < h.n_trees; g += gridDim.x * blockDim.x) {
@@ -321,6 +328,7 @@ __global__ void children_place_kernel(const BatchCtl *ctl, RunDev *runs, const u
 // Run tile counts -> exclusive offsets (entry n_runs = all tiles).
 __global__ void run_tiles_scan_kernel(BatchCtl *ctl, uint32_t *run_tiles)
 {
+    pdl_wait();
     if (threadIdx.x != 0) return;
     const uint32_t n = ctl->head.n_runs;
     uint64_t s = 0;
@@ -365,6 +373,7 @@ __global__ void cut_fused_kernel(const BatchCtl *ctl, uint32_t C, const uint8_t 
                                  const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
                                  uint32_t *__restrict__ t_nch, uint32_t *__restrict__ t_cut)
 {
+    pdl_wait();
     if (ctl->err != 0) return;
     const uint32_t n = ctl->head.n_trees;
     const int lane = threadIdx.x & 31;
@@ -407,6 +416,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     const uint32_t *__restrict__ t_nch, const uint32_t *__restrict__ t_cut, EvalItem *__restrict__ items,
     EvalItem *__restrict__ rope_items)
 {
+    pdl_wait();
     __shared__ uint64_t sa[kScanT], sb[kScanT];
     __shared__ uint32_t s_cnt[kBuckets], s_fill[kBuckets];
     __shared__ uint32_t s_rcnt[kBuckets], s_rfill[kBuckets], s_rbase[kBuckets];
@@ -607,6 +617,7 @@ __global__ void fill_chunks_kernel(const BatchCtl *ctl, uint32_t C, const uint32
                                    const uint64_t *__restrict__ t_lo, const uint64_t *__restrict__ t_hi,
                                    EvalItem *__restrict__ items)
 {
+    pdl_wait();
     const uint32_t n = ctl->n_chunks, n_trees = ctl->head.n_trees;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         uint32_t lo = 0, hi = n_trees;
@@ -636,6 +647,7 @@ __global__ void check_kernel(BatchCtl *ctl, uint64_t cap_codes, uint64_t cap_val
                              uint32_t idx, uint32_t *counter, uint32_t cond, cudaGraphConditionalHandle more,
                              cudaGraphConditionalHandle zero)
 {
+    pdl_wait();
     __shared__ uint32_t s_ok;
     const uint64_t codes = ctl->totals[0], vals = ctl->totals[1];
     if (threadIdx.x == 0) {
@@ -1289,17 +1301,22 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
     uint32_t nl = 0;
     const bool wide = dyn || level > 0;
     const int k = level & 1;
+    const bool pdl = !dyn;               // inside a conditional body: plain launches
     LevelArgs A{dyn ? kDynLevel : level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu),
                 dyn ? levels_cap_graph : (level + 1 == levels_max ? 1u : 0u), w.spill_base, w.cap_dedicated,
                 w.cap_slots};
     if (level == 0 && !dyn) {
-        cut_fused_kernel<<<sms * 8, 256, 0, s>>>(ctl, w.C, heap, bstart_, bsize_, t_nch_, t_cut_);
-        GK(cudaGetLastError());
+        GK(launch_pdl(cut_fused_kernel, dim3(sms * 8), dim3(256), 0, s, ctl, w.C, heap, bstart_, bsize_, t_nch_, t_cut_));
         ++nl;
     }
-    items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
-                                      t_state_, t_nch_, t_cut_, w.items, rope_items_);
-    GK(cudaGetLastError());
+    if (pdl) {
+        GK(launch_pdl(items_kernel, dim3(1), dim3(kScanT), 0, s, ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_,
+                      t_prev_, t_first_, t_state_, t_nch_, t_cut_, w.items, rope_items_));
+    } else {
+        items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
+                                          t_state_, t_nch_, t_cut_, w.items, rope_items_);
+        GK(cudaGetLastError());
+    }
     if (sizing) {
         // a dedicated spill pool too small for this level's oversized
         // finals: grow it, clear the error and build the level again
@@ -1342,11 +1359,15 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
         }
         prev_chunks = c.n_chunks;
     }
-    fill_chunks_kernel<<<sms * 4, 256, 0, s>>>(ctl, w.C, t_first_, t_lo_, t_hi_, w.items);
-    GK(cudaGetLastError());
+    if (pdl) {
+        GK(launch_pdl(fill_chunks_kernel, dim3(sms * 4), dim3(256), 0, s, ctl, w.C, t_first_, t_lo_, t_hi_, w.items));
+    } else {
+        fill_chunks_kernel<<<sms * 4, 256, 0, s>>>(ctl, w.C, t_first_, t_lo_, t_hi_, w.items);
+        GK(cudaGetLastError());
+    }
     const void *codes = wide ? (const void *)w.codes[k ^ 1] : (const void *)heap;
-    GK(launch_plan_dev(wide, codes, w.items, (uint32_t)w.cap_items, &ctl->n_chunks, w.plan, sms, s));
-    GK(launch_plan_scan_dev(w.items, w.plan, &ctl->n_chunks, w.frag_off, ctl->totals, s));
+    GK(launch_plan_dev(wide, codes, w.items, (uint32_t)w.cap_items, &ctl->n_chunks, w.plan, sms, s, pdl));
+    GK(launch_plan_scan_dev(w.items, w.plan, &ctl->n_chunks, w.frag_off, ctl->totals, s, pdl));
     nl += 4;
     if (sizing) {
         uint64_t tot[2];
@@ -1380,9 +1401,14 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
             w.cap_values[k] = nv;
         }
     }
-    check_kernel<<<1, 64, 0, s>>>(ctl, w.cap_codes[k], w.cap_values[k], w.codes[k], (uint32_t)k, cond.counter,
-                                  cond.flags, cond.more, cond.zero);
-    GK(cudaGetLastError());
+    if (pdl && !sizing) {
+        GK(launch_pdl(check_kernel, dim3(1), dim3(64), 0, s, ctl, w.cap_codes[k], w.cap_values[k], w.codes[k],
+                      (uint32_t)k, cond.counter, cond.flags, cond.more, cond.zero));
+    } else {
+        check_kernel<<<1, 64, 0, s>>>(ctl, w.cap_codes[k], w.cap_values[k], w.codes[k], (uint32_t)k, cond.counter,
+                                      cond.flags, cond.more, cond.zero);
+        GK(cudaGetLastError());
+    }
     EvalParams p{};
     p.codes = codes;
     p.items = w.items;
@@ -1415,7 +1441,7 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
         p.fz_cap_codes = w.C;
         p.fz_cap_pt = w.fz_cap_pt;
     }
-    GK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s));
+    GK(launch_eval(lanes, wide, p, sms, (int)(wide ? Wu : W), wide ? smem_u : smem, s, pdl));
     nl += 2;
     *nl_out += nl;
     return GP_OK;
@@ -1570,16 +1596,15 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     // (eval_err[3], zeroed above, counts the walks left to the long-walk launch)
     GK(launch_extent_dev(heap, q_, 2 * max_trees, &ctl->n_queries, ends_, &ctl->eval_err[1], xlong_,
                          &ctl->eval_err[3], sms, s));
-    children_size_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, q_, ends_, bstart_, bsize_);
-    GK(cudaGetLastError());
-    children_scan_kernel<<<max_runs, kScanT, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, tile_local_, run_tiles_,
-                                                      bstart_, bsize_);
-    GK(cudaGetLastError());
-    children_place_kernel<<<blocks, 128, 0, s>>>(ctl, runs_dev, slot_run_, tree_base_, q_, ends_, kids_, bstart_,
-                                                  bsize_);
-    GK(cudaGetLastError());
-    run_tiles_scan_kernel<<<1, 32, 0, s>>>(ctl, run_tiles_);
-    GK(cudaGetLastError());
+    // from here to level 0's evaluator every kernel is a programmatic
+    // dependent launch (its launch overlaps the tail of the one before)
+    GK(launch_pdl(children_size_kernel, dim3(blocks), dim3(128), 0, s, ctl, runs_dev, slot_run_, tree_base_, q_, ends_,
+                  bstart_, bsize_));
+    GK(launch_pdl(children_scan_kernel, dim3(max_runs), dim3(kScanT), 0, s, ctl, runs_dev, slot_run_, tree_base_,
+                  tile_local_, run_tiles_, bstart_, bsize_));
+    GK(launch_pdl(children_place_kernel, dim3(blocks), dim3(128), 0, s, ctl, runs_dev, slot_run_, tree_base_, q_, ends_,
+                  kids_, bstart_, bsize_));
+    GK(launch_pdl(run_tiles_scan_kernel, dim3(1), dim3(32), 0, s, ctl, run_tiles_));
     GK(launch_xo_copy_runs(heap, kids_, tile_local_, tree_base_, run_tiles_, &ctl->head.n_runs, &ctl->n_tiles,
                            kTile, sms, s));
     nl += 8;

@@ -650,6 +650,7 @@ __device__ __forceinline__ void eval_item(const EvalParams &P, const EvalItem *i
 template <int LANES, typename Code, bool WIDE>
 __global__ void __launch_bounds__(WIDE ? 512 : 1024, 1) eval_kernel(EvalParams P)
 {
+    pdl_wait();
     const int nwarps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr uint32_t S = LANES * sizeof(float2);
@@ -763,13 +764,24 @@ cudaError_t eval_prepare_at_least(int lanes, bool wide, size_t smem)
 }
 
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
-                        size_t smem, cudaStream_t s)
+                        size_t smem, cudaStream_t s, bool pdl)
 {
     void *fn = eval_fn_for(lanes, wide);
     if (!fn) return cudaErrorInvalidValue;
     EvalParams pp = p;
     void *args[] = {&pp};
-    return cudaLaunchKernel(fn, dim3(ctas), dim3(warps * 32), args, smem, s);
+    if (!pdl) return cudaLaunchKernel(fn, dim3(ctas), dim3(warps * 32), args, smem, s);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(warps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 // ---------------------------------------------------------------- planning
@@ -813,6 +825,7 @@ template <typename Code>
 __global__ void plan_kernel(const Code *__restrict__ codes, const EvalItem *__restrict__ items,
                             uint32_t n, const uint32_t *n_dev, PlanOut *__restrict__ out)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     if (n_dev) n = min(n, *n_dev);
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
@@ -890,12 +903,19 @@ cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uin
 }
 
 cudaError_t launch_plan_dev(bool wide, const void *codes, const EvalItem *items, uint32_t n_max,
-                            const uint32_t *n_dev, PlanOut *out, int sms, cudaStream_t s)
+                            const uint32_t *n_dev, PlanOut *out, int sms, cudaStream_t s, bool pdl)
 {
     if (n_max == 0) return cudaSuccess;
     const int threads = 256;
     const uint64_t want = ((uint64_t)n_max * 32 + threads - 1) / threads;
     const uint32_t blocks = (uint32_t)umin64(want, (uint64_t)sms * 16);
+    if (pdl) {
+        if (wide)
+            return launch_pdl(plan_kernel<uint32_t>, dim3(blocks), dim3(threads), 0, s, (const uint32_t *)codes, items,
+                              n_max, n_dev, out);
+        return launch_pdl(plan_kernel<uint8_t>, dim3(blocks), dim3(threads), 0, s, (const uint8_t *)codes, items,
+                          n_max, n_dev, out);
+    }
     if (wide) plan_kernel<uint32_t><<<blocks, threads, 0, s>>>((const uint32_t *)codes, items, n_max, n_dev, out);
     else plan_kernel<uint8_t><<<blocks, threads, 0, s>>>((const uint8_t *)codes, items, n_max, n_dev, out);
     return cudaGetLastError();
@@ -906,6 +926,7 @@ cudaError_t launch_plan_dev(bool wide, const void *codes, const EvalItem *items,
 __global__ void plan_scan_kernel(EvalItem *items, const PlanOut *plan, uint32_t n,
                                  const uint32_t *n_dev, uint64_t *frag_off, uint64_t *totals)
 {
+    pdl_wait();
     if (n_dev) n = *n_dev;
     if (n == 0) {
         if (threadIdx.x == 0) {
@@ -963,8 +984,9 @@ cudaError_t launch_plan_scan(EvalItem *items, const PlanOut *plan, uint32_t n,
 }
 
 cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uint32_t *n_dev,
-                                 uint64_t *frag_off, uint64_t *totals, cudaStream_t s)
+                                 uint64_t *frag_off, uint64_t *totals, cudaStream_t s, bool pdl)
 {
+    if (pdl) return launch_pdl(plan_scan_kernel, dim3(1), dim3(1024), 0, s, items, plan, 0u, n_dev, frag_off, totals);
     plan_scan_kernel<<<1, 1024, 0, s>>>(items, plan, 0, n_dev, frag_off, totals);
     return cudaGetLastError();
 }

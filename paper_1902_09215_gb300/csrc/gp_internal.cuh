@@ -1,6 +1,7 @@
 // Internal types shared by libgp's host code and its CUDA kernels.
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace gpk {
@@ -22,6 +23,30 @@ constexpr uint32_t kErrExtent = 8u;     // subtree extent walked off the end of 
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+// Programmatic dependent launch: a kernel started by launch_pdl may begin
+// while the kernel before it in the stream is still finishing, so its
+// launch overlaps that kernel's tail; it calls pdl_wait() before it reads or
+// writes any memory (the wait returns once the kernel before it has
+// completed and its writes are visible; without the launch attribute it
+// returns at once).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 constexpr uint32_t kLowWindow = 512;       // codes searched before a chunk's longest end (16 per lane)
 
@@ -184,8 +209,9 @@ void note_launches(uint64_t n);
 // Launchers (defined in the .cu files; return the launch's error).
 size_t eval_smem_bytes(int lanes, int warps, int window, bool wide, int leaf_rows = (int)kLeafRows);
 cudaError_t eval_prepare_at_least(int lanes, bool wide, size_t smem);
+// pdl: launched with programmatic stream serialization (launch_pdl).
 cudaError_t launch_eval(int lanes, bool wide, const EvalParams &p, int ctas, int warps,
-                        size_t smem, cudaStream_t s);
+                        size_t smem, cudaStream_t s, bool pdl = false);
 cudaError_t launch_plan(bool wide, const void *codes, const EvalItem *items, uint32_t n,
                         PlanOut *out, cudaStream_t s);
 cudaError_t launch_plan_scan(EvalItem *items, const PlanOut *plan, uint32_t n,
@@ -194,9 +220,9 @@ cudaError_t launch_plan_scan(EvalItem *items, const PlanOut *plan, uint32_t n,
 // Device-count forms: at most n_max items, the count read from *n_dev on the
 // device (for launch sequences that never return to the host).
 cudaError_t launch_plan_dev(bool wide, const void *codes, const EvalItem *items, uint32_t n_max,
-                            const uint32_t *n_dev, PlanOut *out, int sms, cudaStream_t s);
+                            const uint32_t *n_dev, PlanOut *out, int sms, cudaStream_t s, bool pdl = false);
 cudaError_t launch_plan_scan_dev(EvalItem *items, const PlanOut *plan, const uint32_t *n_dev,
-                                 uint64_t *frag_off, uint64_t *totals, cudaStream_t s);
+                                 uint64_t *frag_off, uint64_t *totals, cudaStream_t s, bool pdl = false);
 // Level-0 items of trees whose sizes are on the device, all at most
 // max_chunks chunks of C codes: counts[0] items (fused chunks, then
 // finals), counts[1] ropes (next launch), counts[2] slots.  A multi-chunk

@@ -30,6 +30,7 @@ __global__ void plan0_count_kernel(const uint8_t *__restrict__ arena, const uint
                                    const uint64_t *__restrict__ size, uint32_t n, uint32_t C, uint32_t mcap_max,
                                    uint32_t *cls, uint32_t *meta, uint32_t *cuts)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t t = warp; t < n; t += warps) {
@@ -61,6 +62,7 @@ __global__ void plan0_count_kernel(const uint8_t *__restrict__ arena, const uint
 // err[12] (the redo count); stat[3] (the crossover layout's error) stays.
 __global__ void plan0_zero_kernel(uint32_t *__restrict__ zero, uint32_t n_zero, uint32_t *err, uint32_t *stat)
 {
+    pdl_wait();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_zero; i += gridDim.x * blockDim.x) zero[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x < 4) err[threadIdx.x] = 0;
     if (blockIdx.x == 0 && threadIdx.x >= 4 && threadIdx.x < 7) stat[threadIdx.x] = 0;
@@ -70,6 +72,7 @@ __global__ void plan0_zero_kernel(uint32_t *__restrict__ zero, uint32_t n_zero, 
 // counts[0..2] (and stat[0..2] when given) from the class counts.
 __global__ void plan0_bases_kernel(uint32_t *cls, uint32_t *counts, uint32_t *stat)
 {
+    pdl_wait();
     __shared__ uint32_t v[3 * kCls];
     for (int i = threadIdx.x; i < 3 * kCls; i += blockDim.x) v[i] = cls[i];
     __syncthreads();
@@ -107,6 +110,7 @@ __global__ void plan0_place_kernel(const uint64_t *__restrict__ start, const uin
                                    uint32_t C, const uint32_t *__restrict__ meta, const uint32_t *__restrict__ cuts,
                                    EvalItem *__restrict__ items, EvalItem *__restrict__ ropes, uint32_t *cls)
 {
+    pdl_wait();
     uint32_t *slots = cls + 3 * kCls;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint64_t z = size[t], b = start[t];
@@ -159,12 +163,16 @@ cudaError_t launch_plan_level0(const uint8_t *arena, const uint64_t *start, cons
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)umin64((n + 255) / 256, (uint64_t)sms * 4);
     const uint32_t warp_blocks = (uint32_t)umin64((n + 7) / 8, (uint64_t)sms * 16);   // a warp per tree
-    plan0_zero_kernel<<<(uint32_t)umin64((n_zero + 255) / 256 + 1, (uint64_t)sms * 4), 256, 0, s>>>(zero, n_zero, err,
-                                                                                                   stat);
-    plan0_count_kernel<<<warp_blocks, 256, 0, s>>>(arena, start, size, n, C, max_chunks, cls, meta, cuts);
-    plan0_bases_kernel<<<1, 3 * kCls, 0, s>>>(cls, counts, stat);
-    plan0_place_kernel<<<blocks, 256, 0, s>>>(start, size, n, C, meta, cuts, items, ropes, cls);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(plan0_zero_kernel, dim3((uint32_t)umin64((n_zero + 255) / 256 + 1, (uint64_t)sms * 4)),
+                               dim3(256), 0, s, zero, n_zero, err, stat);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(plan0_count_kernel, dim3(warp_blocks), dim3(256), 0, s, arena, start, size, n, C, max_chunks, cls,
+                   meta, cuts);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(plan0_bases_kernel, dim3(1), dim3(3 * kCls), 0, s, cls, counts, stat);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(plan0_place_kernel, dim3(blocks), dim3(256), 0, s, start, size, n, C, meta, cuts, items, ropes,
+                      cls);
 }
 
 }  // namespace gpk

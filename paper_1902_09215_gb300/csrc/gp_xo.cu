@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(kExtT) extent_long_kernel(const uint8_t *__res
                                                           const uint32_t *n_long, uint64_t *__restrict__ end_out,
                                                           uint32_t *err)
 {
+    pdl_wait();
     __shared__ int s_wsum[kExtT / 32];
     __shared__ int s_first;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(256, 8) extent_dev_kernel(const uint8_t *__res
                                   uint32_t n_max, const uint32_t *n_dev, uint64_t *__restrict__ end_out,
                                   uint32_t *err, ExtentLong *__restrict__ list, uint32_t *n_long)
 {
+    pdl_wait();
     const uint32_t n = min(n_max, *n_dev);
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += n_warps)
@@ -231,8 +233,10 @@ cudaError_t launch_extent(const uint8_t *arena, const ExtentQuery *q, uint32_t n
     const int threads = 256;
     const uint32_t blocks = (uint32_t)(((uint64_t)n * 32 + threads - 1) / threads);
     extent_kernel<<<blocks, threads, 0, s>>>(arena, q, n, end, err, list, n_long);
-    extent_long_kernel<<<(uint32_t)umin64(n, (uint64_t)sms * 4), kExtT, 0, s>>>(arena, q, list, n_long, end, err);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_pdl(extent_long_kernel, dim3((uint32_t)umin64(n, (uint64_t)sms * 4)), dim3(kExtT), 0, s, arena, q,
+                      (const ExtentLong *)list, (const uint32_t *)n_long, end, err);
 }
 
 cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32_t n_max, const uint32_t *n_dev,
@@ -243,10 +247,11 @@ cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32
     const int threads = 256;
     const uint64_t want = ((uint64_t)n_max * 32 + threads - 1) / threads;
     const uint32_t blocks = (uint32_t)umin64(want, (uint64_t)sms * 16);
-    extent_dev_kernel<<<blocks, threads, 0, s>>>(arena, q, n_max, n_dev, end, err, list, n_long);
-    extent_long_kernel<<<(uint32_t)umin64(n_max, (uint64_t)sms * 4), kExtT, 0, s>>>(arena, q, list, n_long, end,
-                                                                                   err);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(extent_dev_kernel, dim3(blocks), dim3(threads), 0, s, arena, q, n_max, n_dev, end, err,
+                               list, n_long);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(extent_long_kernel, dim3((uint32_t)umin64(n_max, (uint64_t)sms * 4)), dim3(kExtT), 0, s, arena,
+                      q, (const ExtentLong *)list, (const uint32_t *)n_long, end, err);
 }
 
 
@@ -343,6 +348,7 @@ __global__ void xo_copy_runs_kernel(uint8_t *__restrict__ heap, const XoChild *_
                                     const uint32_t *__restrict__ run_tile_base, const uint32_t *n_runs_dev,
                                     const uint32_t *n_tiles_dev, uint32_t tile_bytes)
 {
+    pdl_wait();
     const uint32_t n_tiles = *n_tiles_dev, n_runs = *n_runs_dev;
     for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         uint32_t lo = 0, hi = n_runs;
@@ -368,9 +374,8 @@ cudaError_t launch_xo_copy_runs(uint8_t *heap, const XoChild *kids, const uint32
                                 const uint32_t *n_runs_dev, const uint32_t *n_tiles_dev, uint32_t tile_bytes,
                                 int sms, cudaStream_t s)
 {
-    xo_copy_runs_kernel<<<sms * 8, 256, 0, s>>>(heap, kids, tile_local, tree_base, run_tile_base, n_runs_dev,
-                                                 n_tiles_dev, tile_bytes);
-    return cudaGetLastError();
+    return launch_pdl(xo_copy_runs_kernel, dim3(sms * 8), dim3(256), 0, s, heap, kids, tile_local, tree_base,
+                      run_tile_base, n_runs_dev, n_tiles_dev, tile_bytes);
 }
 
 // Exclusive scan of a (64-bit, 32-bit) pair over the CTA (a multiple of 32
@@ -438,6 +443,7 @@ __global__ void __launch_bounds__(kLayoutT) xo_size_kernel(const ExtentQuery *__
                                                            uint32_t tile_bytes, uint64_t *__restrict__ csize,
                                                            uint64_t *__restrict__ part_len, uint32_t *__restrict__ part_tiles)
 {
+    pdl_wait();
     const uint32_t k = blockIdx.x * kLayoutT + threadIdx.x;
     uint64_t z = 0;
     if (k < n) {
@@ -458,6 +464,7 @@ __global__ void __launch_bounds__(1024) xo_part_scan_kernel(uint64_t *__restrict
                                                             uint32_t *__restrict__ tile_base, uint32_t n,
                                                             uint32_t *n_tiles)
 {
+    pdl_wait();
     __shared__ uint64_t carry_len;
     __shared__ uint32_t carry_t;
     if (threadIdx.x == 0) {
@@ -499,6 +506,7 @@ __global__ void __launch_bounds__(kLayoutT) xo_place_kernel(const ExtentQuery *_
                                                             uint32_t *__restrict__ tile_base,
                                                             uint32_t *__restrict__ tile_child, uint32_t *err)
 {
+    pdl_wait();
     const uint32_t k = blockIdx.x * kLayoutT + threadIdx.x;
     const uint64_t z = k < n ? csize[k] : 0;
     const uint64_t alen = (z + 15) & ~15ull;
@@ -537,11 +545,13 @@ cudaError_t launch_xo_layout(const ExtentQuery *q, const uint64_t *ends, uint32_
 {
     if (n == 0) return cudaSuccess;
     const uint32_t parts = xo_layout_parts(n);
-    xo_size_kernel<<<parts, kLayoutT, 0, s>>>(q, ends, n, tile_bytes, csize, part_len, part_tiles);
-    xo_part_scan_kernel<<<1, 1024, 0, s>>>(part_len, part_tiles, parts, tile_base, n, n_tiles);
-    xo_place_kernel<<<parts, kLayoutT, 0, s>>>(q, ends, n, tile_bytes, arena_cap, part_len, part_tiles, kids, cstart,
-                                               csize, tile_base, tile_child, err);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(xo_size_kernel, dim3(parts), dim3(kLayoutT), 0, s, q, ends, n, tile_bytes, csize,
+                               part_len, part_tiles);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(xo_part_scan_kernel, dim3(1), dim3(1024), 0, s, part_len, part_tiles, parts, tile_base, n, n_tiles);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(xo_place_kernel, dim3(parts), dim3(kLayoutT), 0, s, q, ends, n, tile_bytes, arena_cap, part_len,
+                      part_tiles, kids, cstart, csize, tile_base, tile_child, err);
 }
 
 // Copy tiles numbered on the device, each tile's child read from the map the
@@ -554,6 +564,7 @@ __global__ void xo_copy_map_kernel(const uint8_t *__restrict__ src, uint8_t *__r
                                    const uint32_t *__restrict__ tile_child, const uint32_t *n_tiles_dev,
                                    uint32_t tile_bytes)
 {
+    pdl_wait();
     const uint32_t n_tiles = *n_tiles_dev;
     const uint32_t first = WARP ? (threadIdx.x & 31) : threadIdx.x, stride = WARP ? 32 : blockDim.x;
     const uint32_t unit = WARP ? (blockIdx.x * blockDim.x + threadIdx.x) >> 5 : blockIdx.x;
@@ -570,12 +581,10 @@ cudaError_t launch_xo_copy_map(const uint8_t *src, uint8_t *dst, const XoChild *
 {
     if (max_tiles == 0) return cudaSuccess;
     if (warp_tiles)
-        xo_copy_map_kernel<true><<<(uint32_t)umin64((max_tiles + 7) / 8, 2048), 256, 0, s>>>(
-            src, dst, children, tile_base, tile_child, n_tiles_dev, tile_bytes);
-    else
-        xo_copy_map_kernel<false><<<(uint32_t)umin64(max_tiles, 8192), 256, 0, s>>>(
-            src, dst, children, tile_base, tile_child, n_tiles_dev, tile_bytes);
-    return cudaGetLastError();
+        return launch_pdl(xo_copy_map_kernel<true>, dim3((uint32_t)umin64((max_tiles + 7) / 8, 2048)), dim3(256), 0,
+                          s, src, dst, children, tile_base, tile_child, n_tiles_dev, tile_bytes);
+    return launch_pdl(xo_copy_map_kernel<false>, dim3((uint32_t)umin64(max_tiles, 8192)), dim3(256), 0, s, src, dst,
+                      children, tile_base, tile_child, n_tiles_dev, tile_bytes);
 }
 
 cudaError_t launch_xo_copy_dev(const uint8_t *src, uint8_t *dst, const XoChild *children,
