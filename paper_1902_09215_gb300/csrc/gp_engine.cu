@@ -364,14 +364,17 @@ __device__ __forceinline__ uint32_t size_bucket(uint64_t len)
     return min(b, kBuckets - 1);
 }
 
-// Level 0, before its items: every tree of 2..kFuseMaxChunks chunks is cut
-// where its arity walk is low (cut_low; one chunk more than ceil(size / C)
-// at most, never more than kFuseMaxChunks), a warp per tree.  t_nch[i]: the
+// Level 0, before its items, a warp per tree: the tree's level-0 range and
+// state (t_lo, t_hi, t_prev, t_state), and every tree of 2..kFuseMaxChunks
+// chunks is cut where its arity walk is low (cut_low; one chunk more than
+// ceil(size / C) at most, never more than kFuseMaxChunks).  t_nch[i]: the
 // tree's chunk count (0 for the other trees); t_cut[i * (kFuseMaxChunks - 1)
 // + j]: the end of its chunk j, relative to the tree's start.
 __global__ void cut_fused_kernel(const BatchCtl *ctl, uint32_t C, const uint8_t *__restrict__ heap,
                                  const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
-                                 uint32_t *__restrict__ t_nch, uint32_t *__restrict__ t_cut)
+                                 uint32_t *__restrict__ t_nch, uint32_t *__restrict__ t_cut,
+                                 uint64_t *__restrict__ t_lo, uint64_t *__restrict__ t_hi,
+                                 uint64_t *__restrict__ t_prev, uint32_t *__restrict__ t_state)
 {
     pdl_wait();
     if (ctl->err != 0) return;
@@ -389,7 +392,14 @@ __global__ void cut_fused_kernel(const BatchCtl *ctl, uint32_t C, const uint8_t 
                 if (lane == 0) cut[j - 1] = (uint32_t)(e - b);
             });
         }
-        if (lane == 0) t_nch[i] = k;
+        if (lane == 0) {
+            t_nch[i] = k;
+            const uint64_t b = bstart[i];
+            t_lo[i] = b;
+            t_hi[i] = b + z;
+            t_prev[i] = ~0ull;
+            t_state[i] = z != 0;
+        }
     }
 }
 
@@ -406,15 +416,22 @@ __global__ void cut_fused_kernel(const BatchCtl *ctl, uint32_t C, const uint8_t 
 // tree's chunks are the ones cut_fused_kernel chose (t_nch, t_cut).
 // Items: planned chunks first in tree order (their fragments must be
 // contiguous per tree), then fused chunks, then finals (ropes included)
-// from the largest size bucket down.
+// from the largest size bucket down.  This CTA only takes the decisions and
+// the offsets (tree-order scans); the items themselves are written by
+// fill_items_kernel from three compact lists: fz_tree (the tree of every
+// fused chunk), fin_tree (the tree of every final item, bit 31 for a rope)
+// and rope_tree (level 0's ropes, largest first), so that one SM does not
+// carry every item's bytes.
 // Tree states: 0 done or empty, 1 open (planned), 2 rope pending (t_lo: its
-// first slot, t_hi: its chunk count).
+// first slot, t_hi: its chunk count).  At level 0, cut_fused_kernel has set
+// every tree's range and state; a final with a dedicated spill area keeps
+// its spill offset in t_prev.
 __global__ void __launch_bounds__(kScanT) items_kernel(
     BatchCtl *ctl, LevelArgs A, const uint64_t *__restrict__ bstart, const uint64_t *__restrict__ bsize,
     const uint64_t *__restrict__ frag_off, uint64_t *__restrict__ t_lo, uint64_t *__restrict__ t_hi,
     uint64_t *__restrict__ t_prev, uint32_t *__restrict__ t_first, uint32_t *__restrict__ t_state,
-    const uint32_t *__restrict__ t_nch, const uint32_t *__restrict__ t_cut, EvalItem *__restrict__ items,
-    EvalItem *__restrict__ rope_items)
+    const uint32_t *__restrict__ t_nch, uint32_t *__restrict__ fz_tree, uint32_t *__restrict__ fin_tree,
+    uint32_t *__restrict__ rope_tree, bool list_ropes)
 {
     pdl_wait();
     __shared__ uint64_t sa[kScanT], sb[kScanT];
@@ -441,74 +458,74 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
         s_rcnt[t] = 0;
         s_rfill[t] = 0;
     }
-    const uint32_t per = (n + kScanT - 1) / kScanT;
-    const uint32_t lo = min(t * per, n), hi = min(lo + per, n);
     const uint64_t fuse_hi = (level == 0 && A.cap_slots) ? (uint64_t)kFuseMaxChunks * C : 0;
+    // Trees go through in rounds of kScanT, one tree per thread (coalesced
+    // loads and stores); every prefix over trees is a block scan per round
+    // plus a running carry, so all offsets stay in tree order.
+    const uint32_t rounds = (n + kScanT - 1) / kScanT;
 
     // phase 1: this level's range of every open tree (all reads of the old
     // t_first happen before the barrier; phase 3 rewrites it)
-    for (uint32_t i = lo; i < hi; ++i) {
-        if (level == 0) {
-            t_lo[i] = bstart[i];
-            t_hi[i] = bstart[i] + bsize[i];
-            t_prev[i] = ~0ull;
-            t_state[i] = bsize[i] != 0;
-        } else if (t_state[i] == 1) {
-            t_lo[i] = frag_off[t_first[i]];
-            t_hi[i] = frag_off[t_first[i + 1]];
+    if (level > 0) {
+        for (uint32_t i = t; i < n; i += kScanT) {
+            if (t_state[i] == 1) {
+                t_lo[i] = frag_off[t_first[i]];
+                t_hi[i] = frag_off[t_first[i + 1]];
+            }
         }
     }
     __syncthreads();
     // level 0: trees of 2..kFuseMaxChunks chunks take fused slots in tree
     // order while slots remain (the ones after are planned: a batch that
     // outgrew the slots still runs); state 3 marks them until phase 3
-    uint64_t ncand = 0;
     if (fuse_hi) {
-        for (uint32_t i = lo; i < hi; ++i) {
-            const uint64_t len = t_hi[i] - t_lo[i];
-            if (t_state[i] == 1 && len > C && len <= fuse_hi) ncand += t_nch[i];
+        uint64_t run_c = 0;                   // slots asked for by the trees of earlier rounds
+        for (uint32_t r = 0; r < rounds; ++r) {
+            const uint32_t i = r * kScanT + t;
+            uint64_t m = 0;
+            if (i < n && t_state[i] == 1) {
+                const uint64_t len = t_hi[i] - t_lo[i];
+                if (len > C && len <= fuse_hi) m = t_nch[i];
+            }
+            block_scan2(sa, sb, m, 0);
+            if (m && run_c + sa[t] <= A.cap_slots) t_state[i] = 3;   // sa[t]: up to and including tree i
+            run_c += sa[kScanT - 1];
+            __syncthreads();                  // the arrays are scanned again
         }
+        if (t == 0) ctl->need_slots = max(ctl->need_slots, run_c);
     }
-    block_scan2(sa, sb, ncand, 0);
-    uint64_t run_c = sa[t] - ncand;
-    if (t == 0) ctl->need_slots = max(ctl->need_slots, sa[kScanT - 1]);
-    __syncthreads();                          // the arrays are scanned again
-    if (fuse_hi) {
-        for (uint32_t i = lo; i < hi; ++i) {
-            const uint64_t len = t_hi[i] - t_lo[i];
-            if (t_state[i] != 1 || len <= C || len > fuse_hi) continue;
-            const uint64_t m = t_nch[i];
-            if (run_c + m <= A.cap_slots) t_state[i] = 3;
-            run_c += m;
-        }
-    }
-    // phase 2: planned chunks, dedicated spill, fused chunks and finals per
-    // size bucket
-    uint64_t nch = 0, ded = 0, nfz = 0;
-    for (uint32_t i = lo; i < hi; ++i) {
-        if (!t_state[i]) continue;
-        if (t_state[i] == 2) {                // a rope: final
-            atomicAdd(&s_cnt[size_bucket(t_hi[i] * C)], 1u);
-            continue;
-        }
+    // phase 2 (counts) and phase 3 (items) see each tree the same way: its
+    // planned chunks, dedicated spill entries and fused chunks, with the
+    // finals and ropes counted per size bucket in phase 2
+    auto shares = [&](uint32_t i, uint64_t &nch, uint64_t &ded, uint64_t &nfz) {
+        nch = ded = nfz = 0;
+        if (i >= n) return;
+        const uint32_t st = t_state[i];
+        if (st == 0 || st == 2) return;
         const uint64_t len = t_hi[i] - t_lo[i];
-        if (t_state[i] == 3) {
-            nfz += t_nch[i];
-            atomicAdd(&s_rcnt[size_bucket(len)], 1u);
-        } else if (last || len <= C || 2 * len > t_prev[i]) {
-            atomicAdd(&s_cnt[size_bucket(len)], 1u);
-            if (len > C) ded += len;
-        } else {
-            nch += (len + C - 1) / C;
+        if (st == 3) nfz = t_nch[i];
+        else if (last || len <= C || 2 * len > t_prev[i]) ded = len > C ? len : 0;
+        else nch = (len + C - 1) / C;
+    };
+    uint64_t tot_ch = 0, tot_ded = 0, tot_fz = 0;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t i = r * kScanT + t;
+        uint64_t nch, ded, nfz;
+        shares(i, nch, ded, nfz);
+        if (i < n && t_state[i] != 0) {
+            const uint32_t st = t_state[i];
+            if (st == 2) atomicAdd(&s_cnt[size_bucket(t_hi[i] * C)], 1u);      // a rope: final
+            else if (st == 3) atomicAdd(&s_rcnt[size_bucket(t_hi[i] - t_lo[i])], 1u);
+            else if (nch == 0) atomicAdd(&s_cnt[size_bucket(t_hi[i] - t_lo[i])], 1u);
         }
+        // chunk and fused counts are below 2^32 in all (item counts), so one
+        // 64-bit word carries both
+        block_scan2(sa, sb, (nch << 32) | nfz, ded);
+        tot_ch += sa[kScanT - 1] >> 32;
+        tot_fz += sa[kScanT - 1] & 0xffffffffull;
+        tot_ded += sb[kScanT - 1];
+        __syncthreads();                      // the arrays are scanned again
     }
-    block_scan2(sa, sb, nch, ded);
-    uint64_t ex_ch = sa[t] - nch, ex_ded = sb[t] - ded;
-    const uint64_t tot_ch = sa[kScanT - 1], tot_ded = sb[kScanT - 1];
-    __syncthreads();                          // the arrays are scanned again
-    block_scan2(sa, sb, nfz, 0);
-    uint64_t ex_fz = sa[t] - nfz;
-    const uint64_t tot_fz = sa[kScanT - 1];
     if (t == 0) {
         uint64_t pos = tot_ch + tot_fz;       // finals after the chunks, largest bucket first
         for (int b = (int)kBuckets - 1; b >= 0; --b) {
@@ -533,7 +550,7 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
             ctl->n_chunks = (uint32_t)tot_ch;
             ctl->n_ropes = (uint32_t)tot_fz;
             if (pos) ctl->levels = level + 1;
-            if (level == 0 && rope_items) {
+            if (level == 0 && list_ropes) {
                 ctl->n_rope_items = rpos;
                 if (rpos) ctl->levels = 2;    // the ropes are level 1
             }
@@ -544,95 +561,124 @@ __global__ void __launch_bounds__(kScanT) items_kernel(
     if (s_err) return;
     // phase 3: chunk offsets per tree, fused chunks, final items (any order
     // within a bucket), states
-    for (uint32_t i = lo; i < hi; ++i) {
-        t_first[i] = (uint32_t)ex_ch;
-        if (!t_state[i]) continue;
-        if (t_state[i] == 2) {
-            const uint32_t b = size_bucket(t_hi[i] * C);
-            EvalItem it{};
-            it.tree = i;
-            it.flags = kItemFinal | gpk::kItemRope;
-            it.pt_base = t_lo[i];
-            it.frag_len = (uint32_t)t_hi[i];
-            it.spill_off = kNoSpill;
-            items[s_base[b] + atomicAdd(&s_fill[b], 1u)] = it;
-            t_state[i] = 0;
-            continue;
-        }
-        const uint64_t len = t_hi[i] - t_lo[i];
-        if (t_state[i] != 3 && (last || len <= C || 2 * len > t_prev[i])) {
-            const uint32_t b = size_bucket(len);
-            EvalItem it{};
-            it.begin = t_lo[i];
-            it.end = t_hi[i];
-            it.tree = i;
-            it.flags = kItemFinal;
-            it.spill_off = kNoSpill;
-            if (len > C) {
-                it.spill_off = A.spill_base + ex_ded;
-                it.spill_cap = len;
-                ex_ded += len;
-            }
-            items[s_base[b] + atomicAdd(&s_fill[b], 1u)] = it;
-            t_state[i] = 0;
-        } else if (t_state[i] == 3) {
-            const uint32_t m = t_nch[i];
-            const uint32_t *cut = t_cut + (uint64_t)i * (kFuseMaxChunks - 1);
-            for (uint32_t j = 0; j < m; ++j) {
-                EvalItem it{};
-                it.begin = t_lo[i] + (j ? cut[j - 1] : 0u);
-                it.end = j + 1 < m ? t_lo[i] + cut[j] : t_hi[i];
-                it.tree = i;
-                it.flags = gpk::kItemFused;
-                it.frag_off = ex_fz + j;
-                it.pt_base = ex_fz;
-                it.frag_len = m;
-                it.spill_off = kNoSpill;
-                items[tot_ch + ex_fz + j] = it;
-            }
-            if (rope_items) {
-                EvalItem r{};
-                r.tree = i;
-                r.flags = kItemFinal | gpk::kItemRope;
-                r.pt_base = ex_fz;
-                r.frag_len = m;
-                r.spill_off = kNoSpill;
+    uint64_t c_ch = 0, c_ded = 0, c_fz = 0;   // carries from earlier rounds
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t i = r * kScanT + t;
+        uint64_t nch, ded, nfz;
+        shares(i, nch, ded, nfz);
+        block_scan2(sa, sb, (nch << 32) | nfz, ded);
+        const uint64_t ex = sa[t] - ((nch << 32) | nfz);
+        const uint64_t ex_ch = c_ch + (ex >> 32), ex_fz = c_fz + (ex & 0xffffffffull);
+        const uint64_t ex_ded = c_ded + sb[t] - ded;
+        c_ch += sa[kScanT - 1] >> 32;
+        c_fz += sa[kScanT - 1] & 0xffffffffull;
+        c_ded += sb[kScanT - 1];
+        if (i < n) {
+            t_first[i] = (uint32_t)ex_ch;
+            const uint32_t st = t_state[i];
+            const uint64_t fin0 = tot_ch + tot_fz;      // first final item
+            if (st == 2) {
+                const uint32_t b = size_bucket(t_hi[i] * C);
+                fin_tree[s_base[b] - fin0 + atomicAdd(&s_fill[b], 1u)] = i | 0x80000000u;
+                t_state[i] = 0;
+            } else if (st == 3) {
+                const uint64_t len = t_hi[i] - t_lo[i];
+                const uint32_t m = t_nch[i];
+                for (uint32_t j = 0; j < m; ++j) fz_tree[ex_fz + j] = i;
+                if (list_ropes) {
+                    const uint32_t b = size_bucket(len);
+                    rope_tree[s_rbase[b] + atomicAdd(&s_rfill[b], 1u)] = i;
+                }
+                t_state[i] = 2;
+                t_lo[i] = ex_fz;
+                t_hi[i] = m;
+            } else if (st != 0 && nch == 0) {
+                const uint64_t len = t_hi[i] - t_lo[i];
                 const uint32_t b = size_bucket(len);
-                rope_items[s_rbase[b] + atomicAdd(&s_rfill[b], 1u)] = r;
+                if (len > C) t_prev[i] = ex_ded;
+                fin_tree[s_base[b] - fin0 + atomicAdd(&s_fill[b], 1u)] = i;
+                t_state[i] = 0;
+            } else if (st != 0) {
+                t_prev[i] = t_hi[i] - t_lo[i];
             }
-            t_state[i] = 2;
-            t_lo[i] = ex_fz;
-            t_hi[i] = m;
-            ex_fz += m;
-        } else {
-            t_prev[i] = len;
-            ex_ch += (len + C - 1) / C;
         }
+        __syncthreads();                      // the arrays are scanned again
     }
-    if (t == kScanT - 1) t_first[n] = (uint32_t)tot_ch;
+    if (t == 0) t_first[n] = (uint32_t)tot_ch;
 }
 
-// Chunk items: item i belongs to the last tree whose first chunk is <= i.
-__global__ void fill_chunks_kernel(const BatchCtl *ctl, uint32_t C, const uint32_t *__restrict__ t_first,
-                                   const uint64_t *__restrict__ t_lo, const uint64_t *__restrict__ t_hi,
-                                   EvalItem *__restrict__ items)
+// A level's items: [0, n_chunks) planned chunks (item i belongs to the last
+// tree whose first chunk is <= i), then the fused chunks of fz_tree (level
+// 0), then the finals of fin_tree; and level 0's ropes for a rope-only
+// level from rope_tree.  A grid-stride thread per item.
+__global__ void fill_items_kernel(const BatchCtl *ctl, LevelArgs A, const uint32_t *__restrict__ t_first,
+                                  const uint64_t *__restrict__ t_lo, const uint64_t *__restrict__ t_hi,
+                                  const uint64_t *__restrict__ t_prev, const uint64_t *__restrict__ bstart,
+                                  const uint64_t *__restrict__ bsize, const uint32_t *__restrict__ t_cut,
+                                  const uint32_t *__restrict__ fz_tree, const uint32_t *__restrict__ fin_tree,
+                                  const uint32_t *__restrict__ rope_tree, EvalItem *__restrict__ items,
+                                  EvalItem *__restrict__ rope_items)
 {
     pdl_wait();
-    const uint32_t n = ctl->n_chunks, n_trees = ctl->head.n_trees;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t lo = 0, hi = n_trees;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (t_first[mid] <= i) lo = mid;
-            else hi = mid;
-        }
+    if (ctl->err != 0) return;
+    const uint32_t C = A.C;
+    const uint32_t n_ch = ctl->n_chunks, n_fz = ctl->n_ropes, n_items = ctl->n_items, n_trees = ctl->head.n_trees;
+    const uint32_t n_rope = rope_items ? ctl->n_rope_items : 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_items; k += stride) {
         EvalItem it{};
-        it.begin = t_lo[lo] + (uint64_t)(i - t_first[lo]) * C;
-        it.end = umin64(t_hi[lo], it.begin + C);
-        it.tree = lo;
-        it.flags = 0;
         it.spill_off = kNoSpill;
-        items[i] = it;
+        if (k < n_ch) {
+            uint32_t lo = 0, hi = n_trees;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (t_first[mid] <= k) lo = mid;
+                else hi = mid;
+            }
+            it.begin = t_lo[lo] + (uint64_t)(k - t_first[lo]) * C;
+            it.end = umin64(t_hi[lo], it.begin + C);
+            it.tree = lo;
+        } else if (k < n_ch + n_fz) {
+            const uint32_t f = k - n_ch, i = fz_tree[f];
+            const uint32_t first = (uint32_t)t_lo[i], m = (uint32_t)t_hi[i], j = f - first;
+            const uint32_t *cut = t_cut + (uint64_t)i * (kFuseMaxChunks - 1);
+            const uint64_t b = bstart[i];
+            it.begin = b + (j ? cut[j - 1] : 0u);
+            it.end = j + 1 < m ? b + cut[j] : b + bsize[i];
+            it.tree = i;
+            it.flags = gpk::kItemFused;
+            it.frag_off = f;
+            it.pt_base = first;
+            it.frag_len = m;
+        } else {
+            const uint32_t e = fin_tree[k - n_ch - n_fz], i = e & 0x7fffffffu;
+            it.tree = i;
+            if (e >> 31) {                          // a rope: its slots
+                it.flags = kItemFinal | gpk::kItemRope;
+                it.pt_base = t_lo[i];
+                it.frag_len = (uint32_t)t_hi[i];
+            } else {
+                it.flags = kItemFinal;
+                it.begin = t_lo[i];
+                it.end = t_hi[i];
+                const uint64_t len = it.end - it.begin;
+                if (len > C) {
+                    it.spill_off = A.spill_base + t_prev[i];
+                    it.spill_cap = len;
+                }
+            }
+        }
+        items[k] = it;
+    }
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_rope; k += stride) {
+        const uint32_t i = rope_tree[k];
+        EvalItem r{};
+        r.tree = i;
+        r.flags = kItemFinal | gpk::kItemRope;
+        r.pt_base = t_lo[i];
+        r.frag_len = (uint32_t)t_hi[i];
+        r.spill_off = kNoSpill;
+        rope_items[k] = r;
     }
 }
 
@@ -898,6 +944,9 @@ gp_status Engine::init(const gp_problem *problem, uint64_t heap_bytes_, uint32_t
     if ((st = galloc(v, (void **)&t_state_, sizeof(uint32_t) * T))) return st;
     if ((st = galloc(v, (void **)&t_nch_, sizeof(uint32_t) * T))) return st;
     if ((st = galloc(v, (void **)&t_cut_, sizeof(uint32_t) * T * (kFuseMaxChunks - 1)))) return st;
+    if ((st = galloc(v, (void **)&fz_tree_, sizeof(uint32_t) * T * kFuseMaxChunks))) return st;
+    if ((st = galloc(v, (void **)&fin_tree_, sizeof(uint32_t) * T))) return st;
+    if ((st = galloc(v, (void **)&rope_tree_, sizeof(uint32_t) * T))) return st;
     if ((st = galloc(v, (void **)&rope_items_, sizeof(EvalItem) * T))) return st;
     if ((st = galloc(v, (void **)&x_, sizeof(float) * 2 * lanes))) return st;
     if ((st = galloc(v, (void **)&y_, sizeof(float) * 2 * lanes))) return st;
@@ -1305,18 +1354,31 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
     LevelArgs A{dyn ? kDynLevel : level, w.C, (uint32_t)std::min<uint64_t>(w.cap_items, 0xffffffffu),
                 dyn ? levels_cap_graph : (level + 1 == levels_max ? 1u : 0u), w.spill_base, w.cap_dedicated,
                 w.cap_slots};
-    if (level == 0 && !dyn) {
-        GK(launch_pdl(cut_fused_kernel, dim3(sms * 8), dim3(256), 0, s, ctl, w.C, heap, bstart_, bsize_, t_nch_, t_cut_));
-        ++nl;
-    }
-    if (pdl) {
-        GK(launch_pdl(items_kernel, dim3(1), dim3(kScanT), 0, s, ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_,
-                      t_prev_, t_first_, t_state_, t_nch_, t_cut_, w.items, rope_items_));
-    } else {
+    // the level's decisions: at level 0 the cut kernel first (it also sets
+    // every tree's level-0 range and state, so a build started again in the
+    // sizing pass starts from scratch), then the single-CTA item builder
+    auto build = [&](bool use_pdl) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (level == 0 && !dyn) {
+            if (use_pdl)
+                e = launch_pdl(cut_fused_kernel, dim3(sms * 8), dim3(256), 0, s, ctl, w.C, heap, bstart_, bsize_,
+                               t_nch_, t_cut_, t_lo_, t_hi_, t_prev_, t_state_);
+            else
+                cut_fused_kernel<<<sms * 8, 256, 0, s>>>(ctl, w.C, heap, bstart_, bsize_, t_nch_, t_cut_, t_lo_, t_hi_,
+                                                         t_prev_, t_state_);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        if (use_pdl)
+            return launch_pdl(items_kernel, dim3(1), dim3(kScanT), 0, s, ctl, A, bstart_, bsize_, w.frag_off, t_lo_,
+                              t_hi_, t_prev_, t_first_, t_state_, t_nch_, fz_tree_, fin_tree_, rope_tree_,
+                              rope_items_ != nullptr);
         items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_, t_first_,
-                                          t_state_, t_nch_, t_cut_, w.items, rope_items_);
-        GK(cudaGetLastError());
-    }
+                                          t_state_, t_nch_, fz_tree_, fin_tree_, rope_tree_, rope_items_ != nullptr);
+        return cudaGetLastError();
+    };
+    GK(build(pdl));
+    if (level == 0 && !dyn) ++nl;
     if (sizing) {
         // a dedicated spill pool too small for this level's oversized
         // finals: grow it, clear the error and build the level again
@@ -1333,9 +1395,7 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
             GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
             GK(cudaMemsetAsync(w.fz_over, 0, sizeof(uint32_t) * max_trees, s));
             GK(cudaMemsetAsync(w.fz_redo, 0, sizeof(uint32_t), s));
-            items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
-                                              t_first_, t_state_, t_nch_, t_cut_, w.items, rope_items_);
-            GK(cudaGetLastError());
+            GK(build(false));
             GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             GK(cudaStreamSynchronize(s));
         }
@@ -1351,18 +1411,19 @@ gp_status Engine::enqueue_level(uint32_t level, bool dyn, cudaStream_t s, bool s
             // from: put back the previous level's before building again
             GK(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), s));
             GK(cudaMemcpyAsync(&ctl->n_chunks, &prev_chunks, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
-            items_kernel<<<1, kScanT, 0, s>>>(ctl, A, bstart_, bsize_, w.frag_off, t_lo_, t_hi_, t_prev_,
-                                              t_first_, t_state_, t_nch_, t_cut_, w.items, rope_items_);
-            GK(cudaGetLastError());
+            GK(build(false));
             GK(cudaMemcpyAsync(&c, ctl, sizeof(c), cudaMemcpyDeviceToHost, s));
             GK(cudaStreamSynchronize(s));
         }
         prev_chunks = c.n_chunks;
     }
+    EvalItem *ropes_out = (level == 0 && !dyn) ? rope_items_ : nullptr;
     if (pdl) {
-        GK(launch_pdl(fill_chunks_kernel, dim3(sms * 4), dim3(256), 0, s, ctl, w.C, t_first_, t_lo_, t_hi_, w.items));
+        GK(launch_pdl(fill_items_kernel, dim3(sms * 4), dim3(256), 0, s, ctl, A, t_first_, t_lo_, t_hi_, t_prev_,
+                      bstart_, bsize_, t_cut_, fz_tree_, fin_tree_, rope_tree_, w.items, ropes_out));
     } else {
-        fill_chunks_kernel<<<sms * 4, 256, 0, s>>>(ctl, w.C, t_first_, t_lo_, t_hi_, w.items);
+        fill_items_kernel<<<sms * 4, 256, 0, s>>>(ctl, A, t_first_, t_lo_, t_hi_, t_prev_, bstart_, bsize_, t_cut_,
+                                                  fz_tree_, fin_tree_, rope_tree_, w.items, ropes_out);
         GK(cudaGetLastError());
     }
     const void *codes = wide ? (const void *)w.codes[k ^ 1] : (const void *)heap;

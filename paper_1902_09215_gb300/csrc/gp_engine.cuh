@@ -237,6 +237,7 @@ class Engine {
     uint64_t *t_lo_ = nullptr, *t_hi_ = nullptr, *t_prev_ = nullptr;
     uint32_t *t_first_ = nullptr, *t_state_ = nullptr, *t_nch_ = nullptr, *t_cut_ = nullptr;
     ExtentLong *xlong_ = nullptr;
+    uint32_t *fz_tree_ = nullptr, *fin_tree_ = nullptr, *rope_tree_ = nullptr;   // item builder's lists
     float *x_ = nullptr, *y_ = nullptr, *c_ = nullptr;
     // the last head written (a batch whose head is unchanged skips the copies)
     uint32_t last_mode_ = ~0u;
