@@ -20,7 +20,6 @@ using namespace gpk;
 namespace gpe {
 namespace {
 
-constexpr uint32_t kTile = 16384;        // copy tile (bytes)
 constexpr uint32_t kScanT = 1024;        // threads of the single-CTA scan kernels
 constexpr uint32_t kBuckets = 40;        // final items ordered by floor(log2(size)), largest first
 constexpr uint64_t kHeapLead = 256;      // heap bytes [0, 256): code 4 ('x'), a one-node tree
@@ -223,7 +222,7 @@ __global__ void children_size_kernel(const BatchCtl *ctl, RunDev *runs, const ui
 __global__ void __launch_bounds__(kScanT) children_scan_kernel(
     BatchCtl *ctl, RunDev *runs, const uint32_t *__restrict__ slot_run, const uint32_t *__restrict__ tree_base,
     uint32_t *__restrict__ tile_local, uint32_t *__restrict__ run_tiles, uint64_t *__restrict__ bstart,
-    uint64_t *__restrict__ bsize)
+    uint64_t *__restrict__ bsize, uint32_t tile)
 {
     pdl_wait();
     __shared__ uint64_t sa[kScanT], sb[kScanT];
@@ -258,7 +257,7 @@ __global__ void __launch_bounds__(kScanT) children_scan_kernel(
             if (max_nodes && m > max_nodes) bad |= kGErrLimit;
             nodes += m;
         }
-        const uint64_t a = (m + 15) & ~15ull, b = (m + kTile - 1) / kTile;
+        const uint64_t a = (m + 15) & ~15ull, b = (m + tile - 1) / tile;
         block_scan2(sa, sb, a, b);
         if (c < n) {
             bstart[base + c] = carry_a + sa[t] - a;
@@ -1662,12 +1661,12 @@ gp_status Engine::enqueue_body(uint32_t mode, cudaStream_t s, bool sizing, uint3
     GK(launch_pdl(children_size_kernel, dim3(blocks), dim3(128), 0, s, ctl, runs_dev, slot_run_, tree_base_, q_, ends_,
                   bstart_, bsize_));
     GK(launch_pdl(children_scan_kernel, dim3(max_runs), dim3(kScanT), 0, s, ctl, runs_dev, slot_run_, tree_base_,
-                  tile_local_, run_tiles_, bstart_, bsize_));
+                  tile_local_, run_tiles_, bstart_, bsize_, xo_tile));
     GK(launch_pdl(children_place_kernel, dim3(blocks), dim3(128), 0, s, ctl, runs_dev, slot_run_, tree_base_, q_, ends_,
                   kids_, bstart_, bsize_));
     GK(launch_pdl(run_tiles_scan_kernel, dim3(1), dim3(32), 0, s, ctl, run_tiles_));
     GK(launch_xo_copy_runs(heap, kids_, tile_local_, tree_base_, run_tiles_, &ctl->head.n_runs, &ctl->n_tiles,
-                           kTile, sms, s));
+                           xo_tile, xo_warp, sms, s));
     nl += 8;
     gp_status st = enqueue_eval(s, sizing, &nl);
     if (st) return st;

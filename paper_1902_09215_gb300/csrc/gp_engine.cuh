@@ -199,6 +199,10 @@ class Engine {
     Work w;
     uint32_t kernels_per_batch[2] = {0, 0};
     // kernels of a captured batch outside the level loop, and per loop level
+    // children's copy: CTAs on 16 KB tiles, or warps on 2 KB tiles for
+    // populations of small trees (set before the first capture)
+    uint32_t xo_tile = 16384;
+    bool xo_warp = false;
     uint32_t kernels_fixed[2] = {0, 0}, kernels_per_level = 0;
     // levels the captured loop may run (its last makes every open tree final)
     uint32_t levels_cap_graph = 16;

@@ -137,6 +137,10 @@ gp_status gp_generation_create(const gp_problem *problem, const gp_generation_pa
     gp_status st = E.init(problem, 2 * ((cap_arena + 255) & ~255ull), 1, n_trees,
                           params->max_levels ? params->max_levels : 8);
     if (st) return fail(st);
+    if (n_trees && offsets[n_trees] < 8192ull * n_trees) {   // small trees: warps copy 2 KB tiles
+        E.xo_tile = 2048;
+        E.xo_warp = true;
+    }
     step = "open_run";
     if ((st = E.open_run(n_trees, cap_arena, params->seed, params->tournament_size, problem->max_tree_nodes,
                          &G->run)))

@@ -271,7 +271,7 @@ cudaError_t launch_extent_dev(const uint8_t *arena, const ExtentQuery *q, uint32
 cudaError_t launch_xo_copy_runs(uint8_t *heap, const XoChild *kids, const uint32_t *tile_local,
                                 const uint32_t *tree_base, const uint32_t *run_tile_base,
                                 const uint32_t *n_runs_dev, const uint32_t *n_tiles_dev, uint32_t tile_bytes,
-                                int sms, cudaStream_t s);
+                                bool warp_tiles, int sms, cudaStream_t s);
 cudaError_t launch_xo_copy_dev(const uint8_t *src, uint8_t *dst, const XoChild *children,
                                const uint32_t *tile_base, uint32_t n_children,
                                const uint32_t *n_tiles_dev, uint32_t tile_bytes, int sms,

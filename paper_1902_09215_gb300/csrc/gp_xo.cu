@@ -343,6 +343,8 @@ cudaError_t launch_xo_copy(const uint8_t *src, uint8_t *dst, const XoChild *chil
 // Children of a batch of runs in one heap: tile t belongs to the last run
 // whose first tile is <= t, then to the last of that run's children whose
 // first tile (counted within the run) is <= the tile's index in the run.
+// A CTA per tile, or a warp per tile (WARP, small children).
+template <bool WARP>
 __global__ void xo_copy_runs_kernel(uint8_t *__restrict__ heap, const XoChild *__restrict__ kids,
                                     const uint32_t *__restrict__ tile_local, const uint32_t *__restrict__ tree_base,
                                     const uint32_t *__restrict__ run_tile_base, const uint32_t *n_runs_dev,
@@ -350,7 +352,10 @@ __global__ void xo_copy_runs_kernel(uint8_t *__restrict__ heap, const XoChild *_
 {
     pdl_wait();
     const uint32_t n_tiles = *n_tiles_dev, n_runs = *n_runs_dev;
-    for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint32_t first = WARP ? (threadIdx.x & 31) : threadIdx.x, stride = WARP ? 32 : blockDim.x;
+    const uint32_t unit = WARP ? (blockIdx.x * blockDim.x + threadIdx.x) >> 5 : blockIdx.x;
+    const uint32_t units = WARP ? (gridDim.x * blockDim.x) >> 5 : gridDim.x;
+    for (uint32_t t = unit; t < n_tiles; t += units) {
         uint32_t lo = 0, hi = n_runs;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -364,17 +369,19 @@ __global__ void xo_copy_runs_kernel(uint8_t *__restrict__ heap, const XoChild *_
             if (tile_local[mid] <= lt) a = mid;
             else b = mid;
         }
-        copy_tile(heap, heap, kids[a], (uint64_t)(lt - tile_local[a]) * tile_bytes, tile_bytes, threadIdx.x,
-                  blockDim.x);
+        copy_tile(heap, heap, kids[a], (uint64_t)(lt - tile_local[a]) * tile_bytes, tile_bytes, first, stride);
     }
 }
 
 cudaError_t launch_xo_copy_runs(uint8_t *heap, const XoChild *kids, const uint32_t *tile_local,
                                 const uint32_t *tree_base, const uint32_t *run_tile_base,
                                 const uint32_t *n_runs_dev, const uint32_t *n_tiles_dev, uint32_t tile_bytes,
-                                int sms, cudaStream_t s)
+                                bool warp_tiles, int sms, cudaStream_t s)
 {
-    return launch_pdl(xo_copy_runs_kernel, dim3(sms * 8), dim3(256), 0, s, heap, kids, tile_local, tree_base,
+    if (warp_tiles)
+        return launch_pdl(xo_copy_runs_kernel<true>, dim3(sms * 8), dim3(256), 0, s, heap, kids, tile_local, tree_base,
+                          run_tile_base, n_runs_dev, n_tiles_dev, tile_bytes);
+    return launch_pdl(xo_copy_runs_kernel<false>, dim3(sms * 8), dim3(256), 0, s, heap, kids, tile_local, tree_base,
                       run_tile_base, n_runs_dev, n_tiles_dev, tile_bytes);
 }
 
