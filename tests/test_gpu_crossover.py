@@ -153,3 +153,28 @@ def test_crossover_on_another_stream_then_parents_freed(gpu, oracle):
     kn, ko = gpu.read_all_trees(kids)
     assert np.array_equal(kn, rn) and np.array_equal(ko, ro)
     gpu.gp_destroy_population(other)
+
+
+def test_long_subtree_walks(gpu, oracle):
+    """Subtree ends found by the two-phase walk (a 512-byte warp step, then
+    a CTA per still-open walk at 16 KB per step): points at and near the
+    roots of trees of 1e5..3e5 nodes and of a left spine of depth 2e4 (its
+    subtrees end near the tree's end, so the CTA steps run into the tree's
+    last bytes), every child equal to the oracle's."""
+    rng = np.random.default_rng(31)
+    trees = [synth.random_tree(rng, 300001), synth.random_tree(rng, 100001),
+             synth.left_spine_tree(rng, 20000, 3), synth.random_tree(rng, 16385)]
+    nodes, offs = synth.pack(trees)
+    pop = make_pop(gpu, nodes, offs)
+    sizes = np.diff(offs.astype(np.int64))
+    recs = []
+    for a in range(len(trees)):
+        pts = sorted({0, 1, 2, 3, 17, int(sizes[a]) // 7, int(sizes[a]) - 2, int(sizes[a]) - 1})
+        for i in pts:
+            recs.append((a, (a + 1) % len(trees), i, pts[len(pts) // 2]))
+            recs.append((a, a, int(sizes[a]) - 1, i))
+    ops = tuple(np.array(v) for v in zip(*recs))
+    kids = gpu.gp_crossover(pop, ops)
+    kn, ko = gpu.read_all_trees(kids)
+    rn, ro = oracle.crossover_population(nodes, offs, *ops)
+    assert np.array_equal(kn, rn) and np.array_equal(ko, ro)
