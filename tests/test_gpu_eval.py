@@ -178,7 +178,7 @@ def test_repeat_evaluation_is_deterministic(gpu):
         assert same_f32(f, outs[0][0]) and same_f32(v, outs[0][1])
 
 
-@pytest.mark.parametrize("C", [1024, 4096])
+@pytest.mark.parametrize("C", [1024, 4096, 8192])
 def test_operators_sent_upward_follow_the_arity_walk(gpu, oracle, C):
     """The count of operators evaluated above level 0 (gp_eval_stats) equals
     the spine operators of every chunk, for an uploaded population (levels
