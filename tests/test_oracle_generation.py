@@ -125,6 +125,30 @@ def test_generation_records_points_uniform_and_in_range(oracle):
     assert np.sum(mum == best) > 20 * max(1, np.sum(mum == worst))
 
 
+def test_generation_records_parents_and_points_independent(oracle):
+    """Both parents come from tournaments of their own (Table gp.details):
+    mum == dad happens with probability sum_r p_r^2, p_r the rank-r winning
+    probability of a size-T tournament.  Each point is uniform over the nodes
+    of its own parent (Sec. 3.1), whatever the other parent's size."""
+    P, T, M = 40, 7, 20000
+    rng = np.random.default_rng(4)
+    fit = rng.permutation(P).astype(np.float32) * 0.5
+    sizes = (1 + 2 * rng.permutation(P)).astype(np.uint64)          # 1, 3, .., 79
+    mum, dad, mp, dp = oracle.generation_records(fit, sizes, M, seed=17, g=3, tsize=T)
+    pr = np.array([((P - r) / P) ** T - ((P - r - 1) / P) ** T for r in range(P)])
+    q = float((pr ** 2).sum())
+    same = float(np.mean(mum == dad))
+    assert abs(same - q) < 6 * math.sqrt(q * (1 - q) / M), (same, q)
+    assert np.all(mp < sizes[mum]) and np.all(dp < sizes[dad])
+    best = int(np.argmin(fit))
+    for who, pts in ((mum, mp), (dad, dp)):
+        sel = pts[who == best].astype(np.int64)
+        s = int(sizes[best])
+        if s > 1:
+            ok, chi2 = chi2_ok(np.bincount(sel, minlength=s), np.full(s, 1.0 / s))
+            assert ok, chi2
+
+
 def test_generation_records_deterministic_and_distinct(oracle):
     P = 30
     rng = np.random.default_rng(3)

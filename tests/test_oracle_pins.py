@@ -178,6 +178,10 @@ def test_prefix_invariant_generated_and_malformed(oracle):
     t = synth.random_tree(rng, 31)
     assert not oracle.check_tree(t[:-1])                          # truncated
     assert not oracle.check_tree(np.concatenate([t, [4]]))        # trailing node
+    # a complete tree followed by an operator and one leaf: the node count
+    # balances again, but the walk reached -1 before the last node
+    more = np.concatenate([t, [ADD, X]]).astype(np.uint8)
+    assert not arity_walk_ok(more) and not oracle.check_tree(more)
     bad = t.copy(); bad[-1] = 5 + 127
     assert not oracle.check_tree(bad)                             # code beyond table
     assert not oracle.check_tree(np.zeros(0, np.uint8))
