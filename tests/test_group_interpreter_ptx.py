@@ -153,14 +153,48 @@ def test_group_loop_matches_push_pop(parsed):
         assert bad is None, bad
 
 
-def test_model_catches_a_planted_operand_swap(parsed):
-    """The comparison has teeth: with the operands of one subtraction
-    swapped in the PTX text, some run disagrees."""
-    text = group_asm(SRC)
-    planted = text.replace("sub.rn.f32x2 %0, %0, v;", "sub.rn.f32x2 %0, v, %0;", 1)
-    assert planted != text
+# Planted mistakes in the PTX text (function, text, replacement, every
+# occurrence or only the first): each must make some random run disagree
+# with the plain meaning.  A run that the model cannot finish (a read of a
+# shared entry below the window, which on the GPU would read another lane's
+# or warp's data) counts as caught too.
+PLANTS = [
+    ("groups_u8", "sub.rn.f32x2 %0, %0, v;", "sub.rn.f32x2 %0, v, %0;", False),
+    ("groups_u8", "mul.rn.f32x2 %0, %0, v;", "add.rn.f32x2 %0, %0, v;", False),
+    ("groups_u8", "setp.lt.u32 p, c, 2;", "setp.lt.u32 p, c, 1;", False),
+    ("groups_u8", "selp.f32 tx, qx, %6, p;", "selp.f32 tx, %6, qx, p;", False),
+    ("groups_u8", "RET: .branchtargets E0, E1,", "RET: .branchtargets E1, E0,", False),
+    ("groups_u8", "setp.gt.u32 p, dd, %8;", "setp.lt.u32 p, dd, %8;", False),
+    ("groups_u8", "st.shared.b64 [%1], %0;\n\tadd.u32 %1, %1, %9;",
+     "add.u32 %1, %1, %9;\n\tst.shared.b64 [%1], %0;", False),
+    ("groups_u8", "setp.eq.u32 p, %1, %7;", "setp.eq.u32 p, %1, %5;", True),
+    ("groups_u8", "ENT: .branchtargets N0, N1, N2, W0,", "ENT: .branchtargets N0, N1, N2, N3,", False),
+    ("group_u32", "sub.rn.f32x2 %0, %0, v;", "sub.rn.f32x2 %0, v, %0;", False),
+    ("group_u32", "ld.shared.b64 %0, [%24+15*%23];", "ld.shared.b64 %0, [%24+14*%23];", False),
+    ("group_u32", "256;", "128;", True),
+    ("group_u32", "selp.f32 ty, qy, %20, p;", "selp.f32 ty, %20, qy, p;", False),
+    ("group_u32", "setp.gt.u32 p, dd, %22;", "setp.lt.u32 p, dd, %22;", False),
+]
+
+
+@pytest.mark.parametrize("fn,find,repl,every", PLANTS,
+                         ids=[f"{p[0]}:{p[1][:28]}" for p in PLANTS])
+def test_model_catches_planted_mistakes(fn, find, repl, every):
+    """The comparison has teeth: with one mistake planted in the PTX text,
+    some run disagrees."""
+    text = group_asm(SRC, fn)
+    assert find in text
+    planted = text.replace(find, repl) if every else text.replace(find, repl, 1)
+    prog = parse(planted)
+    trial = one_loop if fn == "groups_u8" else one_upper_group
     rng = np.random.default_rng(7)
-    assert any(one_loop(parse(planted), rng) for _ in range(300))
+    for _ in range(3000):
+        try:
+            if trial(prog, rng):
+                return
+        except (KeyError, RuntimeError):
+            return
+    pytest.fail("planted mistake not caught")
 
 
 STAGE = 0x200000                     # staged value entries of the group: STAGE + position * S
