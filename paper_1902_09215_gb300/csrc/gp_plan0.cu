@@ -160,6 +160,7 @@ cudaError_t launch_plan_level0(const uint8_t *arena, const uint64_t *start, cons
                                uint32_t *cls, uint32_t *meta, uint32_t *cuts, uint32_t *zero, uint32_t n_zero,
                                uint32_t *err, uint32_t *stat, int sms, cudaStream_t s)
 {
+    if (max_chunks == 0 || max_chunks > 32) return cudaErrorInvalidValue;   // meta holds chunks - 1 in 5 bits
     if (n == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)umin64((n + 255) / 256, (uint64_t)sms * 4);
     const uint32_t warp_blocks = (uint32_t)umin64((n + 7) / 8, (uint64_t)sms * 16);   // a warp per tree
